@@ -1,0 +1,286 @@
+/*
+ * Plain, slow CPU oracle for the local noise filter of arXiv 1807.03119
+ * ("Real-time Local Noise Filter in 3D Visualization of CT Data").
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the test suite, the smoke check and the
+ * benchmark's CPU-baseline leg may load this file.  It shares no code with the
+ * CUDA path: every filter is evaluated here by literal enumeration of every tap
+ * of its definition, one output voxel at a time, in exact integer arithmetic.
+ *
+ * Conventions (the paper is silent on them; each is a stated reading):
+ *   - volume layout x-fastest: idx = (z*ny + y)*nx + x;
+ *   - clamp-to-edge sampling outside the volume;
+ *   - rounding of an average a/b to the input type is round-half-up,
+ *     floor((2a + b) / (2b));
+ *   - noise gate: a voxel is kept only if its own value P0 >= T and the
+ *     unrounded filter value is >= T (cross-multiplied: sum >= T*count);
+ *     otherwise the output is 0 (the "0, otherwise" branch of Eq. 6 / Eq. 7).
+ *
+ * Filter ids follow the order of the paper's Fig. 5: 0 mean, 1 sigma,
+ * 2 entropy, 3 Okada, 4 the paper's own filter ("ours").
+ */
+#include <stdint.h>
+#include <stddef.h>
+
+typedef struct oracle_params {
+    int32_t filter_id;     /* 0..4 */
+    int32_t radius;        /* r >= 0, kernel size M = 2r+1 (Eq. 3 needs M odd) */
+    int32_t offset;        /* d: diagonal cluster offset, (+-d,+-d,+-d); d=1 is distance sqrt(3) */
+    uint32_t threshold;    /* T: Otsu (Eq. 1) or fixed; 0 disables the gate */
+    uint32_t sigma_band;   /* delta: |P_i - P0| <= delta  (delta = floor(2 sigma), Eq. 5) */
+    int64_t okada_td;      /* T_d: |P0 - P_i| < T_d (Eq. 6) */
+    int64_t entropy_te;    /* T_e (fixed point): keep P0 iff E > T_e (Eq. 7) */
+    const uint32_t *entropy_w; /* w[v] = fixed-point -p_v log2 p_v, one entry per grey level */
+} oracle_params;
+
+typedef struct vol_view {
+    const void *data;
+    int64_t nx, ny, nz;
+    int dtype;             /* 0 = uint8, 1 = uint16 */
+} vol_view;
+
+static int64_t clampi(int64_t v, int64_t lo, int64_t hi)
+{
+    return v < lo ? lo : (v > hi ? hi : v);
+}
+
+/* P(x,y,z) with clamp-to-edge. */
+static uint32_t sample(const vol_view *v, int64_t x, int64_t y, int64_t z)
+{
+    x = clampi(x, 0, v->nx - 1);
+    y = clampi(y, 0, v->ny - 1);
+    z = clampi(z, 0, v->nz - 1);
+    int64_t idx = (z * v->ny + y) * v->nx + x;
+    if (v->dtype == 0)
+        return ((const uint8_t *)v->data)[idx];
+    return ((const uint16_t *)v->data)[idx];
+}
+
+/* round-half-up of a/b, b > 0 */
+static uint32_t round_div(uint64_t a, uint64_t b)
+{
+    return (uint32_t)((2 * a + b) / (2 * b));
+}
+
+/* Eq. 2 without its 1/(3M) factor: the x-, y- and z-line sums of M voxels
+ * through the cluster centre c, with offsets Delta_i = i - (M-1)/2 (Eq. 3).
+ * The centre voxel therefore enters three times. */
+static uint64_t cluster_line_sum(const vol_view *v, int r, int64_t cx, int64_t cy, int64_t cz)
+{
+    int M = 2 * r + 1;
+    uint64_t s = 0;
+    for (int i = 0; i < M; ++i) {
+        int64_t di = i - (M - 1) / 2;
+        s += sample(v, cx + di, cy, cz);
+    }
+    for (int i = 0; i < M; ++i) {
+        int64_t di = i - (M - 1) / 2;
+        s += sample(v, cx, cy + di, cz);
+    }
+    for (int i = 0; i < M; ++i) {
+        int64_t di = i - (M - 1) / 2;
+        s += sample(v, cx, cy, cz + di);
+    }
+    return s;
+}
+
+/* The paper's filter (section "Our Method"): the average cluster S_0 at the
+ * voxel and eight more S_1..S_8 centred at the diagonal offsets (+-d,+-d,+-d);
+ * the voxel is replaced by the mean of the nine cluster averages. */
+static uint32_t filter_ours(const vol_view *v, const oracle_params *p, int64_t x, int64_t y, int64_t z)
+{
+    int r = p->radius, d = p->offset, M = 2 * r + 1;
+    uint64_t U = cluster_line_sum(v, r, x, y, z);           /* S_0 */
+    for (int sz = -1; sz <= 1; sz += 2)
+        for (int sy = -1; sy <= 1; sy += 2)
+            for (int sx = -1; sx <= 1; sx += 2)
+                U += cluster_line_sum(v, r, x + sx * d, y + sy * d, z + sz * d); /* S_1..S_8 */
+    /* mean of nine averages S_k = L_k / (3M): A = U / (27 M) */
+    uint64_t den = 27ull * (uint64_t)M;
+    uint32_t P0 = sample(v, x, y, z);
+    if (P0 < p->threshold || U < den * (uint64_t)p->threshold)
+        return 0;
+    return round_div(U, den);
+}
+
+/* Mean (low-pass) filter, Eq. 4: average over the M^3 cube. */
+static uint32_t filter_mean(const vol_view *v, const oracle_params *p, int64_t x, int64_t y, int64_t z)
+{
+    int r = p->radius, M = 2 * r + 1;
+    uint64_t B = 0;
+    for (int k = 0; k < M; ++k)
+        for (int j = 0; j < M; ++j)
+            for (int i = 0; i < M; ++i)
+                B += sample(v, x + i - r, y + j - r, z + k - r);
+    uint64_t n = (uint64_t)M * M * M;
+    uint32_t P0 = sample(v, x, y, z);
+    if (P0 < p->threshold || B < n * (uint64_t)p->threshold)
+        return 0;
+    return round_div(B, n);
+}
+
+/* Sigma filter, Eq. 5 (reading: band centred on P0, closed interval
+ * |P_i - P0| <= delta, over the M^3 cube; P0 always qualifies). */
+static uint32_t filter_sigma(const vol_view *v, const oracle_params *p, int64_t x, int64_t y, int64_t z)
+{
+    int r = p->radius, M = 2 * r + 1;
+    uint32_t P0 = sample(v, x, y, z);
+    uint64_t s = 0, n = 0;
+    for (int k = 0; k < M; ++k)
+        for (int j = 0; j < M; ++j)
+            for (int i = 0; i < M; ++i) {
+                uint32_t Pi = sample(v, x + i - r, y + j - r, z + k - r);
+                int64_t diff = (int64_t)Pi - (int64_t)P0;
+                if (diff < 0)
+                    diff = -diff;
+                if (diff <= (int64_t)p->sigma_band) {
+                    s += Pi;
+                    n += 1;
+                }
+            }
+    if (P0 < p->threshold || s < n * (uint64_t)p->threshold)
+        return 0;
+    return round_div(s, n);
+}
+
+/* Okada filter, Eq. 6 (reading: the centre and its axis-cross neighbours of
+ * arm r, i.e. the six direct neighbours at M = 3; strict |P0 - P_i| < T_d;
+ * 0 when nothing qualifies). */
+static uint32_t filter_okada(const vol_view *v, const oracle_params *p, int64_t x, int64_t y, int64_t z)
+{
+    int r = p->radius;
+    uint32_t P0 = sample(v, x, y, z);
+    uint64_t s = 0, n = 0;
+    for (int axis = -1; axis < 3; ++axis) {
+        for (int t = -r; t <= r; ++t) {
+            int64_t ox = 0, oy = 0, oz = 0;
+            if (axis == -1) {            /* the centre itself, once */
+                if (t != 0)
+                    continue;
+            } else {
+                if (t == 0)
+                    continue;
+                if (axis == 0) ox = t;
+                if (axis == 1) oy = t;
+                if (axis == 2) oz = t;
+            }
+            uint32_t Pi = sample(v, x + ox, y + oy, z + oz);
+            int64_t diff = (int64_t)P0 - (int64_t)Pi;
+            if (diff < 0)
+                diff = -diff;
+            if (diff < p->okada_td) {
+                s += Pi;
+                n += 1;
+            }
+        }
+    }
+    if (n == 0)
+        return 0;
+    if (P0 < p->threshold || s < n * (uint64_t)p->threshold)
+        return 0;
+    return round_div(s, n);
+}
+
+/* Entropy filter, Eq. 7 (reading: p_i is the global probability of the grey
+ * level of kernel voxel i; the criterion -sum p_i log2 p_i runs over the m =
+ * M^3 cube voxels and is evaluated in the fixed point of the weight table). */
+static uint32_t filter_entropy(const vol_view *v, const oracle_params *p, int64_t x, int64_t y, int64_t z)
+{
+    int r = p->radius, M = 2 * r + 1;
+    uint64_t E = 0;
+    for (int k = 0; k < M; ++k)
+        for (int j = 0; j < M; ++j)
+            for (int i = 0; i < M; ++i)
+                E += p->entropy_w[sample(v, x + i - r, y + j - r, z + k - r)];
+    uint32_t P0 = sample(v, x, y, z);
+    if (P0 < p->threshold)
+        return 0;
+    if ((int64_t)E > p->entropy_te)
+        return P0;
+    return 0;
+}
+
+static uint32_t filter_at(const vol_view *v, const oracle_params *p, int64_t x, int64_t y, int64_t z)
+{
+    switch (p->filter_id) {
+    case 0: return filter_mean(v, p, x, y, z);
+    case 1: return filter_sigma(v, p, x, y, z);
+    case 2: return filter_entropy(v, p, x, y, z);
+    case 3: return filter_okada(v, p, x, y, z);
+    case 4: return filter_ours(v, p, x, y, z);
+    default: return 0;
+    }
+}
+
+/* Filter the box [x0,x1) x [y0,y1) x [z0,z1) of the volume into `out`, which is
+ * laid out x-fastest with dims (x1-x0, y1-y0, z1-z0) and the volume's dtype.
+ * Returns 0 on success, -1 on bad arguments. */
+int oracle_filter_box(const void *vol, int64_t nx, int64_t ny, int64_t nz, int dtype,
+                      const oracle_params *p, void *out,
+                      int64_t x0, int64_t x1, int64_t y0, int64_t y1, int64_t z0, int64_t z1)
+{
+    if (!vol || !p || !out || nx < 1 || ny < 1 || nz < 1 || (dtype != 0 && dtype != 1))
+        return -1;
+    if (x0 < 0 || y0 < 0 || z0 < 0 || x1 > nx || y1 > ny || z1 > nz || x1 < x0 || y1 < y0 || z1 < z0)
+        return -1;
+    if (p->filter_id < 0 || p->filter_id > 4 || p->radius < 0)
+        return -1;
+    vol_view v = {vol, nx, ny, nz, dtype};
+    int64_t bx = x1 - x0, by = y1 - y0;
+    for (int64_t z = z0; z < z1; ++z)
+        for (int64_t y = y0; y < y1; ++y)
+            for (int64_t x = x0; x < x1; ++x) {
+                uint32_t f = filter_at(&v, p, x, y, z);
+                int64_t o = ((z - z0) * by + (y - y0)) * bx + (x - x0);
+                if (dtype == 0)
+                    ((uint8_t *)out)[o] = (uint8_t)f;
+                else
+                    ((uint16_t *)out)[o] = (uint16_t)f;
+            }
+    return 0;
+}
+
+/* Evaluate the filter at npts points given as (x, y, z) triples. */
+int oracle_filter_points(const void *vol, int64_t nx, int64_t ny, int64_t nz, int dtype,
+                         const oracle_params *p, const int64_t *pts, int64_t npts, uint32_t *vals)
+{
+    if (!vol || !p || !pts || !vals || nx < 1 || ny < 1 || nz < 1 || (dtype != 0 && dtype != 1))
+        return -1;
+    vol_view v = {vol, nx, ny, nz, dtype};
+    for (int64_t i = 0; i < npts; ++i) {
+        int64_t x = pts[3 * i], y = pts[3 * i + 1], z = pts[3 * i + 2];
+        if (x < 0 || y < 0 || z < 0 || x >= nx || y >= ny || z >= nz)
+            return -1;
+        vals[i] = filter_at(&v, p, x, y, z);
+    }
+    return 0;
+}
+
+/* Grey-level histogram (counts per value) and the moments S = sum P,
+ * Q = sum P^2, min, max of the whole volume. */
+int oracle_stats(const void *vol, int64_t n, int dtype, uint64_t *hist,
+                 uint64_t *S, uint64_t *Q_lo, uint64_t *Q_hi, uint32_t *minv, uint32_t *maxv)
+{
+    if (!vol || n < 1 || (dtype != 0 && dtype != 1))
+        return -1;
+    int64_t L = dtype == 0 ? 256 : 65536;
+    for (int64_t i = 0; i < L; ++i)
+        hist[i] = 0;
+    unsigned __int128 q = 0;
+    uint64_t s = 0;
+    uint32_t lo = 0xFFFFFFFFu, hi = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        uint32_t P = dtype == 0 ? ((const uint8_t *)vol)[i] : ((const uint16_t *)vol)[i];
+        hist[P] += 1;
+        s += P;
+        q += (unsigned __int128)P * P;
+        if (P < lo) lo = P;
+        if (P > hi) hi = P;
+    }
+    *S = s;
+    *Q_lo = (uint64_t)q;
+    *Q_hi = (uint64_t)(q >> 64);
+    *minv = lo;
+    *maxv = hi;
+    return 0;
+}
