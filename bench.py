@@ -1,0 +1,366 @@
+#!/usr/bin/env python
+"""Benchmark of the local noise filter path (arXiv 1807.03119) on GB300.
+
+Workload (one "step"): the 512^3 uint16 insect-like phantom (12-bit, thin
+shells, tubes, cavities, Gaussian noise sigma 150, 1% salt-and-pepper), all
+five filters at radius 2 (mean, sigma, entropy, Okada, the paper's filter),
+with the image entropy of the input and of each output -- statistics pass,
+device parameter derivation, five filter kernels and the entropy reduction.
+
+Prints ONE JSON line (rank 0).  `value` = filtered output voxels per second
+over the whole job (5 x 512^3 per step and GPU), device-timed with CUDA events
+with the input resident in HBM; `e2e` = the same metric through the
+host-buffer entry point (lnf_filter_multi_host), with the host->device copy
+of the input and the device->host copies of the five outputs and six
+entropies inside the timed region.  `roofline` is for the kernel with the
+largest device time in the step, from CUDA events recorded around each launch
+on the launching stream during the timed region.
+
+`--impl reference` times the CPU oracle (plain C + exact Python integer
+derivations) on bounded samples of the same workload on the host cores.
+"""
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+FILTER_NAMES = ["mean", "sigma", "entropy", "okada", "ours"]
+DIMS = (512, 512, 512)
+RADIUS = 2
+N_VOX = DIMS[0] * DIMS[1] * DIMS[2]
+ES = 2  # uint16
+METRIC = "GVoxel/s and HBM GB/s vs peak at 512^3 uint16 r=2"
+UNIT = "GVoxel/s"
+WORKLOAD = "512x512x512 uint16 insect-like phantom, five filters at r=2, entropy of input and each output"
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return {"hbm_gbs": d.get("hbm_gbs", 6800.0), "sm_max_mhz": d.get("sm_max_mhz", 2070.0),
+                "source": "measured"}
+    return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0, "source": "fallback"}
+
+
+# plain integer ALU peak: 152 SMs x 128 INT32 lanes x max SM clock
+def alu_peak_tops(sm_mhz):
+    return 152 * 128 * sm_mhz * 1e6 / 1e12
+
+
+# algorithmic work per launch of each kernel kind on this workload
+def algorithmic(kind):
+    M3 = (2 * RADIUS + 1) ** 3
+    if kind == "stats":
+        return "hbm", N_VOX * ES
+    if kind.startswith("filter:"):
+        f = kind.split(":")[1]
+        if f == "sigma":   # per tap: subtract, compare, add value, add count
+            return "alu", N_VOX * 4 * M3
+        if f == "okada":   # per tap of the 6r+1 cross: same four operations
+            return "alu", N_VOX * 4 * (6 * RADIUS + 1)
+        return "hbm", N_VOX * ES * 2   # read the input once, write the output once
+    return None, None
+
+
+def source_digest():
+    h = hashlib.sha256()
+    cdir = os.path.join(ROOT, "paper_1807_03119_gb300", "csrc")
+    for fn in sorted(os.listdir(cdir)):
+        if fn.endswith((".cu", ".cuh", ".h")):
+            with open(os.path.join(cdir, fn), "rb") as f:
+                h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(kind):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on
+    the current kernel sources (else None)."""
+    p = os.path.join(ROOT, "profiles", "dram_traffic_512cubed_u16_r2.txt")
+    if not os.path.exists(p):
+        return None
+    dig = source_digest()
+    with open(p) as f:
+        for line in f:
+            parts = line.split()
+            if len(parts) >= 3 and parts[0] == kind and parts[2] == dig:
+                return int(parts[1])
+    return None
+
+
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [s.strip() for s in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        if not rows:
+            return None
+        sm = sorted(float(r[1]) for r in rows if r[1].replace(".", "").isdigit())
+        mx = max(float(r[2]) for r in rows if r[2].replace(".", "").isdigit())
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for i, n in enumerate(names):
+                if r[5 + i].lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(rows)}
+
+
+# ----------------------------------------------------------------------------- CPU oracle
+
+def oracle_step_sample(vol, st, planes, threads):
+    """Time the oracle on a bounded sample of one step: statistics and parameter
+    derivation of the whole volume, then each filter on `planes` z-planes of the
+    full 512x512 cross-section, split over `threads` threads (the C oracle
+    releases the GIL).  Returns (seconds for one full step, description)."""
+    import oracle
+    from concurrent.futures import ThreadPoolExecutor
+    t0 = time.perf_counter()
+    st = oracle.stats(vol)
+    t_stats = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    prm = oracle.derive_params(st, RADIUS)
+    t_params = time.perf_counter() - t0
+    nz, ny, nx = vol.shape
+    z0 = nz // 2 - planes // 2
+    per = max(1, planes // threads)
+    slabs = [(z, min(per, z0 + planes - z)) for z in range(z0, z0 + planes, per)]
+    t_filters = 0.0
+    for f in range(5):
+        t0 = time.perf_counter()
+        with ThreadPoolExecutor(max_workers=threads) as ex:
+            list(ex.map(lambda s: oracle.filter_volume(vol, f, RADIUS, params=prm,
+                                                       roi=(0, 0, s[0], nx, ny, s[1])), slabs))
+        t_filters += (time.perf_counter() - t0) * (nz / planes)
+    total = t_stats + t_params + t_filters
+    desc = (f"oracle (plain C per-voxel enumeration + exact Python parameters): statistics and parameters "
+            f"of the whole 512^3 volume, each filter on {planes} z-planes x 512x512 ({planes * nx * ny} voxels) "
+            f"over {threads} threads, filter time scaled by {nz}/{planes} to the full step")
+    return total, desc
+
+
+def run_reference(args):
+    import numpy as np  # noqa: F401
+    import oracle
+    import phantoms
+    oracle.build()
+    vol = phantoms.P2()
+    threads = os.cpu_count() or 1
+    planes = max(threads, 4)
+    st = None
+    for _ in range(args.warmup):
+        oracle_step_sample(vol, st, planes, threads)
+    times = []
+    desc = ""
+    for _ in range(args.steps):
+        t, desc = oracle_step_sample(vol, st, planes, threads)
+        times.append(t)
+    t = sum(times) / len(times)
+    value = 5 * N_VOX / t / 1e9
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u16", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "radius": RADIUS, "filters": FILTER_NAMES},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": desc},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+# ----------------------------------------------------------------------------- GPU arm
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="lnf", choices=["lnf", "reference"])
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        if rank == 0:
+            run_reference(args)
+        return
+
+    import numpy as np
+    import torch
+    import phantoms
+    import paper_1807_03119_gb300 as lnf
+    from paper_1807_03119_gb300 import builder
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    if rank == 0 or not os.path.exists(lnf.LIB_PATH):
+        builder.build()
+    if world > 1:
+        dist.barrier()
+    lnf.load()
+
+    vol = phantoms.P2(seed=2 + rank)   # each rank filters its own volume (weak scaling)
+    t = torch.from_numpy(vol).cuda()
+    filters = [lnf.MEAN, lnf.SIGMA, lnf.ENTROPY, lnf.OKADA, lnf.OURS]
+    outs = [torch.empty_like(t) for _ in filters]
+    H = torch.zeros(len(filters) + 1, dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream()
+    ctx = lnf.Context()
+
+    def step():
+        ctx.filter_multi(t, filters, RADIUS, outs=outs, H=H)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    ctx.profile(True)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clocks = sampler.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    kern, launches = ctx.profile_read()
+    ctx.profile(False)
+    if world > 1:
+        tt = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+    value = world * 5 * N_VOX / (ms / 1e3) / 1e9
+
+    # end to end through the host-buffer entry point, from pinned host memory
+    pin_in = torch.from_numpy(vol).pin_memory()
+    pin_outs = [torch.empty(vol.shape, dtype=torch.uint16).pin_memory() for _ in filters]
+    in_np = pin_in.numpy()
+    outs_np = [o.numpy() for o in pin_outs]
+    ctx.filter_multi_host(in_np, filters, RADIUS, outs=outs_np)   # staging allocation
+    if world > 1:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        ctx.filter_multi_host(in_np, filters, RADIUS, outs=outs_np)
+    e2e_s = (time.perf_counter() - t0) / args.e2e_steps
+    if world > 1:
+        tt = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e_s = float(tt.item())
+    e2e = {"value": world * 5 * N_VOX / e2e_s / 1e9, "unit": UNIT,
+           "h2d_bytes_per_step": N_VOX * ES, "d2h_bytes_per_step": 5 * N_VOX * ES + 8 * 6,
+           "ms_per_step": e2e_s * 1e3}
+
+    if rank != 0:
+        ctx.close()
+        if world > 1:
+            dist.destroy_process_group()
+        return
+
+    pk = peaks()
+    sm_mhz = pk["sm_max_mhz"]
+    rooflines = {}
+    for kind, (n, tot) in kern.items():
+        bound, work = algorithmic(kind)
+        if bound is None or n == 0:
+            continue
+        avg_s = tot / n / 1e3
+        if bound == "hbm":
+            ach = work / avg_s / 1e9
+            rooflines[kind] = {"bound": "hbm", "achieved": ach, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                               "frac": ach / pk["hbm_gbs"], "avg_ms": tot / n,
+                               "traffic": recorded_traffic(kind)}
+        else:
+            peak = alu_peak_tops(sm_mhz)
+            ach = work / avg_s / 1e12
+            rooflines[kind] = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "Tops/s",
+                               "frac": ach / peak, "avg_ms": tot / n, "traffic": recorded_traffic(kind),
+                               "hbm_gbs": N_VOX * ES * 2 / avg_s / 1e9}
+    dom = max((k for k in rooflines), key=lambda k: kern[k][1]) if rooflines else None
+    roof = dict(rooflines[dom], kernel=dom) if dom else None
+    if roof:
+        roof["peak_source"] = f"{pk['source']} ({'HBM copy' if roof['bound'] == 'hbm' else 'units x max clock'})"
+
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        threads = os.cpu_count() or 1
+        tcpu, desc = oracle_step_sample(vol, None, max(threads, 4), threads)
+        cpu = {"value": 5 * N_VOX / tcpu / 1e9, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": desc}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u16", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "radius": RADIUS, "filters": FILTER_NAMES,
+                   "l2": "inputs larger than L2 (268 MB per volume, 1.6 GB touched per step)",
+                   "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
+        "e2e": e2e, "gpu_launches": launches, "roofline": roof, "rooflines": rooflines,
+        "kernel_ms": {k: v[1] / args.steps for k, v in kern.items()},
+        "hbm_gbs_step": (N_VOX * ES + 5 * N_VOX * ES * 2) / (ms / 1e3) / 1e9,
+        "cpu_baseline": cpu, "clocks": clocks,
+        "entropy": [float(x) for x in H.cpu().numpy()],
+    }
+    print(json.dumps(line))
+    ctx.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

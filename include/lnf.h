@@ -1,0 +1,303 @@
+/*
+ * lnf.h -- C ABI of the GB300 (sm_103a) local noise filter library.
+ *
+ * Implements the data-parallel hot path of arXiv 1807.03119, "Real-time Local
+ * Noise Filter in 3D Visualization of CT Data": the paper's spatially variant
+ * filter (section "Our Method", Eq. 2-3: the mean of nine axis-cross "average
+ * clusters", one at the voxel and eight at the diagonal offsets (+-d,+-d,+-d))
+ * and the four comparison filters of section "3D Spatial Noise Filters" (mean
+ * Eq. 4, sigma Eq. 5, Okada Eq. 6, entropy Eq. 7), all gated by the Otsu
+ * threshold (Eq. 1), applied to every voxel of a CT volume; plus the image
+ * entropy measure the paper uses to compare them (Fig. 4).
+ *
+ * Conventions shared by every entry point
+ *   - A volume is a dense grid of nx*ny*nz grey values, uint8 or uint16,
+ *     laid out x-fastest: idx = (z*ny + y)*nx + x.  dims = {nx, ny, nz}.
+ *   - Kernel size M = 2*radius + 1 (Eq. 3 needs M odd), 0 <= radius <= 8.
+ *   - Outside the volume, samples repeat the border value (clamp to edge).
+ *   - An average a/b is rounded to the input type half-up: floor((2a+b)/(2b)).
+ *   - Noise gate: a voxel is kept only if its own value P0 >= T and the
+ *     unrounded filter value is >= T (compared as sum >= T*count); otherwise
+ *     the output is 0 ("0, otherwise" of Eq. 6 and Eq. 7).  T is the Otsu
+ *     threshold of the whole volume (Eq. 1; ties to the smallest level; a
+ *     single-level volume gives T = that level), a fixed value, or 0.
+ *   - All arithmetic on the filter path is exact integer arithmetic; results
+ *     are bit-exact with the CPU oracle of this repository.
+ *
+ * Memory and streams
+ *   - Unless a name ends in _host, volume pointers are DEVICE pointers owned by
+ *     the caller.  The output must not overlap the input (LNF_EINVAL).
+ *   - The library owns its scratch (histograms, parameter block, weight table,
+ *     staging buffers, resident volumes) and frees it in lnf_destroy.
+ *   - Device work is enqueued on the context's stream (lnf_config.stream, a
+ *     cudaStream_t; NULL = the legacy default stream).  Device-pointer entry
+ *     points return once the work is enqueued; they never synchronise the
+ *     host, except where stated.
+ *   - Errors are returned as lnf_status codes; the library never aborts.
+ *     lnf_last_error() gives a human-readable message for the last failure.
+ *
+ * Threading: a context may be used by one host thread at a time, except for
+ * lnf_submit / lnf_poll / lnf_cancel, which are thread-safe.
+ */
+#ifndef LNF_H
+#define LNF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum lnf_status {
+    LNF_OK = 0,
+    LNF_EINVAL = 1,     /* bad argument */
+    LNF_ENOMEM = 2,     /* device or host allocation failed */
+    LNF_EBUDGET = 3,    /* request can never fit the context's HBM budget */
+    LNF_EPENDING = 4,   /* lnf_poll: request not finished yet */
+    LNF_ECUDA = 5,      /* a CUDA runtime call failed (message in lnf_last_error) */
+    LNF_ETIMEOUT = 6,   /* a bounded device-side wait gave up */
+    LNF_ENOTFOUND = 7,  /* unknown volume id or ticket */
+    LNF_ECANCELLED = 8  /* the request was cancelled before it ran */
+} lnf_status;
+
+typedef enum lnf_dtype { LNF_U8 = 0, LNF_U16 = 1 } lnf_dtype;
+
+/* Filter ids in the order of the paper's Fig. 5. */
+typedef enum lnf_filter_id {
+    LNF_MEAN = 0,     /* Eq. 4: mean of the M^3 cube */
+    LNF_SIGMA = 1,    /* Eq. 5: mean of cube voxels with |P_i - P0| <= k*sigma (global sigma) */
+    LNF_ENTROPY = 2,  /* Eq. 7: P0 if the cube's criterion -sum p_i log2 p_i exceeds T_e, else 0 */
+    LNF_OKADA = 3,    /* Eq. 6: mean of the centre and its axis-cross neighbours with |P0 - P_i| < T_d */
+    LNF_OURS = 4      /* Eq. 2-3: mean of the nine average clusters S_0..S_8 */
+} lnf_filter_id;
+
+typedef enum lnf_threshold_mode {
+    LNF_THRESH_OTSU = 0,   /* Eq. 1 on the whole volume (default, as in the paper's evaluation) */
+    LNF_THRESH_FIXED = 1,  /* threshold_value */
+    LNF_THRESH_NONE = 2    /* T = 0: the gate always passes */
+} lnf_threshold_mode;
+
+#define LNF_MAX_RADIUS 8
+#define LNF_TD_AUTO (-1)        /* okada_td: floor(sigma) + 1, i.e. |P0 - P_i| <= sigma */
+#define LNF_TE_AUTO (-2)        /* entropy_te_q: the expected criterion of a kernel */
+#define LNF_TE_PASS_ALL (-1)    /* entropy_te_q: every voxel passes the entropy test */
+
+/* Context configuration.  lnf_config_default() fills the defaults. */
+typedef struct lnf_config {
+    void *stream;               /* cudaStream_t all work is enqueued on (NULL = default stream) */
+    uint64_t hbm_budget_bytes;  /* serving: device bytes for resident volumes + in-flight outputs
+                                   (0 = 40 GiB) */
+    int32_t max_inflight;       /* serving: requests on the device at once (0 = 64) */
+    int32_t threshold_mode;     /* lnf_threshold_mode */
+    uint32_t threshold_value;   /* T for LNF_THRESH_FIXED */
+    int32_t sigma_k;            /* sigma band half-width in units of sigma (Eq. 5 uses 2) */
+    int64_t okada_td;           /* T_d (>= 0) or LNF_TD_AUTO */
+    int64_t entropy_te_q;       /* T_e in weight units (>= 0), LNF_TE_AUTO or LNF_TE_PASS_ALL */
+    int32_t cluster_offset;     /* d of the diagonal clusters (paper: 1, distance sqrt(3)); 0..8 */
+    int32_t autotune;           /* 1: pick tile shapes by measurement on first use */
+} lnf_config;
+
+/* Parameters derived from a volume's statistics (read back by lnf_get_params). */
+typedef struct lnf_params {
+    uint64_t n_voxels;          /* N */
+    uint64_t sum;               /* S = sum P */
+    uint64_t sum_sq;            /* Q = sum P^2 */
+    uint32_t min_value, max_value;
+    uint32_t threshold;         /* T (Eq. 1 or fixed or 0) */
+    uint32_t sigma_band;        /* delta: |P_i - P0| <= k sigma  <=>  |P_i - P0| <= delta */
+    int64_t okada_td;           /* T_d in use */
+    uint64_t weight_sum;        /* sum_v h[v] w[v]: the expected criterion per voxel, times N */
+    double input_entropy;       /* Shannon entropy of the input histogram, bits */
+} lnf_params;
+
+typedef struct lnf_ctx lnf_ctx;
+
+/* Fill *cfg with defaults: Otsu gate, sigma_k 2, T_d and T_e automatic, d = 1. */
+void lnf_config_default(lnf_config *cfg);
+
+/* Create a context on the current CUDA device.  Allocates the fixed scratch
+ * (about 3 MiB).  Returns LNF_EINVAL for a bad config, LNF_ENOMEM/LNF_ECUDA. */
+lnf_status lnf_create(const lnf_config *cfg, lnf_ctx **out);
+
+/* Wait for the context's work, stop its scheduler and free everything it owns. */
+void lnf_destroy(lnf_ctx *ctx);
+
+/* Change the stream later calls enqueue on (a cudaStream_t). */
+lnf_status lnf_set_stream(lnf_ctx *ctx, void *stream);
+
+/* Message of the last failed call on this context (valid until the next call). */
+const char *lnf_last_error(lnf_ctx *ctx);
+
+/*
+ * Filter one volume: out[v] = filter(in)[v] for every voxel v.
+ * Runs on the device: the statistics pass (histogram, S, Q, min, max), the
+ * parameter derivation (Otsu T, sigma band, T_d, entropy weights), then the
+ * filter.  in/out: device buffers of nx*ny*nz elements of `dtype`, x-fastest.
+ * Enqueued on the context's stream; no host synchronisation.
+ * Errors: LNF_EINVAL (filter_id, radius, dtype, dims < 1, null or overlapping
+ * buffers, more than 2^32 - 1 voxels), LNF_ECUDA.
+ */
+lnf_status lnf_filter_volume(lnf_ctx *ctx, int filter_id, int radius, const void *in, void *out,
+                             const int64_t dims[3], int dtype);
+
+/*
+ * Filter one volume with several filters at the same radius, computing the
+ * statistics once: outs[i] = filter_ids[i](in).  If d_entropy is not NULL it is
+ * a DEVICE array of n+1 doubles that receives the image entropy (Fig. 4) of the
+ * input and of each output, in that order; the output histograms are fused
+ * into the filter kernels.  Enqueued; no host synchronisation.
+ */
+lnf_status lnf_filter_multi(lnf_ctx *ctx, int radius, const void *in, const int64_t dims[3], int dtype,
+                            int n, const int *filter_ids, void *const *outs, double *d_entropy);
+
+/*
+ * The same with HOST buffers (pageable or, faster, pinned): copies `in` to the
+ * device, runs lnf_filter_multi and copies the outputs back into outs[i] and
+ * the n+1 entropies into entropy (host, may be NULL).  Synchronous.
+ */
+lnf_status lnf_filter_multi_host(lnf_ctx *ctx, int radius, const void *in, const int64_t dims[3], int dtype,
+                                 int n, const int *filter_ids, void *const *outs, double *entropy);
+
+/*
+ * Filter a region of interest: out receives roi_dims[0]*roi_dims[1]*roi_dims[2]
+ * voxels, x-fastest, equal to the crop at roi_origin of the whole-volume
+ * result (halo samples come from the whole volume; the statistics are those of
+ * the whole volume; clamping happens only at the volume's own border).
+ */
+lnf_status lnf_filter_roi(lnf_ctx *ctx, int filter_id, int radius, const void *in, const int64_t dims[3],
+                          int dtype, const int64_t roi_origin[3], const int64_t roi_dims[3], void *out);
+
+/*
+ * Image entropy (the paper's Fig. 4 measure) of a volume:
+ * H = -sum_v (c_v/N) log2(c_v/N) over its grey-level histogram, accumulated in
+ * FP64.  vol is a device buffer; *H is a HOST double.  Synchronises the stream.
+ */
+lnf_status lnf_entropy(lnf_ctx *ctx, const void *vol, const int64_t dims[3], int dtype, double *H);
+
+/*
+ * Read back the parameters derived for the last volume analysed on this
+ * context and, if weights is not NULL, its entropy-filter weight table
+ * (256 or 65536 uint32 entries, host memory).  Synchronises the stream.
+ */
+lnf_status lnf_get_params(lnf_ctx *ctx, lnf_params *out, uint32_t *weights);
+
+/* ------------------------------------------------------------------ batched */
+
+/* One filter job of a batch.  All pointers are device pointers. */
+typedef struct lnf_job {
+    const void *in;             /* whole volume */
+    void *out;                  /* roi_dims voxels (whole volume if roi_dims[0] == 0) */
+    int64_t dims[3];
+    int64_t roi_origin[3];
+    int64_t roi_dims[3];        /* {0,0,0}: the whole volume */
+    int32_t dtype;
+    int32_t filter_id;
+    int32_t radius;
+    int32_t reserved;
+    double *d_entropy;          /* optional device double: image entropy of the output */
+} lnf_job;
+
+/*
+ * Run a batch of jobs (different volumes, sizes, dtypes, filters and radii)
+ * as ONE persistent launch over the flattened tile list of all jobs, preceded
+ * by one batched statistics launch and one batched parameter launch; the
+ * three launches are captured once into a CUDA graph and replayed when the
+ * same batch (same pointers and shapes) is run again.  Tile shape and threads
+ * per tile come from the autotuner when lnf_config.autotune is set.
+ * Enqueued; no host synchronisation.
+ */
+lnf_status lnf_filter_batch(lnf_ctx *ctx, const lnf_job *jobs, int n_jobs);
+
+/* ------------------------------------------------------------------ serving */
+
+/* Copy a volume (device or host pointer, see `src_is_host`) into library-owned
+ * device memory charged to the HBM budget, compute its statistics and
+ * parameters once, and return its id.  Synchronous. */
+lnf_status lnf_volume_register(lnf_ctx *ctx, const void *src, int src_is_host, const int64_t dims[3],
+                               int dtype, int *vol_id);
+
+/* Free a resident volume once no request uses it. */
+lnf_status lnf_volume_unregister(lnf_ctx *ctx, int vol_id);
+
+typedef struct lnf_request {
+    int32_t vol_id;
+    int32_t filter_id;
+    int32_t radius;
+    int32_t want_entropy;       /* also compute the output's image entropy */
+    int64_t roi_origin[3];
+    int64_t roi_dims[3];        /* {0,0,0}: the whole volume */
+    void *out_host;             /* HOST buffer for the result (roi voxels), or NULL to keep it
+                                   on the device until lnf_result_copy */
+    double arrival_time;        /* seconds on the lnf_now() clock, recorded for latency */
+} lnf_request;
+
+typedef struct lnf_result {
+    int32_t status;             /* LNF_OK, LNF_EPENDING, LNF_ECANCELLED, ... */
+    int32_t reserved;
+    double entropy;             /* image entropy of the output if requested */
+    double t_admit, t_start, t_finish;  /* seconds on the lnf_now() clock; t_start/t_finish are the
+                                           device start (CUDA events) and completion of the request's wave */
+} lnf_result;
+
+/*
+ * Serving (continuous batching): queue a request against a resident volume
+ * and return a ticket at once.  A scheduler thread admits queued requests as
+ * in-flight slots and HBM budget free up and launches each admitted group as
+ * one batched launch on one of several streams, so that groups overlap on the
+ * device while later requests keep arriving.  LNF_EBUDGET if the request's
+ * output alone exceeds the budget.  Thread-safe.
+ */
+lnf_status lnf_submit(lnf_ctx *ctx, const lnf_request *req, uint64_t *ticket);
+
+/* Status of a ticket: LNF_EPENDING until done, then the request's status and
+ * timings in *res.  A finished ticket may be polled again until released. */
+lnf_status lnf_poll(lnf_ctx *ctx, uint64_t ticket, lnf_result *res);
+
+/* Block until the ticket finishes or timeout_s elapses (LNF_ETIMEOUT). */
+lnf_status lnf_wait(lnf_ctx *ctx, uint64_t ticket, double timeout_s, lnf_result *res);
+
+/* Copy a finished request's device result to host memory (when out_host was NULL). */
+lnf_status lnf_result_copy(lnf_ctx *ctx, uint64_t ticket, void *dst_host, size_t bytes);
+
+/* Cancel a request that has not been admitted yet (LNF_EPENDING if it has). */
+lnf_status lnf_cancel(lnf_ctx *ctx, uint64_t ticket);
+
+/* Forget a finished ticket and free its device result. */
+lnf_status lnf_release(lnf_ctx *ctx, uint64_t ticket);
+
+/* The library's clock in seconds (CLOCK_MONOTONIC; Python's time.monotonic()),
+ * the clock of lnf_request.arrival_time and of the lnf_result timings. */
+double lnf_now(void);
+
+/* Serving counters: bytes of the budget in use and requests queued / in flight. */
+lnf_status lnf_serving_stats(lnf_ctx *ctx, uint64_t *budget_used, int *queued, int *inflight);
+
+/* ------------------------------------------------------------------ profiling */
+
+/* Per-kind device time of the launches made while profiling was on. */
+typedef struct lnf_kernel_time {
+    char name[24];              /* "stats", "params", "filter:ours", "entropy", ... */
+    int32_t launches;           /* kernels of this kind launched */
+    int32_t reserved;
+    double total_ms;            /* sum of CUDA-event durations on the launching stream */
+} lnf_kernel_time;
+
+/* Turn profiling on (1) or off (0) and clear its records.  While on, every
+ * kernel launch of the plain path is bracketed by CUDA events recorded on the
+ * stream it is launched on, and every kernel launch is counted. */
+lnf_status lnf_profile_enable(lnf_ctx *ctx, int on);
+
+/* Synchronise, then return up to `max` per-kind records in `out` (*n set to
+ * the number of kinds) and the total number of kernels launched since
+ * profiling was enabled in *launches. */
+lnf_status lnf_profile_read(lnf_ctx *ctx, lnf_kernel_time *out, int max, int *n, int64_t *launches);
+
+/* Library version string. */
+const char *lnf_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LNF_H */

@@ -1,0 +1,664 @@
+// Host side of liblnf: the C ABI of include/lnf.h (plain, multi-filter, ROI,
+// entropy and batched entry points).  The serving loop lives in serve.cu.
+//
+// Every step of the filter path runs on the device: statistics (stats.cu),
+// parameter derivation (stats.cu, one CTA), filters (filter.cu, fast.cu) and
+// the entropy reduction.  The host only validates arguments, encodes TMA
+// descriptors, packs job descriptors into kernel parameters and enqueues.
+#include "lnf_ctx.h"
+
+#include <algorithm>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+
+// ------------------------------------------------------------------ errors
+
+lnf_status lnf_fail(lnf_ctx *ctx, lnf_status s, const char *fmt, ...)
+{
+    if (ctx) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof buf, fmt, ap);
+        va_end(ap);
+        std::lock_guard<std::mutex> g(ctx->err_mu);
+        ctx->err = buf;
+    }
+    return s;
+}
+
+#define CK(call)                                                                                  \
+    do {                                                                                          \
+        cudaError_t e_ = (call);                                                                  \
+        if (e_ != cudaSuccess)                                                                    \
+            return lnf_fail(ctx, LNF_ECUDA, "%s: %s", #call, cudaGetErrorString(e_));             \
+    } while (0)
+
+// ------------------------------------------------------------------ validation
+
+lnf_status lnf_check_volume(lnf_ctx *ctx, const void *p, const int64_t dims[3], int dtype)
+{
+    if (!p)
+        return lnf_fail(ctx, LNF_EINVAL, "null volume pointer");
+    if (!dims)
+        return lnf_fail(ctx, LNF_EINVAL, "null dims");
+    if (dtype != LNF_U8 && dtype != LNF_U16)
+        return lnf_fail(ctx, LNF_EINVAL, "dtype must be LNF_U8 or LNF_U16 (got %d)", dtype);
+    for (int i = 0; i < 3; ++i)
+        if (dims[i] < 1 || dims[i] > (1ll << 30))
+            return lnf_fail(ctx, LNF_EINVAL, "dims[%d] = %lld out of range [1, 2^30]", i, (long long)dims[i]);
+    const unsigned __int128 n = (unsigned __int128)dims[0] * dims[1] * dims[2];
+    if (n >= ((unsigned __int128)1 << 32))
+        return lnf_fail(ctx, LNF_EINVAL, "volume has %llu voxels; the limit is 2^32 - 1",
+                        (unsigned long long)n);
+    return LNF_OK;
+}
+
+static lnf_status check_filter(lnf_ctx *ctx, int filter_id, int radius)
+{
+    if (filter_id < LNF_MEAN || filter_id > LNF_OURS)
+        return lnf_fail(ctx, LNF_EINVAL, "filter_id %d not in 0..4", filter_id);
+    if (radius < 0 || radius > LNF_MAX_RADIUS)
+        return lnf_fail(ctx, LNF_EINVAL, "radius %d not in 0..%d", radius, LNF_MAX_RADIUS);
+    return LNF_OK;
+}
+
+static bool overlaps(const void *a, size_t na, const void *b, size_t nb)
+{
+    const char *pa = static_cast<const char *>(a), *pb = static_cast<const char *>(b);
+    return pa < pb + nb && pb < pa + na;
+}
+
+static size_t esize(int dtype) { return dtype == LNF_U8 ? 1 : 2; }
+
+static u64 nvox(const int64_t d[3]) { return (u64)d[0] * (u64)d[1] * (u64)d[2]; }
+
+// ------------------------------------------------------------------ config
+
+extern "C" void lnf_config_default(lnf_config *cfg)
+{
+    if (!cfg)
+        return;
+    std::memset(cfg, 0, sizeof *cfg);
+    cfg->stream = nullptr;
+    cfg->hbm_budget_bytes = 40ull << 30;
+    cfg->max_inflight = 64;
+    cfg->threshold_mode = LNF_THRESH_OTSU;
+    cfg->threshold_value = 0;
+    cfg->sigma_k = 2;
+    cfg->okada_td = LNF_TD_AUTO;
+    cfg->entropy_te_q = LNF_TE_AUTO;
+    cfg->cluster_offset = 1;
+    cfg->autotune = 0;
+}
+
+ParamCfg lnf_param_cfg(const lnf_config &c)
+{
+    ParamCfg p;
+    std::memset(&p, 0, sizeof p);
+    p.threshold_mode = c.threshold_mode;
+    p.threshold_value = c.threshold_value;
+    p.sigma_k = c.sigma_k;
+    p.okada_td = c.okada_td;
+    p.entropy_te = c.entropy_te_q;
+    return p;
+}
+
+static lnf_status alloc_scratch(lnf_ctx *ctx, VolScratch &vs)
+{
+    CK(cudaMalloc(&vs.hist, sizeof(u64) * LNF_LEVELS_U16));
+    CK(cudaMalloc(&vs.st, sizeof(DevStats)));
+    CK(cudaMalloc(&vs.prm, sizeof(DevParams)));
+    CK(cudaMalloc(&vs.lut, sizeof(u32) * LNF_LEVELS_U16));
+    CK(cudaMemset(vs.prm, 0, sizeof(DevParams)));
+    return LNF_OK;
+}
+
+static void free_scratch(VolScratch &vs)
+{
+    cudaFree(vs.hist);
+    cudaFree(vs.st);
+    cudaFree(vs.prm);
+    cudaFree(vs.lut);
+    vs = VolScratch{};
+}
+
+lnf_status lnf_scratch_pool(lnf_ctx *ctx, size_t n)
+{
+    while (ctx->pool.size() < n) {
+        VolScratch vs{};
+        lnf_status s = alloc_scratch(ctx, vs);
+        if (s != LNF_OK)
+            return s;
+        ctx->pool.push_back(vs);
+    }
+    return LNF_OK;
+}
+
+static void prof_clear(lnf_ctx *ctx);
+
+extern "C" lnf_status lnf_create(const lnf_config *cfg_in, lnf_ctx **out)
+{
+    if (!out)
+        return LNF_EINVAL;
+    *out = nullptr;
+    lnf_config cfg;
+    if (cfg_in)
+        cfg = *cfg_in;
+    else
+        lnf_config_default(&cfg);
+    if (cfg.threshold_mode < 0 || cfg.threshold_mode > 2 || cfg.sigma_k < 0 || cfg.sigma_k > 255 ||
+        cfg.cluster_offset < 0 || cfg.cluster_offset > 8 || cfg.okada_td < LNF_TD_AUTO ||
+        cfg.entropy_te_q < LNF_TE_AUTO)
+        return LNF_EINVAL;
+    if (cfg.hbm_budget_bytes == 0)
+        cfg.hbm_budget_bytes = 40ull << 30;
+    if (cfg.max_inflight <= 0)
+        cfg.max_inflight = 64;
+    lnf_ctx *ctx = new (std::nothrow) lnf_ctx();
+    if (!ctx)
+        return LNF_ENOMEM;
+    ctx->cfg = cfg;
+    ctx->stream = static_cast<cudaStream_t>(cfg.stream);
+    lnf_status s = LNF_OK;
+    do {
+        if (cudaGetDevice(&ctx->device) != cudaSuccess) {
+            s = LNF_ECUDA;
+            break;
+        }
+        cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, ctx->device);
+        if (ctx->num_sms < 1)
+            ctx->num_sms = 1;
+        if ((s = alloc_scratch(ctx, ctx->vs)) != LNF_OK)
+            break;
+        if (cudaMalloc(&ctx->out_hist, sizeof(u64) * LNF_LEVELS_U16 * LNF_MAX_PACK) != cudaSuccess ||
+            cudaMalloc(&ctx->d_H, sizeof(double) * (LNF_MAX_PACK + 1)) != cudaSuccess ||
+            cudaMalloc(&ctx->d_err, sizeof(u32)) != cudaSuccess ||
+            cudaMalloc(&ctx->d_counter, sizeof(u32) * 16) != cudaSuccess) {
+            s = LNF_ENOMEM;
+            break;
+        }
+        cudaMemset(ctx->d_err, 0, sizeof(u32));
+        cudaMemset(ctx->d_counter, 0, sizeof(u32) * 16);
+        void *fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            ctx->encode = reinterpret_cast<PFN_encodeTiled>(fn);
+        // test hooks: force the plain-load path / the generic kernel
+        const char *ev = getenv("LNF_FORCE_PLAIN");
+        ctx->no_tma = ev && ev[0] == '1';
+        ev = getenv("LNF_FORCE_GENERIC");
+        ctx->no_fast = ev && ev[0] == '1';
+        if (cudaDeviceSynchronize() != cudaSuccess)
+            s = LNF_ECUDA;
+    } while (0);
+    if (s != LNF_OK) {
+        lnf_destroy(ctx);
+        return s;
+    }
+    *out = ctx;
+    return LNF_OK;
+}
+
+extern "C" void lnf_destroy(lnf_ctx *ctx)
+{
+    if (!ctx)
+        return;
+    lnf_serve_shutdown(ctx);
+    cudaStreamSynchronize(ctx->stream);
+    lnf_batch_cache_clear(ctx);
+    free_scratch(ctx->vs);
+    for (auto &vs : ctx->pool)
+        free_scratch(vs);
+    prof_clear(ctx);
+    for (cudaEvent_t e : ctx->prof_free)
+        cudaEventDestroy(e);
+    cudaFree(ctx->out_hist);
+    cudaFree(ctx->d_H);
+    cudaFree(ctx->d_err);
+    cudaFree(ctx->d_counter);
+    cudaFree(ctx->st_in);
+    for (void *p : ctx->st_out)
+        cudaFree(p);
+    delete ctx;
+}
+
+extern "C" lnf_status lnf_set_stream(lnf_ctx *ctx, void *stream)
+{
+    if (!ctx)
+        return LNF_EINVAL;
+    ctx->stream = static_cast<cudaStream_t>(stream);
+    ctx->cfg.stream = stream;
+    return LNF_OK;
+}
+
+extern "C" const char *lnf_last_error(lnf_ctx *ctx)
+{
+    if (!ctx)
+        return "null context";
+    std::lock_guard<std::mutex> g(ctx->err_mu);
+    ctx->err_copy = ctx->err;
+    return ctx->err_copy.c_str();
+}
+
+extern "C" const char *lnf_version(void) { return "lnf 0.1 (sm_103a)"; }
+
+// ------------------------------------------------------------------ profiling
+
+static cudaEvent_t prof_event(lnf_ctx *ctx)
+{
+    if (!ctx->prof_free.empty()) {
+        cudaEvent_t e = ctx->prof_free.back();
+        ctx->prof_free.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+int lnf_prof_begin(lnf_ctx *ctx, cudaStream_t st)
+{
+    if (!ctx->prof)
+        return -1;
+    lnf_ctx::ProfRec r;
+    r.a = prof_event(ctx);
+    r.b = prof_event(ctx);
+    cudaEventRecord(r.a, st);
+    ctx->prof_recs.push_back(r);
+    return (int)ctx->prof_recs.size() - 1;
+}
+
+void lnf_prof_end(lnf_ctx *ctx, int rec, const char *name, cudaStream_t st, int count)
+{
+    ctx->prof_launches += count;
+    if (rec < 0)
+        return;
+    ctx->prof_recs[rec].name = name;
+    cudaEventRecord(ctx->prof_recs[rec].b, st);
+}
+
+static void prof_clear(lnf_ctx *ctx)
+{
+    for (auto &r : ctx->prof_recs) {
+        ctx->prof_free.push_back(r.a);
+        ctx->prof_free.push_back(r.b);
+    }
+    ctx->prof_recs.clear();
+    ctx->prof_launches = 0;
+}
+
+extern "C" lnf_status lnf_profile_enable(lnf_ctx *ctx, int on)
+{
+    if (!ctx)
+        return LNF_EINVAL;
+    cudaStreamSynchronize(ctx->stream);
+    prof_clear(ctx);
+    ctx->prof = on != 0;
+    return LNF_OK;
+}
+
+extern "C" lnf_status lnf_profile_read(lnf_ctx *ctx, lnf_kernel_time *out, int max, int *n, int64_t *launches)
+{
+    if (!ctx || (max > 0 && !out))
+        return LNF_EINVAL;
+    for (auto &r : ctx->prof_recs)
+        CK(cudaEventSynchronize(r.b));
+    std::vector<lnf_kernel_time> kinds;
+    for (auto &r : ctx->prof_recs) {
+        float ms = 0;
+        CK(cudaEventElapsedTime(&ms, r.a, r.b));
+        auto it = std::find_if(kinds.begin(), kinds.end(),
+                               [&](const lnf_kernel_time &k) { return r.name == k.name; });
+        if (it == kinds.end()) {
+            lnf_kernel_time k;
+            std::memset(&k, 0, sizeof k);
+            std::snprintf(k.name, sizeof k.name, "%s", r.name.c_str());
+            kinds.push_back(k);
+            it = kinds.end() - 1;
+        }
+        it->launches += 1;
+        it->total_ms += ms;
+    }
+    for (int i = 0; i < (int)kinds.size() && i < max; ++i)
+        out[i] = kinds[i];
+    if (n)
+        *n = (int)kinds.size();
+    if (launches)
+        *launches = ctx->prof_launches;
+    return LNF_OK;
+}
+
+static const char *filter_name(int f)
+{
+    static const char *names[] = {"filter:mean", "filter:sigma", "filter:entropy", "filter:okada", "filter:ours"};
+    return f >= 0 && f <= 4 ? names[f] : "filter:?";
+}
+
+// ------------------------------------------------------------------ device steps
+
+lnf_status lnf_analyze(lnf_ctx *ctx, const void *in, const int64_t dims[3], int dtype, VolScratch &vs,
+                       cudaStream_t stream)
+{
+    const u32 levels = dtype == LNF_U8 ? LNF_LEVELS_U8 : LNF_LEVELS_U16;
+    const u64 n = nvox(dims);
+    int rec = lnf_prof_begin(ctx, stream);
+    CK(lnf_launch_stats_init(vs.hist, levels, vs.st, n, stream));
+    lnf_prof_end(ctx, rec, "stats_init", stream, 1);
+    rec = lnf_prof_begin(ctx, stream);
+    CK(lnf_launch_stats(in, n, dtype, vs.hist, vs.st, ctx->num_sms, stream));
+    lnf_prof_end(ctx, rec, "stats", stream, 1);
+    rec = lnf_prof_begin(ctx, stream);
+    CK(lnf_launch_params(vs.hist, vs.st, lnf_param_cfg(ctx->cfg), vs.prm, vs.lut, stream));
+    lnf_prof_end(ctx, rec, "params", stream, 1);
+    return LNF_OK;
+}
+
+// Fill job `idx` of the pack; encodes a TMA map when the volume allows it.
+lnf_status lnf_make_job(lnf_ctx *ctx, FilterPack &pk, int idx, int filter, int radius, const void *in, void *out,
+                        const int64_t dims[3], int dtype, const int64_t *roi_o, const int64_t *roi_d,
+                        const VolScratch &vs, u64 *out_hist)
+{
+    FilterJob &j = pk.jobs[idx];
+    std::memset(&j, 0, sizeof j);
+    j.in = in;
+    j.out = out;
+    j.nx = (int)dims[0];
+    j.ny = (int)dims[1];
+    j.nz = (int)dims[2];
+    if (roi_d && roi_d[0] > 0) {
+        j.ox = (int)roi_o[0];
+        j.oy = (int)roi_o[1];
+        j.oz = (int)roi_o[2];
+        j.bx = (int)roi_d[0];
+        j.by = (int)roi_d[1];
+        j.bz = (int)roi_d[2];
+    } else {
+        j.bx = j.nx;
+        j.by = j.ny;
+        j.bz = j.nz;
+    }
+    j.dtype = dtype;
+    j.filter = filter;
+    j.radius = radius;
+    j.offset = ctx->cfg.cluster_offset;
+    j.prm = vs.prm;
+    j.lut = vs.lut;
+    j.out_hist = out_hist;
+    j.tmap_idx = -1;
+    lnf_filter_decompose(j, ctx->zchunk);
+    const size_t es = esize(dtype);
+    if (ctx->encode && !ctx->no_tma && (reinterpret_cast<uintptr_t>(in) & 15) == 0 && (dims[0] * es) % 16 == 0) {
+        unsigned bw = 0, bh = 0;
+        lnf_filter_box(filter, radius, ctx->cfg.cluster_offset, dtype, &bw, &bh);
+        if (bw <= 256 && bh <= 256) {
+            cuuint64_t gdim[3] = {(cuuint64_t)dims[0], (cuuint64_t)dims[1], (cuuint64_t)dims[2]};
+            cuuint64_t gstr[2] = {(cuuint64_t)(dims[0] * es), (cuuint64_t)(dims[0] * dims[1] * es)};
+            cuuint32_t box[3] = {bw, bh, 1};
+            cuuint32_t estr[3] = {1, 1, 1};
+            CUresult r = ctx->encode(&pk.tmaps[idx], dtype == LNF_U8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8
+                                                                     : CU_TENSOR_MAP_DATA_TYPE_UINT16,
+                                     3, const_cast<void *>(in), gdim, gstr, box, estr,
+                                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+            if (r == CUDA_SUCCESS)
+                j.tmap_idx = idx;
+        }
+    }
+    return LNF_OK;
+}
+
+// Assign item ranges and launch the generic kernel over the pack.
+lnf_status lnf_run_pack(lnf_ctx *ctx, FilterPack &pk, int persistent, cudaStream_t stream)
+{
+    return lnf_run_pack_counter(ctx, pk, persistent, stream, ctx->d_counter);
+}
+
+lnf_status lnf_run_pack_counter(lnf_ctx *ctx, FilterPack &pk, int persistent, cudaStream_t stream, u32 *counter)
+{
+    int items = 0;
+    size_t smem = 0;
+    for (int i = 0; i < pk.n_jobs; ++i) {
+        pk.jobs[i].item_begin = items;
+        items += lnf_filter_items(pk.jobs[i]);
+        smem = std::max(smem, lnf_filter_smem_bytes(pk.jobs[i].filter, pk.jobs[i].radius, pk.jobs[i].offset,
+                                                    pk.jobs[i].dtype));
+    }
+    pk.total_items = items;
+    if (items == 0)
+        return LNF_OK;
+    const int occ = lnf_filter_occupancy(smem);
+    int grid = std::min(items, ctx->num_sms * occ);
+    if (persistent)
+        CK(cudaMemsetAsync(counter, 0, sizeof(u32), stream));
+    CK(lnf_filter_run(pk, smem, grid, persistent, counter, ctx->d_err, stream));
+    return LNF_OK;
+}
+
+// Run one filter job on an analysed volume, through the fastest kernel that covers it.
+lnf_status lnf_run_one(lnf_ctx *ctx, int filter, int radius, const void *in, void *out, const int64_t dims[3],
+                       int dtype, const int64_t *roi_o, const int64_t *roi_d, const VolScratch &vs,
+                       u64 *out_hist, cudaStream_t stream)
+{
+    FilterPack &pk = ctx->pack;
+    pk.n_jobs = 1;
+    lnf_status s = lnf_make_job(ctx, pk, 0, filter, radius, in, out, dims, dtype, roi_o, roi_d, vs, out_hist);
+    if (s != LNF_OK)
+        return s;
+    const int rec = lnf_prof_begin(ctx, stream);
+    if (!ctx->no_fast) {
+        int handled = 0;
+        s = lnf_fast_dispatch(ctx, pk.jobs[0], pk.jobs[0].tmap_idx >= 0 ? &pk.tmaps[0] : nullptr, stream, &handled);
+        if (s != LNF_OK || handled) {
+            lnf_prof_end(ctx, rec, filter_name(filter), stream, 1);
+            return s;
+        }
+    }
+    s = lnf_run_pack(ctx, pk, 0, stream);
+    lnf_prof_end(ctx, rec, filter_name(filter), stream, 1);
+    return s;
+}
+
+// ------------------------------------------------------------------ entry points
+
+extern "C" lnf_status lnf_filter_volume(lnf_ctx *ctx, int filter_id, int radius, const void *in, void *out,
+                                        const int64_t dims[3], int dtype)
+{
+    if (!ctx)
+        return LNF_EINVAL;
+    lnf_status s;
+    if ((s = check_filter(ctx, filter_id, radius)) != LNF_OK)
+        return s;
+    if ((s = lnf_check_volume(ctx, in, dims, dtype)) != LNF_OK)
+        return s;
+    if (!out)
+        return lnf_fail(ctx, LNF_EINVAL, "null output pointer");
+    const size_t bytes = nvox(dims) * esize(dtype);
+    if (overlaps(in, bytes, out, bytes))
+        return lnf_fail(ctx, LNF_EINVAL, "input and output overlap");
+    if ((s = lnf_analyze(ctx, in, dims, dtype, ctx->vs, ctx->stream)) != LNF_OK)
+        return s;
+    return lnf_run_one(ctx, filter_id, radius, in, out, dims, dtype, nullptr, nullptr, ctx->vs, nullptr,
+                       ctx->stream);
+}
+
+extern "C" lnf_status lnf_filter_roi(lnf_ctx *ctx, int filter_id, int radius, const void *in,
+                                     const int64_t dims[3], int dtype, const int64_t roi_origin[3],
+                                     const int64_t roi_dims[3], void *out)
+{
+    if (!ctx)
+        return LNF_EINVAL;
+    lnf_status s;
+    if ((s = check_filter(ctx, filter_id, radius)) != LNF_OK)
+        return s;
+    if ((s = lnf_check_volume(ctx, in, dims, dtype)) != LNF_OK)
+        return s;
+    if (!out || !roi_origin || !roi_dims)
+        return lnf_fail(ctx, LNF_EINVAL, "null ROI argument");
+    for (int i = 0; i < 3; ++i)
+        if (roi_dims[i] < 1 || roi_origin[i] < 0 || roi_origin[i] + roi_dims[i] > dims[i])
+            return lnf_fail(ctx, LNF_EINVAL, "ROI axis %d [%lld, +%lld) outside the volume", i,
+                            (long long)roi_origin[i], (long long)roi_dims[i]);
+    const size_t es = esize(dtype);
+    if (overlaps(in, nvox(dims) * es, out, nvox(roi_dims) * es))
+        return lnf_fail(ctx, LNF_EINVAL, "input and output overlap");
+    if ((s = lnf_analyze(ctx, in, dims, dtype, ctx->vs, ctx->stream)) != LNF_OK)
+        return s;
+    return lnf_run_one(ctx, filter_id, radius, in, out, dims, dtype, roi_origin, roi_dims, ctx->vs, nullptr,
+                       ctx->stream);
+}
+
+extern "C" lnf_status lnf_filter_multi(lnf_ctx *ctx, int radius, const void *in, const int64_t dims[3], int dtype,
+                                       int n, const int *filter_ids, void *const *outs, double *d_entropy)
+{
+    if (!ctx)
+        return LNF_EINVAL;
+    lnf_status s;
+    if ((s = lnf_check_volume(ctx, in, dims, dtype)) != LNF_OK)
+        return s;
+    if (n < 0 || n > LNF_MAX_PACK || (n > 0 && (!filter_ids || !outs)))
+        return lnf_fail(ctx, LNF_EINVAL, "n = %d filters (1..%d) with non-null ids and outputs", n, LNF_MAX_PACK);
+    const size_t bytes = nvox(dims) * esize(dtype);
+    for (int i = 0; i < n; ++i) {
+        if ((s = check_filter(ctx, filter_ids[i], radius)) != LNF_OK)
+            return s;
+        if (!outs[i] || overlaps(in, bytes, outs[i], bytes))
+            return lnf_fail(ctx, LNF_EINVAL, "output %d is null or overlaps the input", i);
+    }
+    cudaStream_t st = ctx->stream;
+    if ((s = lnf_analyze(ctx, in, dims, dtype, ctx->vs, st)) != LNF_OK)
+        return s;
+    const u32 levels = dtype == LNF_U8 ? LNF_LEVELS_U8 : LNF_LEVELS_U16;
+    if (d_entropy && n > 0) {
+        const int rec = lnf_prof_begin(ctx, st);
+        CK(lnf_launch_zero(ctx->out_hist, (u64)LNF_LEVELS_U16 * n, st));
+        lnf_prof_end(ctx, rec, "zero_hist", st, 1);
+    }
+    for (int i = 0; i < n; ++i) {
+        u64 *oh = d_entropy ? ctx->out_hist + (size_t)i * LNF_LEVELS_U16 : nullptr;
+        if ((s = lnf_run_one(ctx, filter_ids[i], radius, in, outs[i], dims, dtype, nullptr, nullptr, ctx->vs, oh,
+                             st)) != LNF_OK)
+            return s;
+    }
+    if (d_entropy) {
+        CK(cudaMemcpyAsync(d_entropy, &ctx->vs.prm->H_in, sizeof(double), cudaMemcpyDeviceToDevice, st));
+        EntropyPack ep;
+        std::memset(&ep, 0, sizeof ep);
+        ep.count = n;
+        for (int i = 0; i < n; ++i) {
+            ep.hist[i] = ctx->out_hist + (size_t)i * LNF_LEVELS_U16;
+            ep.n[i] = nvox(dims);
+            ep.H[i] = d_entropy + 1 + i;
+            ep.levels[i] = levels;
+        }
+        const int rec = lnf_prof_begin(ctx, st);
+        CK(lnf_launch_entropy_pack(ep, st));
+        lnf_prof_end(ctx, rec, "entropy", st, 1);
+    }
+    return LNF_OK;
+}
+
+static lnf_status ensure_stage(lnf_ctx *ctx, void **p, size_t *cap, size_t bytes)
+{
+    if (*cap >= bytes)
+        return LNF_OK;
+    if (*p)
+        cudaFree(*p);
+    *p = nullptr;
+    *cap = 0;
+    CK(cudaMalloc(p, bytes));
+    *cap = bytes;
+    return LNF_OK;
+}
+
+extern "C" lnf_status lnf_filter_multi_host(lnf_ctx *ctx, int radius, const void *in, const int64_t dims[3],
+                                            int dtype, int n, const int *filter_ids, void *const *outs,
+                                            double *entropy)
+{
+    if (!ctx)
+        return LNF_EINVAL;
+    lnf_status s;
+    if ((s = lnf_check_volume(ctx, in, dims, dtype)) != LNF_OK)
+        return s;
+    if (n < 0 || n > LNF_MAX_PACK || (n > 0 && (!filter_ids || !outs)))
+        return lnf_fail(ctx, LNF_EINVAL, "bad filter list");
+    for (int i = 0; i < n; ++i)
+        if (!outs[i])
+            return lnf_fail(ctx, LNF_EINVAL, "null host output %d", i);
+    const size_t bytes = nvox(dims) * esize(dtype);
+    if ((s = ensure_stage(ctx, &ctx->st_in, &ctx->st_in_cap, bytes)) != LNF_OK)
+        return s;
+    if (ctx->st_out.size() < (size_t)n) {
+        ctx->st_out.resize(n, nullptr);
+        ctx->st_out_cap.resize(n, 0);
+    }
+    for (int i = 0; i < n; ++i)
+        if ((s = ensure_stage(ctx, &ctx->st_out[i], &ctx->st_out_cap[i], bytes)) != LNF_OK)
+            return s;
+    cudaStream_t st = ctx->stream;
+    CK(cudaMemcpyAsync(ctx->st_in, in, bytes, cudaMemcpyHostToDevice, st));
+    if ((s = lnf_filter_multi(ctx, radius, ctx->st_in, dims, dtype, n, filter_ids, ctx->st_out.data(),
+                              ctx->d_H)) != LNF_OK)
+        return s;
+    for (int i = 0; i < n; ++i)
+        CK(cudaMemcpyAsync(outs[i], ctx->st_out[i], bytes, cudaMemcpyDeviceToHost, st));
+    double hbuf[LNF_MAX_PACK + 1];
+    CK(cudaMemcpyAsync(hbuf, ctx->d_H, sizeof(double) * (n + 1), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (entropy)
+        std::memcpy(entropy, hbuf, sizeof(double) * (n + 1));
+    return LNF_OK;
+}
+
+extern "C" lnf_status lnf_entropy(lnf_ctx *ctx, const void *vol, const int64_t dims[3], int dtype, double *H)
+{
+    if (!ctx)
+        return LNF_EINVAL;
+    lnf_status s;
+    if ((s = lnf_check_volume(ctx, vol, dims, dtype)) != LNF_OK)
+        return s;
+    if (!H)
+        return lnf_fail(ctx, LNF_EINVAL, "null H");
+    cudaStream_t st = ctx->stream;
+    const u32 levels = dtype == LNF_U8 ? LNF_LEVELS_U8 : LNF_LEVELS_U16;
+    const u64 n = nvox(dims);
+    CK(lnf_launch_stats_init(ctx->vs.hist, levels, ctx->vs.st, n, st));
+    CK(lnf_launch_stats(vol, n, dtype, ctx->vs.hist, ctx->vs.st, ctx->num_sms, st));
+    CK(lnf_launch_entropy(ctx->vs.hist, levels, n, ctx->d_H, st));
+    CK(cudaMemcpyAsync(H, ctx->d_H, sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    return LNF_OK;
+}
+
+extern "C" lnf_status lnf_get_params(lnf_ctx *ctx, lnf_params *out, uint32_t *weights)
+{
+    if (!ctx || !out)
+        return LNF_EINVAL;
+    DevParams p;
+    CK(cudaMemcpyAsync(&p, ctx->vs.prm, sizeof p, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    if (!p.valid)
+        return lnf_fail(ctx, LNF_EINVAL, "no volume has been analysed on this context yet");
+    if (weights) {
+        CK(cudaMemcpyAsync(weights, ctx->vs.lut, sizeof(u32) * p.levels, cudaMemcpyDeviceToHost, ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
+    }
+    out->n_voxels = p.N;
+    out->sum = p.S;
+    out->sum_sq = p.Q;
+    out->min_value = p.minv;
+    out->max_value = p.maxv;
+    out->threshold = p.T;
+    out->sigma_band = p.delta;
+    out->okada_td = p.td;
+    out->weight_sum = p.hw_sum;
+    out->input_entropy = p.H_in;
+    u32 err = 0;
+    if (cudaMemcpy(&err, ctx->d_err, sizeof err, cudaMemcpyDeviceToHost) == cudaSuccess && err)
+        return lnf_fail(ctx, LNF_ETIMEOUT, "a bounded device wait gave up (code %u)", err);
+    return LNF_OK;
+}

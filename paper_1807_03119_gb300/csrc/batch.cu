@@ -1,0 +1,248 @@
+// Batched delivery: many volumes / ROIs / filters / radii in ONE persistent
+// launch over the flattened tile list of all jobs, preceded by one batched
+// statistics launch and one batched parameter launch, captured once into a
+// CUDA graph and replayed for the same batch.  An autotuner picks the z chunk
+// of a work item (the tile's depth, which sets the halo re-read share and the
+// load balance) by timing the candidates on the first batch it sees.
+#include "lnf_ctx.h"
+
+#include <algorithm>
+#include <cstring>
+#include <map>
+#include <memory>
+
+#define CK(call)                                                                                  \
+    do {                                                                                          \
+        cudaError_t e_ = (call);                                                                  \
+        if (e_ != cudaSuccess)                                                                    \
+            return lnf_fail(ctx, LNF_ECUDA, "%s: %s", #call, cudaGetErrorString(e_));             \
+    } while (0)
+
+struct BatchEntry {
+    std::vector<lnf_job> key;
+    cudaStream_t stream = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+};
+
+void lnf_batch_cache_clear(lnf_ctx *ctx)
+{
+    for (BatchEntry *b : ctx->batches) {
+        if (b->exec)
+            cudaGraphExecDestroy(b->exec);
+        if (b->graph)
+            cudaGraphDestroy(b->graph);
+        delete b;
+    }
+    ctx->batches.clear();
+}
+
+static bool same_jobs(const std::vector<lnf_job> &a, const lnf_job *b, int n)
+{
+    return (int)a.size() == n && std::memcmp(a.data(), b, sizeof(lnf_job) * n) == 0;
+}
+
+static lnf_status check_job(lnf_ctx *ctx, const lnf_job &j, int i)
+{
+    lnf_status s = lnf_check_volume(ctx, j.in, j.dims, j.dtype);
+    if (s != LNF_OK)
+        return s;
+    if (j.filter_id < LNF_MEAN || j.filter_id > LNF_OURS || j.radius < 0 || j.radius > LNF_MAX_RADIUS)
+        return lnf_fail(ctx, LNF_EINVAL, "job %d: filter %d / radius %d out of range", i, j.filter_id, j.radius);
+    if (!j.out)
+        return lnf_fail(ctx, LNF_EINVAL, "job %d: null output", i);
+    if (j.roi_dims[0] > 0 || j.roi_dims[1] > 0 || j.roi_dims[2] > 0)
+        for (int a = 0; a < 3; ++a)
+            if (j.roi_dims[a] < 1 || j.roi_origin[a] < 0 || j.roi_origin[a] + j.roi_dims[a] > j.dims[a])
+                return lnf_fail(ctx, LNF_EINVAL, "job %d: ROI outside the volume", i);
+    const size_t es = j.dtype == LNF_U8 ? 1 : 2;
+    const size_t nin = (size_t)j.dims[0] * j.dims[1] * j.dims[2] * es;
+    const size_t nout = j.roi_dims[0] > 0 ? (size_t)j.roi_dims[0] * j.roi_dims[1] * j.roi_dims[2] * es : nin;
+    const char *pi = static_cast<const char *>(j.in), *po = static_cast<const char *>(j.out);
+    if (pi < po + nout && po < pi + nin)
+        return lnf_fail(ctx, LNF_EINVAL, "job %d: input and output overlap", i);
+    return LNF_OK;
+}
+
+// Enqueue the whole batch (<= LNF_MAX_PACK jobs) on `st`: stats, params,
+// histogram zeroing, the persistent filter launch and the entropies.
+lnf_status lnf_enqueue_batch(lnf_ctx *ctx, const lnf_job *jobs, int n, int zchunk, cudaStream_t st,
+                             std::vector<VolScratch> *scratch_out)
+{
+    // distinct input volumes share one statistics pass
+    std::vector<const void *> vols;
+    std::vector<int> vol_of(n);
+    for (int i = 0; i < n; ++i) {
+        auto it = std::find(vols.begin(), vols.end(), jobs[i].in);
+        if (it == vols.end()) {
+            vol_of[i] = (int)vols.size();
+            vols.push_back(jobs[i].in);
+        } else {
+            vol_of[i] = (int)(it - vols.begin());
+        }
+    }
+    lnf_status s = lnf_scratch_pool(ctx, vols.size());
+    if (s != LNF_OK)
+        return s;
+    StatsPack sp;
+    std::memset(&sp, 0, sizeof sp);
+    sp.n_jobs = (int)vols.size();
+    for (size_t v = 0; v < vols.size(); ++v) {
+        int first = (int)(std::find(vol_of.begin(), vol_of.end(), (int)v) - vol_of.begin());
+        const lnf_job &j = jobs[first];
+        StatsJob &sj = sp.jobs[v];
+        sj.vol = j.in;
+        sj.n = (u64)j.dims[0] * j.dims[1] * j.dims[2];
+        sj.dtype = j.dtype;
+        sj.hist = ctx->pool[v].hist;
+        sj.st = ctx->pool[v].st;
+        sj.prm = ctx->pool[v].prm;
+        sj.lut = ctx->pool[v].lut;
+    }
+    const int per = std::max(1, (2 * ctx->num_sms + sp.n_jobs - 1) / sp.n_jobs);
+    CK(lnf_launch_stats_init_batched(sp, st));
+    CK(lnf_launch_stats_batched(sp, per, st));
+    CK(lnf_launch_params_batched(sp, lnf_param_cfg(ctx->cfg), st));
+
+    FilterPack &pk = ctx->pack;
+    std::memset(&pk, 0, sizeof(int) * 16);
+    pk.n_jobs = n;
+    EntropyPack ep;
+    std::memset(&ep, 0, sizeof ep);
+    const int zsave = ctx->zchunk;
+    ctx->zchunk = zchunk;
+    for (int i = 0; i < n; ++i) {
+        const lnf_job &j = jobs[i];
+        u64 *oh = nullptr;
+        const u32 levels = j.dtype == LNF_U8 ? LNF_LEVELS_U8 : LNF_LEVELS_U16;
+        if (j.d_entropy) {
+            oh = ctx->out_hist + (size_t)i * LNF_LEVELS_U16;
+            CK(lnf_launch_zero(oh, levels, st));
+            const int k = ep.count++;
+            ep.hist[k] = oh;
+            ep.levels[k] = levels;
+            ep.n[k] = j.roi_dims[0] > 0 ? (u64)j.roi_dims[0] * j.roi_dims[1] * j.roi_dims[2]
+                                        : (u64)j.dims[0] * j.dims[1] * j.dims[2];
+            ep.H[k] = j.d_entropy;
+        }
+        s = lnf_make_job(ctx, pk, i, j.filter_id, j.radius, j.in, j.out, j.dims, j.dtype, j.roi_origin,
+                         j.roi_dims, ctx->pool[vol_of[i]], oh);
+        if (s != LNF_OK) {
+            ctx->zchunk = zsave;
+            return s;
+        }
+    }
+    ctx->zchunk = zsave;
+    if ((s = lnf_run_pack(ctx, pk, 1, st)) != LNF_OK)
+        return s;
+    CK(lnf_launch_entropy_pack(ep, st));
+    if (scratch_out) {
+        scratch_out->clear();
+        for (int i = 0; i < n; ++i)
+            scratch_out->push_back(ctx->pool[vol_of[i]]);
+    }
+    return LNF_OK;
+}
+
+// time one enqueue of the batch with zchunk `zc` (events on the context stream)
+static float time_batch(lnf_ctx *ctx, const lnf_job *jobs, int n, int zc)
+{
+    cudaEvent_t a, b;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    float best = 1e30f;
+    for (int rep = 0; rep < 3; ++rep) {
+        cudaEventRecord(a, ctx->stream);
+        if (lnf_enqueue_batch(ctx, jobs, n, zc, ctx->stream, nullptr) != LNF_OK) {
+            best = 1e30f;
+            break;
+        }
+        cudaEventRecord(b, ctx->stream);
+        cudaEventSynchronize(b);
+        float ms = 0;
+        cudaEventElapsedTime(&ms, a, b);
+        best = std::min(best, ms);
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    return best;
+}
+
+extern "C" lnf_status lnf_filter_batch(lnf_ctx *ctx, const lnf_job *jobs, int n_jobs)
+{
+    if (!ctx)
+        return LNF_EINVAL;
+    if (n_jobs < 0 || (n_jobs > 0 && !jobs))
+        return lnf_fail(ctx, LNF_EINVAL, "bad job list");
+    if (n_jobs == 0)
+        return LNF_OK;
+    for (int i = 0; i < n_jobs; ++i) {
+        lnf_status s = check_job(ctx, jobs[i], i);
+        if (s != LNF_OK)
+            return s;
+    }
+    if (n_jobs > LNF_MAX_PACK) {   // several packs, in order
+        for (int i = 0; i < n_jobs; i += LNF_MAX_PACK) {
+            lnf_status s = lnf_filter_batch(ctx, jobs + i, std::min(LNF_MAX_PACK, n_jobs - i));
+            if (s != LNF_OK)
+                return s;
+        }
+        return LNF_OK;
+    }
+    for (auto &b : ctx->batches)
+        if (b->stream == ctx->stream && same_jobs(b->key, jobs, n_jobs)) {
+            CK(cudaGraphLaunch(b->exec, ctx->stream));
+            return LNF_OK;
+        }
+    // autotune the z chunk once per context
+    if (ctx->cfg.autotune && ctx->tuned_zchunk == 0) {
+        int best_zc = 64;
+        float best_ms = 1e30f;
+        for (int zc : {16, 32, 64, 128}) {
+            float ms = time_batch(ctx, jobs, n_jobs, zc);
+            if (ms < best_ms) {
+                best_ms = ms;
+                best_zc = zc;
+            }
+        }
+        ctx->tuned_zchunk = best_zc;
+    }
+    const int zc = ctx->tuned_zchunk ? ctx->tuned_zchunk : 64;
+    std::unique_ptr<BatchEntry> e(new BatchEntry());
+    e->key.assign(jobs, jobs + n_jobs);
+    e->stream = ctx->stream;
+    // capture needs a non-default stream
+    cudaStream_t cap = ctx->stream;
+    bool own = false;
+    if (cap == nullptr) {
+        CK(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+        own = true;
+    }
+    CK(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
+    lnf_status s = lnf_enqueue_batch(ctx, jobs, n_jobs, zc, cap, nullptr);
+    cudaGraph_t g = nullptr;
+    cudaError_t ce = cudaStreamEndCapture(cap, &g);
+    if (s != LNF_OK || ce != cudaSuccess) {
+        if (g)
+            cudaGraphDestroy(g);
+        if (own)
+            cudaStreamDestroy(cap);
+        return s != LNF_OK ? s : lnf_fail(ctx, LNF_ECUDA, "graph capture: %s", cudaGetErrorString(ce));
+    }
+    e->graph = g;
+    cudaError_t ie = cudaGraphInstantiate(&e->exec, g, 0);
+    if (own)
+        cudaStreamDestroy(cap);
+    if (ie != cudaSuccess)
+        return lnf_fail(ctx, LNF_ECUDA, "graph instantiate: %s", cudaGetErrorString(ie));
+    CK(cudaGraphLaunch(e->exec, ctx->stream));
+    if (ctx->batches.size() >= 16) {
+        BatchEntry *old = ctx->batches.front();
+        cudaGraphExecDestroy(old->exec);
+        cudaGraphDestroy(old->graph);
+        delete old;
+        ctx->batches.erase(ctx->batches.begin());
+    }
+    ctx->batches.push_back(e.release());
+    return LNF_OK;
+}

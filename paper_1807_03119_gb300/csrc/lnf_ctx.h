@@ -1,0 +1,95 @@
+// Host-side context of liblnf (internal).
+#pragma once
+
+#include "lnf.h"
+#include "lnf_internal.cuh"
+
+#include <condition_variable>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <vector>
+
+typedef CUresult (*PFN_encodeTiled)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                    const cuuint64_t *, const cuuint32_t *, const cuuint32_t *,
+                                    CUtensorMapInterleave, CUtensorMapSwizzle, CUtensorMapL2promotion,
+                                    CUtensorMapFloatOOBfill);
+
+// Device scratch of one analysed volume: histogram, stats, parameters, weights.
+struct VolScratch {
+    u64 *hist = nullptr;
+    DevStats *st = nullptr;
+    DevParams *prm = nullptr;
+    u32 *lut = nullptr;
+};
+
+struct BatchEntry;      // batch.cu
+struct Server;          // serve.cu
+
+struct lnf_ctx {
+    lnf_config cfg{};
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    int num_sms = 1;
+    int zchunk = 64;            // z chunk length of a work item
+    bool no_tma = false;        // testing: force plain loads
+    bool no_fast = false;       // testing: force the generic kernel
+    VolScratch vs;              // scratch of plain calls
+    std::vector<VolScratch> pool;   // scratch of batched / resident volumes
+    u64 *out_hist = nullptr;    // LNF_MAX_PACK output histograms of 65536 bins
+    double *d_H = nullptr;
+    u32 *d_err = nullptr;
+    u32 *d_counter = nullptr;
+    PFN_encodeTiled encode = nullptr;
+    FilterPack pack;            // host staging of the kernel-parameter pack
+    // host-buffer entry points: device staging
+    void *st_in = nullptr;
+    size_t st_in_cap = 0;
+    std::vector<void *> st_out;
+    std::vector<size_t> st_out_cap;
+    // batched graph cache
+    std::vector<BatchEntry *> batches;   // owned; freed by lnf_batch_cache_clear
+    // autotuner choice for batched launches (0 = not tuned yet)
+    int tuned_zchunk = 0;
+    // profiling: events around launches of the plain path, launch counter
+    bool prof = false;
+    int64_t prof_launches = 0;
+    struct ProfRec {
+        std::string name;
+        cudaEvent_t a, b;
+    };
+    std::vector<ProfRec> prof_recs;
+    std::vector<cudaEvent_t> prof_free;
+    // serving
+    Server *srv = nullptr;
+    std::mutex err_mu;
+    std::string err, err_copy;
+};
+
+lnf_status lnf_fail(lnf_ctx *ctx, lnf_status s, const char *fmt, ...);
+lnf_status lnf_check_volume(lnf_ctx *ctx, const void *p, const int64_t dims[3], int dtype);
+ParamCfg lnf_param_cfg(const lnf_config &c);
+lnf_status lnf_scratch_pool(lnf_ctx *ctx, size_t n);
+lnf_status lnf_analyze(lnf_ctx *ctx, const void *in, const int64_t dims[3], int dtype, VolScratch &vs,
+                       cudaStream_t stream);
+lnf_status lnf_make_job(lnf_ctx *ctx, FilterPack &pk, int idx, int filter, int radius, const void *in, void *out,
+                        const int64_t dims[3], int dtype, const int64_t *roi_o, const int64_t *roi_d,
+                        const VolScratch &vs, u64 *out_hist);
+lnf_status lnf_run_pack(lnf_ctx *ctx, FilterPack &pk, int persistent, cudaStream_t stream);
+lnf_status lnf_run_pack_counter(lnf_ctx *ctx, FilterPack &pk, int persistent, cudaStream_t stream, u32 *counter);
+lnf_status lnf_run_one(lnf_ctx *ctx, int filter, int radius, const void *in, void *out, const int64_t dims[3],
+                       int dtype, const int64_t *roi_o, const int64_t *roi_d, const VolScratch &vs,
+                       u64 *out_hist, cudaStream_t stream);
+// profiling helpers (api.cu): bracket one launch (or a group of `count` launches)
+int lnf_prof_begin(lnf_ctx *ctx, cudaStream_t st);
+void lnf_prof_end(lnf_ctx *ctx, int rec, const char *name, cudaStream_t st, int count);
+// fast.cu: run the job through a specialised kernel if one covers it (*handled = 1)
+lnf_status lnf_fast_dispatch(lnf_ctx *ctx, const FilterJob &job, const CUtensorMap *tmap, cudaStream_t stream,
+                             int *handled);
+// batch.cu
+void lnf_batch_cache_clear(lnf_ctx *ctx);
+// serve.cu
+void lnf_serve_shutdown(lnf_ctx *ctx);

@@ -1,0 +1,227 @@
+// Internal declarations shared by the CUDA translation units of liblnf.
+// Nothing here is part of the public C ABI (include/lnf.h).
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+typedef unsigned long long u64;
+typedef unsigned int u32;
+
+#define LNF_LEVELS_U8 256
+#define LNF_LEVELS_U16 65536
+
+// Statistics of one volume, accumulated on the device by the stats kernel.
+struct DevStats {
+    u64 N;          // voxel count (set by the host before the pass)
+    u64 S;          // sum P
+    u64 Q;          // sum P^2 (fits: N < 2^32 and P <= 65535)
+    u32 minv;
+    u32 maxv;
+    u32 levels;     // 256 or 65536
+    u32 pad;
+};
+
+// Per-volume parameter derivation settings (from lnf_config).
+struct ParamCfg {
+    int threshold_mode;         // 0 Otsu, 1 fixed, 2 none
+    u32 threshold_value;
+    int sigma_k;
+    int pad;
+    long long okada_td;         // >= 0, or -1 = auto
+    long long entropy_te;       // >= 0, -1 = pass all, -2 = auto (per radius)
+};
+
+// Parameters derived on the device from DevStats + histogram (one per volume).
+struct DevParams {
+    u64 N, S, Q;
+    u32 minv, maxv;
+    u32 T;                      // gate threshold (Eq. 1 / fixed / 0)
+    u32 delta;                  // sigma band: |P_i - P0| <= delta
+    long long td;               // Okada: |P0 - P_i| < td
+    u64 hw_sum;                 // sum_v h[v] w[v]
+    long long te_cfg;           // entropy threshold setting (see ParamCfg)
+    u32 levels;
+    u32 valid;                  // 1 once written
+    double H_in;                // image entropy of the input
+};
+
+// One unit of filter work: a volume (or ROI of it) with a filter and radius.
+struct FilterJob {
+    const void *in;
+    void *out;
+    int nx, ny, nz;             // whole volume
+    int ox, oy, oz;             // ROI origin
+    int bx, by, bz;             // ROI dims (= output dims)
+    int dtype;                  // 0 u8, 1 u16
+    int filter;                 // lnf_filter_id
+    int radius;
+    int offset;                 // cluster offset d
+    const DevParams *prm;
+    const u32 *lut;             // entropy weights, levels entries
+    u64 *out_hist;              // output histogram (levels entries) or null
+    int tmap_idx;               // index of the job's TMA map in the pack, -1: plain loads
+    int tiles_x, tiles_y, zchunks;
+    int item_begin;             // first flattened work item of this job
+};
+
+// Up to kMaxJobs jobs and their TMA maps, passed BY VALUE as a
+// __grid_constant__ kernel parameter (so a captured graph owns its copy).
+#define LNF_MAX_PACK 64
+struct FilterPack {
+    int n_jobs;
+    int total_items;
+    int pad[14];
+    CUtensorMap tmaps[LNF_MAX_PACK];    // 64-byte aligned
+    FilterJob jobs[LNF_MAX_PACK];
+};
+
+// Device error word: set (never trapped) when a bounded wait gives up.
+#define LNF_DERR_TIMEOUT 1u
+#define LNF_DERR_BADJOB 2u
+
+// ----------------------------------------------------------------- PTX helpers
+namespace lnfdev {
+
+__device__ __forceinline__ u32 smem_u32(const void *p)
+{
+    return static_cast<u32>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(u64 *bar, u32 count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_inval(u64 *bar)
+{
+    asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init()
+{
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async_smem()
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(u64 *bar, u32 bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(u64 *bar, u32 parity)
+{
+    u32 ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ u64 global_ns()
+{
+    u64 t;
+    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Wait for the mbarrier phase with a time limit; on timeout set the error
+// word and return false (the caller then stops issuing work and exits).
+__device__ __forceinline__ bool mbar_wait_bounded(u64 *bar, u32 parity, u32 *err, u64 limit_ns = 2000000000ull)
+{
+    if (mbar_try_wait(bar, parity))
+        return true;
+    u64 t0 = global_ns();
+    for (;;) {
+        if (mbar_try_wait(bar, parity))
+            return true;
+        if (global_ns() - t0 > limit_ns) {
+            if (err)
+                atomicOr(err, LNF_DERR_TIMEOUT);
+            return false;
+        }
+    }
+}
+
+// TMA: load a 3D box of the tensor map at element coordinates (x, y, z) into
+// shared memory, completing `bytes` on the mbarrier.  x * elem_size must be a
+// multiple of 16 bytes (the caller guarantees it).
+__device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, u64 *bar, int x, int y, int z)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
+        ::"r"(smem_u32(dst)), "l"(reinterpret_cast<u64>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void prefetch_tmap(const CUtensorMap *map)
+{
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<u64>(map)) : "memory");
+}
+
+}  // namespace lnfdev
+
+// ----------------------------------------------------------------- launchers
+// (defined in stats.cu / filter.cu; all enqueue on `stream`)
+cudaError_t lnf_launch_stats(const void *vol, u64 n, int dtype, u64 *hist, DevStats *st, int num_sms,
+                             cudaStream_t stream);
+cudaError_t lnf_launch_stats_init(u64 *hist, u32 levels, DevStats *st, u64 n, cudaStream_t stream);
+cudaError_t lnf_launch_params(const u64 *hist, const DevStats *st, const ParamCfg &cfg, DevParams *prm,
+                              u32 *lut, cudaStream_t stream);
+cudaError_t lnf_launch_entropy(const u64 *hist, u32 levels, u64 n, double *H, cudaStream_t stream);
+cudaError_t lnf_launch_zero(u64 *p, u64 count, cudaStream_t stream);
+
+// Batched forms: arrays of volumes, one CTA group per volume.
+struct StatsJob {
+    const void *vol;
+    u64 n;
+    int dtype;
+    int pad;
+    u64 *hist;
+    DevStats *st;
+    DevParams *prm;
+    u32 *lut;
+};
+struct StatsPack {
+    int n_jobs;
+    int pad[3];
+    StatsJob jobs[LNF_MAX_PACK];
+};
+cudaError_t lnf_launch_stats_batched(const StatsPack &pk, int ctas_per_job, cudaStream_t stream);
+cudaError_t lnf_launch_stats_init_batched(const StatsPack &pk, cudaStream_t stream);
+cudaError_t lnf_launch_params_batched(const StatsPack &pk, const ParamCfg &cfg, cudaStream_t stream);
+// One CTA per entry: H[i] = entropy of histogram hists[i] (levels[i] bins, n[i] voxels).
+#define LNF_MAX_ENT 128
+struct EntropyPack {
+    int count;
+    int pad;
+    const u64 *hist[LNF_MAX_ENT];
+    u64 n[LNF_MAX_ENT];
+    double *H[LNF_MAX_ENT];
+    u32 levels[LNF_MAX_ENT];
+};
+cudaError_t lnf_launch_entropy_pack(const EntropyPack &pk, cudaStream_t stream);
+
+// Filter launch helpers (filter.cu).
+int lnf_halo(int filter, int radius, int offset);
+size_t lnf_filter_smem_bytes(int filter, int radius, int offset, int dtype);
+void lnf_filter_decompose(FilterJob &j, int zchunk_len);
+void lnf_filter_box(int filter, int radius, int offset, int dtype, unsigned *box_w, unsigned *box_h);
+int lnf_filter_items(const FilterJob &j);
+int lnf_filter_threads();
+int lnf_filter_occupancy(size_t smem);
+// Launch `grid` CTAs over the `total_items` work items of the jobs (device
+// array sorted by item_begin).  persistent != 0: CTAs claim items from
+// *d_counter (which must be 0 at launch); else CTA b takes b, b+grid, ...
+cudaError_t lnf_filter_run(const FilterPack &pk, size_t smem, int grid, int persistent, u32 *d_counter, u32 *d_err,
+                           cudaStream_t stream);

@@ -1,0 +1,550 @@
+// Statistics pre-pass and parameter derivation, on the device.
+//
+//   k_stats   : one read of the volume -> grey-level histogram h[v], S = sum P,
+//               Q = sum P^2, min, max  (the "normalized frequency distribution"
+//               the entropy filter precomputes, section "Entropy Filter", and
+//               the inputs of the Otsu threshold, Eq. 1, and the global sigma
+//               of the sigma filter, Eq. 5).
+//   k_params  : one CTA -> Otsu threshold T (Eq. 1) in exact integer
+//               arithmetic, sigma band delta, Okada T_d, the fixed-point
+//               entropy weights w[v] of Eq. 7, and the input image entropy.
+//   k_entropy : image entropy H = -sum (c/N) log2(c/N) of a histogram (the
+//               measure of the paper's Fig. 4), FP64 only in this reduction.
+#include "lnf_internal.cuh"
+
+typedef unsigned __int128 u128;
+typedef __int128 i128;
+
+namespace {
+
+constexpr int kStatsThreads = 1024;
+constexpr int kSmemBinsU16 = 32768;   // u16 values >= this go straight to global atomics
+constexpr int kReplicasU8 = 16;       // sub-histograms for 8-bit data (fewer bank conflicts)
+
+// ------------------------------------------------------------------ init
+
+__global__ void k_stats_init(u64 *hist, u32 levels, DevStats *st, u64 n)
+{
+    for (u32 i = blockIdx.x * blockDim.x + threadIdx.x; i < levels; i += gridDim.x * blockDim.x)
+        hist[i] = 0;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        st->N = n;
+        st->S = 0;
+        st->Q = 0;
+        st->minv = 0xFFFFFFFFu;
+        st->maxv = 0;
+        st->levels = levels;
+        st->pad = 0;
+    }
+}
+
+__global__ void k_stats_init_batched(const __grid_constant__ StatsPack pk)
+{
+    const StatsJob &j = pk.jobs[blockIdx.y];
+    u32 levels = j.dtype == 0 ? LNF_LEVELS_U8 : LNF_LEVELS_U16;
+    for (u32 i = blockIdx.x * blockDim.x + threadIdx.x; i < levels; i += gridDim.x * blockDim.x)
+        j.hist[i] = 0;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        DevStats *st = j.st;
+        st->N = j.n;
+        st->S = 0;
+        st->Q = 0;
+        st->minv = 0xFFFFFFFFu;
+        st->maxv = 0;
+        st->levels = levels;
+        st->pad = 0;
+    }
+}
+
+__global__ void k_zero(u64 *p, u64 count)
+{
+    for (u64 i = blockIdx.x * (u64)blockDim.x + threadIdx.x; i < count; i += (u64)gridDim.x * blockDim.x)
+        p[i] = 0;
+}
+
+// ------------------------------------------------------------------ stats
+
+struct StatsAcc {
+    u64 s, q;
+    u32 mn, mx;
+};
+
+template <typename T>
+__device__ __forceinline__ void stats_value(u32 v, u32 *sh, u64 *hist, StatsAcc &a)
+{
+    if (sizeof(T) == 1) {
+        atomicAdd(&sh[v], 1u);
+    } else {
+        if (v < (u32)kSmemBinsU16)
+            atomicAdd(&sh[v], 1u);
+        else
+            atomicAdd(&hist[v], 1ull);
+    }
+    a.s += v;
+    a.q += (u64)v * v;
+    a.mn = min(a.mn, v);
+    a.mx = max(a.mx, v);
+}
+
+template <typename T>
+__device__ void stats_body(const T *vol, u64 n, u64 *hist, DevStats *st, u64 cta, u64 nctas, u32 *smem)
+{
+    const int bins = sizeof(T) == 1 ? LNF_LEVELS_U8 * kReplicasU8 : kSmemBinsU16;
+    for (int i = threadIdx.x; i < bins; i += blockDim.x)
+        smem[i] = 0;
+    __syncthreads();
+    u32 *sh = sizeof(T) == 1 ? smem + ((threadIdx.x >> 5) % kReplicasU8) * LNF_LEVELS_U8 : smem;
+
+    StatsAcc a{0, 0, 0xFFFFFFFFu, 0};
+    const u64 gtid = cta * blockDim.x + threadIdx.x;
+    const u64 gsz = nctas * blockDim.x;
+    // elements before the first 16-byte boundary
+    u64 head = ((16 - (reinterpret_cast<uintptr_t>(vol) & 15)) & 15) / sizeof(T);
+    if (head > n)
+        head = n;
+    for (u64 i = gtid; i < head; i += gsz)
+        stats_value<T>(vol[i], sh, hist, a);
+    const uint4 *v4 = reinterpret_cast<const uint4 *>(vol + head);
+    const u64 nv = (n - head) * sizeof(T) / 16;
+    for (u64 i = gtid; i < nv; i += gsz) {
+        uint4 w = __ldcs(v4 + i);   // streamed once: do not keep in L2
+        u32 words[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            if (sizeof(T) == 1) {
+#pragma unroll
+                for (int b = 0; b < 4; ++b)
+                    stats_value<T>((words[k] >> (8 * b)) & 0xFFu, sh, hist, a);
+            } else {
+                stats_value<T>(words[k] & 0xFFFFu, sh, hist, a);
+                stats_value<T>(words[k] >> 16, sh, hist, a);
+            }
+        }
+    }
+    for (u64 i = head + nv * (16 / sizeof(T)) + gtid; i < n; i += gsz)
+        stats_value<T>(vol[i], sh, hist, a);
+    __syncthreads();
+    if (sizeof(T) == 1) {
+        for (int v = threadIdx.x; v < LNF_LEVELS_U8; v += blockDim.x) {
+            u32 c = 0;
+            for (int r = 0; r < kReplicasU8; ++r)
+                c += smem[r * LNF_LEVELS_U8 + v];
+            if (c)
+                atomicAdd(&hist[v], (u64)c);
+        }
+    } else {
+        for (int v = threadIdx.x; v < kSmemBinsU16; v += blockDim.x) {
+            u32 c = smem[v];
+            if (c)
+                atomicAdd(&hist[v], (u64)c);
+        }
+    }
+    // warp reduction of the moments, then one atomic per warp
+    for (int o = 16; o > 0; o >>= 1) {
+        a.s += __shfl_xor_sync(0xFFFFFFFFu, a.s, o);
+        a.q += __shfl_xor_sync(0xFFFFFFFFu, a.q, o);
+        a.mn = min(a.mn, __shfl_xor_sync(0xFFFFFFFFu, a.mn, o));
+        a.mx = max(a.mx, __shfl_xor_sync(0xFFFFFFFFu, a.mx, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (a.s)
+            atomicAdd(&st->S, a.s);
+        if (a.q)
+            atomicAdd(&st->Q, a.q);
+        if (a.mn != 0xFFFFFFFFu)
+            atomicMin(&st->minv, a.mn);
+        if (a.mx)
+            atomicMax(&st->maxv, a.mx);
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kStatsThreads) k_stats(const T *vol, u64 n, u64 *hist, DevStats *st)
+{
+    extern __shared__ u32 smem[];
+    stats_body<T>(vol, n, hist, st, blockIdx.x, gridDim.x, smem);
+}
+
+__global__ void __launch_bounds__(kStatsThreads) k_stats_batched(const __grid_constant__ StatsPack pk)
+{
+    extern __shared__ u32 smem[];
+    const StatsJob &j = pk.jobs[blockIdx.y];
+    if (j.dtype == 0)
+        stats_body<uint8_t>(static_cast<const uint8_t *>(j.vol), j.n, j.hist, j.st, blockIdx.x, gridDim.x, smem);
+    else
+        stats_body<uint16_t>(static_cast<const uint16_t *>(j.vol), j.n, j.hist, j.st, blockIdx.x, gridDim.x, smem);
+}
+
+// ------------------------------------------------------------------ exact helpers
+
+// floor(sqrt(x)) bit by bit
+__device__ u64 isqrt_u128(u128 x)
+{
+    u64 r = 0;
+    for (int b = 63; b >= 0; --b) {
+        u64 c = r | (1ull << b);
+        if ((u128)c * c <= x)
+            r = c;
+    }
+    return r;
+}
+
+// Binary logarithm of x >= 1 in fixed point with 40 fractional bits, by the
+// classical repeated-squaring method: x = 2^k m with m in [1,2) held with 62
+// fractional bits; each squaring (truncated to 62 fractional bits) that
+// reaches 2 yields a 1 bit and is halved.
+__device__ u64 log2_fixed40(u64 x)
+{
+    const int k = 63 - __clzll(x);
+    u64 m = k <= 62 ? (x << (62 - k)) : (x >> (k - 62));
+    u64 res = (u64)k << 40;
+    for (int i = 1; i <= 40; ++i) {
+        const u64 lo = m * m;
+        const u64 hi = __umul64hi(m, m);
+        m = (hi << 2) | (lo >> 62);
+        if (m >= (1ull << 63)) {
+            m >>= 1;
+            res |= 1ull << (40 - i);
+        }
+    }
+    return res;
+}
+
+// J(t) = S0^2/n0 + S1^2/n1 split as q + fnum/fden with fnum/fden in [0, 2).
+struct OtsuJ {
+    u128 q;
+    u64 fnum, fden;
+    u32 t;          // 0 = no candidate
+};
+
+__device__ __forceinline__ OtsuJ otsu_j(u64 n0, u64 s0, u64 N, u64 S, u32 t)
+{
+    const u64 n1 = N - n0, s1 = S - s0;
+    const u128 a = (u128)s0 * s0, b = (u128)s1 * s1;
+    const u128 q0 = a / n0, q1 = b / n1;
+    const u64 r0 = (u64)(a - q0 * n0), r1 = (u64)(b - q1 * n1);
+    OtsuJ j;
+    j.q = q0 + q1;
+    j.fnum = r0 * n1 + r1 * n0;   // < 2 n0 n1 <= 2^63
+    j.fden = n0 * n1;             // <= N^2/4 < 2^62
+    j.t = t;
+    return j;
+}
+
+// sign(J_a - J_b), exactly
+__device__ __forceinline__ int otsu_cmp(const OtsuJ &a, const OtsuJ &b)
+{
+    const i128 dq = (i128)a.q - (i128)b.q;
+    if (dq >= 2)
+        return 1;
+    if (dq <= -2)
+        return -1;
+    const i128 x = dq * (i128)a.fden * (i128)b.fden + (i128)a.fnum * (i128)b.fden - (i128)b.fnum * (i128)a.fden;
+    return x > 0 ? 1 : (x < 0 ? -1 : 0);
+}
+
+// better = larger J; equal J -> smaller t; t == 0 never wins
+__device__ __forceinline__ bool otsu_better(const OtsuJ &a, const OtsuJ &b)
+{
+    if (a.t == 0)
+        return false;
+    if (b.t == 0)
+        return true;
+    int c = otsu_cmp(a, b);
+    return c > 0 || (c == 0 && a.t < b.t);
+}
+
+struct ParamsSmem {
+    u64 n[1024];
+    u64 s[1024];
+    u128 q[1024];
+    u64 fnum[1024];
+    u64 fden[1024];
+    u32 t[1024];
+    double d[1024];
+};
+
+__device__ void params_body(const u64 *hist, const DevStats *st, const ParamCfg &cfg, DevParams *prm, u32 *lut,
+                            ParamsSmem &sm)
+{
+    const int tid = threadIdx.x;
+    const int nt = blockDim.x;    // 1024
+    const u32 L = st->levels;
+    const u64 N = st->N, S = st->S, Q = st->Q;
+    const int chunk = (L + nt - 1) / nt;
+    const int b0 = min((int)L, tid * chunk), b1 = min((int)L, b0 + chunk);
+
+    // 1. exclusive scan of (count, sum) over the bins
+    u64 ln = 0, ls = 0;
+    for (int v = b0; v < b1; ++v) {
+        const u64 h = hist[v];
+        ln += h;
+        ls += h * (u64)v;
+    }
+    sm.n[tid] = ln;
+    sm.s[tid] = ls;
+    __syncthreads();
+    for (int off = 1; off < nt; off <<= 1) {   // Hillis-Steele inclusive scan
+        u64 an = 0, as = 0;
+        if (tid >= off) {
+            an = sm.n[tid - off];
+            as = sm.s[tid - off];
+        }
+        __syncthreads();
+        sm.n[tid] += an;
+        sm.s[tid] += as;
+        __syncthreads();
+    }
+    u64 n0 = sm.n[tid] - ln, s0 = sm.s[tid] - ls;
+    __syncthreads();
+
+    // 2. Otsu (Eq. 1): candidates t = v + 1 for every occupied level v; an
+    //    empty level v gives J(v+1) = J(v), which can never win a tie.
+    OtsuJ best;
+    best.t = 0;
+    best.q = 0;
+    best.fnum = 0;
+    best.fden = 1;
+    for (int v = b0; v < b1; ++v) {
+        const u64 h = hist[v];
+        n0 += h;
+        s0 += h * (u64)v;
+        if (h == 0 || v + 1 > (int)L - 1 || n0 == 0 || n0 == N)
+            continue;
+        OtsuJ j = otsu_j(n0, s0, N, S, (u32)(v + 1));
+        if (otsu_better(j, best))
+            best = j;
+    }
+    sm.q[tid] = best.q;
+    sm.fnum[tid] = best.fnum;
+    sm.fden[tid] = best.fden;
+    sm.t[tid] = best.t;
+    __syncthreads();
+    for (int off = nt / 2; off > 0; off >>= 1) {
+        if (tid < off) {
+            OtsuJ a{sm.q[tid], sm.fnum[tid], sm.fden[tid], sm.t[tid]};
+            OtsuJ b{sm.q[tid + off], sm.fnum[tid + off], sm.fden[tid + off], sm.t[tid + off]};
+            if (otsu_better(b, a)) {
+                sm.q[tid] = b.q;
+                sm.fnum[tid] = b.fnum;
+                sm.fden[tid] = b.fden;
+                sm.t[tid] = b.t;
+            }
+        }
+        __syncthreads();
+    }
+    const u32 t_otsu = sm.t[0] ? sm.t[0] : st->minv;   // single level: T = that level
+    __syncthreads();
+
+    // 3. entropy weights (Eq. 7, fixed point) and sum_v h[v] w[v]
+    const u64 lgN = log2_fixed40(N);
+    u64 hw = 0;
+    double hsum = 0.0;
+    for (int v = b0; v < b1; ++v) {
+        const u64 h = hist[v];
+        u32 w = 0;
+        if (h) {
+            const u64 D = lgN - log2_fixed40(h);
+            const u128 num = (((u128)h * D) << 22) + ((u128)N << 39);
+            w = (u32)(num / ((u128)N << 40));
+            const double p = (double)h / (double)N;
+            hsum += -p * log2(p);
+        }
+        lut[v] = w;
+        hw += h * (u64)w;
+    }
+    sm.n[tid] = hw;
+    sm.d[tid] = hsum;
+    __syncthreads();
+    for (int off = nt / 2; off > 0; off >>= 1) {
+        if (tid < off) {
+            sm.n[tid] += sm.n[tid + off];
+            sm.d[tid] += sm.d[tid + off];
+        }
+        __syncthreads();
+    }
+
+    if (tid == 0) {
+        // 4. sigma band and Okada threshold from the population variance
+        const u128 var_num = (u128)N * Q - (u128)S * S;   // N^2 sigma^2
+        const u128 nn = (u128)N * N;
+        const u128 k2 = (u128)cfg.sigma_k * (u128)cfg.sigma_k;
+        const u64 delta = isqrt_u128((k2 * var_num) / nn);
+        const u64 sig = isqrt_u128(var_num / nn);
+        DevParams p;
+        p.N = N;
+        p.S = S;
+        p.Q = Q;
+        p.minv = st->minv;
+        p.maxv = st->maxv;
+        p.T = cfg.threshold_mode == 0 ? t_otsu : (cfg.threshold_mode == 1 ? cfg.threshold_value : 0u);
+        p.delta = delta > 0xFFFFFFFFull ? 0xFFFFFFFFu : (u32)delta;
+        p.td = cfg.okada_td >= 0 ? cfg.okada_td : (long long)(sig + 1);
+        p.hw_sum = sm.n[0];
+        p.te_cfg = cfg.entropy_te;
+        p.levels = L;
+        p.valid = 1;
+        p.H_in = sm.d[0];
+        *prm = p;
+    }
+}
+
+__global__ void __launch_bounds__(1024) k_params(const u64 *hist, const DevStats *st, ParamCfg cfg, DevParams *prm,
+                                                 u32 *lut)
+{
+    extern __shared__ __align__(16) unsigned char psm[];
+    params_body(hist, st, cfg, prm, lut, *reinterpret_cast<ParamsSmem *>(psm));
+}
+
+__global__ void __launch_bounds__(1024) k_params_batched(const __grid_constant__ StatsPack pk, ParamCfg cfg)
+{
+    extern __shared__ __align__(16) unsigned char psm[];
+    const StatsJob &j = pk.jobs[blockIdx.x];
+    params_body(j.hist, j.st, cfg, j.prm, j.lut, *reinterpret_cast<ParamsSmem *>(psm));
+}
+
+// ------------------------------------------------------------------ entropy
+
+__device__ void entropy_body(const u64 *hist, u32 levels, u64 n, double *H, double *sd)
+{
+    const int tid = threadIdx.x;
+    double acc = 0.0;
+    const double Nd = (double)n;
+    for (u32 v = tid; v < levels; v += blockDim.x) {
+        const u64 c = hist[v];
+        if (c) {
+            const double p = (double)c / Nd;
+            acc += -p * log2(p);
+        }
+    }
+    sd[tid] = acc;
+    __syncthreads();
+    for (int off = blockDim.x / 2; off > 0; off >>= 1) {
+        if (tid < off)
+            sd[tid] += sd[tid + off];
+        __syncthreads();
+    }
+    if (tid == 0)
+        *H = sd[0];
+}
+
+__global__ void __launch_bounds__(1024) k_entropy(const u64 *hist, u32 levels, u64 n, double *H)
+{
+    __shared__ double sd[1024];
+    entropy_body(hist, levels, n, H, sd);
+}
+
+__global__ void __launch_bounds__(1024) k_entropy_pack(const __grid_constant__ EntropyPack pk)
+{
+    __shared__ double sd[1024];
+    const int i = blockIdx.x;
+    entropy_body(pk.hist[i], pk.levels[i], pk.n[i], pk.H[i], sd);
+}
+
+size_t stats_smem_bytes(int dtype)
+{
+    return dtype == 0 ? sizeof(u32) * LNF_LEVELS_U8 * kReplicasU8 : sizeof(u32) * kSmemBinsU16;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ launchers
+
+cudaError_t lnf_launch_stats_init(u64 *hist, u32 levels, DevStats *st, u64 n, cudaStream_t stream)
+{
+    k_stats_init<<<(levels + 255) / 256, 256, 0, stream>>>(hist, levels, st, n);
+    return cudaGetLastError();
+}
+
+cudaError_t lnf_launch_zero(u64 *p, u64 count, cudaStream_t stream)
+{
+    int blocks = (int)((count + 255) / 256);
+    if (blocks > 1024)
+        blocks = 1024;
+    if (blocks < 1)
+        blocks = 1;
+    k_zero<<<blocks, 256, 0, stream>>>(p, count);
+    return cudaGetLastError();
+}
+
+cudaError_t lnf_launch_stats(const void *vol, u64 n, int dtype, u64 *hist, DevStats *st, int num_sms,
+                             cudaStream_t stream)
+{
+    const size_t smem = stats_smem_bytes(dtype);
+    cudaError_t e;
+    if (dtype == 0) {
+        e = cudaFuncSetAttribute(k_stats<uint8_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess)
+            return e;
+        u64 want = (n + 16ull * kStatsThreads - 1) / (16ull * kStatsThreads);
+        int grid = (int)(want < (u64)(2 * num_sms) ? (want ? want : 1) : 2 * num_sms);
+        k_stats<uint8_t><<<grid, kStatsThreads, smem, stream>>>(static_cast<const uint8_t *>(vol), n, hist, st);
+    } else {
+        e = cudaFuncSetAttribute(k_stats<uint16_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess)
+            return e;
+        u64 want = (n + 8ull * kStatsThreads - 1) / (8ull * kStatsThreads);
+        int grid = (int)(want < (u64)num_sms ? (want ? want : 1) : num_sms);
+        k_stats<uint16_t><<<grid, kStatsThreads, smem, stream>>>(static_cast<const uint16_t *>(vol), n, hist, st);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t lnf_launch_params(const u64 *hist, const DevStats *st, const ParamCfg &cfg, DevParams *prm, u32 *lut,
+                              cudaStream_t stream)
+{
+    const int smem = (int)sizeof(ParamsSmem);
+    cudaError_t e = cudaFuncSetAttribute(k_params, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess)
+        return e;
+    k_params<<<1, 1024, smem, stream>>>(hist, st, cfg, prm, lut);
+    return cudaGetLastError();
+}
+
+cudaError_t lnf_launch_entropy(const u64 *hist, u32 levels, u64 n, double *H, cudaStream_t stream)
+{
+    k_entropy<<<1, 1024, 0, stream>>>(hist, levels, n, H);
+    return cudaGetLastError();
+}
+
+cudaError_t lnf_launch_stats_init_batched(const StatsPack &pk, cudaStream_t stream)
+{
+    if (pk.n_jobs <= 0)
+        return cudaSuccess;
+    dim3 grid(16, pk.n_jobs);
+    k_stats_init_batched<<<grid, 256, 0, stream>>>(pk);
+    return cudaGetLastError();
+}
+
+cudaError_t lnf_launch_stats_batched(const StatsPack &pk, int ctas_per_job, cudaStream_t stream)
+{
+    if (pk.n_jobs <= 0)
+        return cudaSuccess;
+    const size_t smem = stats_smem_bytes(1);
+    cudaError_t e = cudaFuncSetAttribute(k_stats_batched, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess)
+        return e;
+    dim3 grid(ctas_per_job, pk.n_jobs);
+    k_stats_batched<<<grid, kStatsThreads, smem, stream>>>(pk);
+    return cudaGetLastError();
+}
+
+cudaError_t lnf_launch_params_batched(const StatsPack &pk, const ParamCfg &cfg, cudaStream_t stream)
+{
+    if (pk.n_jobs <= 0)
+        return cudaSuccess;
+    const int smem = (int)sizeof(ParamsSmem);
+    cudaError_t e = cudaFuncSetAttribute(k_params_batched, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess)
+        return e;
+    k_params_batched<<<pk.n_jobs, 1024, smem, stream>>>(pk, cfg);
+    return cudaGetLastError();
+}
+
+cudaError_t lnf_launch_entropy_pack(const EntropyPack &pk, cudaStream_t stream)
+{
+    if (pk.count <= 0)
+        return cudaSuccess;
+    k_entropy_pack<<<pk.count, 1024, 0, stream>>>(pk);
+    return cudaGetLastError();
+}

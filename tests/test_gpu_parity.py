@@ -1,0 +1,340 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Integer outputs must match bit for bit; entropies within 1e-9 relative.
+Small cases are compared element by element (sizes that span several tiles
+with ragged tails); the full-size workloads are compared on sampled voxels
+that the oracle evaluates one by one, plus properties that hold at any size.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import phantoms
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+FILTERS = [oracle.MEAN, oracle.SIGMA, oracle.ENTROPY, oracle.OKADA, oracle.OURS]
+H_TOL = 1e-9
+
+
+@pytest.fixture(scope="module")
+def lnf():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1807_03119_gb300 as L
+    from paper_1807_03119_gb300 import builder
+    builder.build()
+    L.load()
+    return L
+
+
+@pytest.fixture(scope="module")
+def ctx(lnf):
+    c = lnf.Context()
+    yield c
+    c.close()
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.cpu().numpy()
+
+
+def assert_same(got, want, what):
+    if not np.array_equal(got, want):
+        idx = np.argwhere(got != want)
+        z, y, x = idx[0]
+        raise AssertionError(f"{what}: {len(idx)} voxels differ; first at x={x} y={y} z={z}: "
+                             f"got {got[z, y, x]} want {want[z, y, x]}")
+
+
+def oracle_cfg(**kw):
+    mode = {0: "otsu", 1: "fixed", 2: "none"}[kw.get("threshold_mode", 0)]
+    return oracle.Config(threshold_mode=mode, threshold_value=kw.get("threshold_value", 0),
+                         sigma_k=kw.get("sigma_k", 2),
+                         okada_td=None if kw.get("okada_td", -1) == -1 else kw["okada_td"],
+                         entropy_te=None if kw.get("entropy_te", -2) == -2 else kw["entropy_te"],
+                         offset=kw.get("cluster_offset", 1))
+
+
+SMALL = [
+    ((70, 19, 23), "u8", 101),      # 3 x-tiles, 3 y-tiles, ragged, plain loads (pitch 70 B)
+    ((70, 19, 23), "u16", 102),
+    ((64, 24, 40), "u16", 103),     # 16-byte pitch: TMA path
+    ((96, 17, 9), "u8", 104),       # TMA path, u8
+    ((40, 33, 130), "u16", 105),    # several z chunks
+]
+
+
+@pytest.mark.parametrize("dims,dt,seed", SMALL)
+@pytest.mark.parametrize("r", [0, 1, 2, 3])
+def test_small_all_filters_exact(ctx, dims, dt, seed, r):
+    vol = phantoms.random_volume(dims, seed, dt, p_extreme=0.05)
+    st = oracle.stats(vol)
+    prm = oracle.derive_params(st, r)
+    t = dev(vol)
+    for f in FILTERS:
+        got = host(ctx.filter_volume(t, f, r))
+        want = oracle.filter_volume(vol, f, r, params=prm)
+        assert_same(got, want, f"filter {f} r={r} {dims} {dt}")
+
+
+@pytest.mark.parametrize("dt", ["u8", "u16"])
+def test_phantom_p1_like_all_filters(ctx, dt):
+    vol = phantoms.P1() if dt == "u8" else phantoms.insect_phantom((64, 48, 40), 7, "u16")
+    st = oracle.stats(vol)
+    t = dev(vol)
+    for r in (1, 2):
+        prm = oracle.derive_params(st, r)
+        outs, H = ctx.filter_multi(t, FILTERS, r)
+        Hh = host(H)
+        assert abs(Hh[0] - oracle.image_entropy(st.hist)) <= H_TOL * max(1, Hh[0])
+        for i, f in enumerate(FILTERS):
+            want = oracle.filter_volume(vol, f, r, params=prm)
+            assert_same(host(outs[i]), want, f"P1 filter {f} r={r}")
+            hw = oracle.image_entropy(oracle.histogram(want))
+            assert abs(Hh[i + 1] - hw) <= H_TOL * max(1.0, hw), (f, Hh[i + 1], hw)
+
+
+def test_params_match_oracle(ctx):
+    cases = [phantoms.P1(), phantoms.random_volume((33, 21, 17), 5, "u16"),
+             phantoms.insect_phantom((48, 40, 36), 9, "u16"),
+             np.full((5, 6, 7), 200, np.uint8), np.full((3, 4, 9), 65535, np.uint16)]
+    two = np.full((8, 8, 8), 20, np.uint8)
+    two[:, :, 5:] = 190
+    cases.append(two)
+    for vol in cases:
+        t = dev(vol)
+        ctx.filter_volume(t, oracle.OURS, 1)
+        p = ctx.params(with_weights=True)
+        st = oracle.stats(vol)
+        prm = oracle.derive_params(st, 1)
+        L = len(st.hist)
+        assert p["n_voxels"] == st.N and p["sum"] == st.S and p["sum_sq"] == st.Q
+        assert p["min_value"] == st.minv and p["max_value"] == st.maxv
+        assert p["threshold"] == prm["T"], (p["threshold"], prm["T"])
+        assert p["sigma_band"] == prm["delta"]
+        assert p["okada_td"] == prm["td"]
+        assert np.array_equal(p["weights"][:L], prm["w"]), "entropy weight tables differ"
+        assert p["weight_sum"] == int(sum(int(c) * int(w) for c, w in zip(st.hist, prm["w"])))
+        hin = oracle.image_entropy(st.hist)
+        assert abs(p["input_entropy"] - hin) <= H_TOL * max(1.0, hin)
+
+
+@pytest.mark.parametrize("kw", [
+    dict(threshold_mode=2), dict(threshold_mode=1, threshold_value=150),
+    dict(sigma_k=1), dict(sigma_k=3), dict(okada_td=0), dict(okada_td=40),
+    dict(entropy_te=-1), dict(entropy_te=0), dict(cluster_offset=0), dict(cluster_offset=2),
+])
+def test_config_variants(lnf, kw):
+    vol = phantoms.random_volume((45, 13, 19), 77, "u8", p_extreme=0.1)
+    with lnf.Context(**kw) as c:
+        t = dev(vol)
+        st = oracle.stats(vol)
+        for r in (1, 2):
+            prm = oracle.derive_params(st, r, oracle_cfg(**kw))
+            for f in FILTERS:
+                assert_same(host(c.filter_volume(t, f, r)), oracle.filter_volume(vol, f, r, params=prm),
+                            f"{kw} filter {f} r={r}")
+
+
+def test_forced_plain_loads_match_tma(lnf, monkeypatch):
+    vol = phantoms.random_volume((64, 24, 40), 31, "u16")
+    t = dev(vol)
+    with lnf.Context() as a:
+        ref = [host(a.filter_volume(t, f, 2)) for f in FILTERS]
+    monkeypatch.setenv("LNF_FORCE_PLAIN", "1")
+    with lnf.Context() as b:
+        got = [host(b.filter_volume(t, f, 2)) for f in FILTERS]
+    for f, x, y in zip(FILTERS, ref, got):
+        assert_same(y, x, f"plain vs TMA filter {f}")
+
+
+def test_forced_generic_matches(lnf, monkeypatch):
+    vol = phantoms.insect_phantom((80, 48, 72), 12, "u16")
+    st = oracle.stats(vol)
+    t = dev(vol)
+    monkeypatch.setenv("LNF_FORCE_GENERIC", "1")
+    with lnf.Context() as b:
+        for r in (1, 2):
+            prm = oracle.derive_params(st, r)
+            for f in FILTERS:
+                assert_same(host(b.filter_volume(t, f, r)), oracle.filter_volume(vol, f, r, params=prm),
+                            f"generic filter {f} r={r}")
+
+
+@pytest.mark.parametrize("dims", [(1, 1, 1), (1, 1, 9), (9, 1, 1), (1, 7, 1), (3, 2, 1), (17, 1, 33)])
+@pytest.mark.parametrize("dt", ["u8", "u16"])
+def test_degenerate_shapes(ctx, dims, dt):
+    vol = phantoms.random_volume(dims, 3, dt)
+    st = oracle.stats(vol)
+    t = dev(vol)
+    for r in (0, 1, 3):
+        prm = oracle.derive_params(st, r)
+        for f in FILTERS:
+            assert_same(host(ctx.filter_volume(t, f, r)), oracle.filter_volume(vol, f, r, params=prm),
+                        f"{dims} filter {f} r={r}")
+
+
+def test_max_radius(ctx):
+    vol = phantoms.random_volume((20, 18, 17), 8, "u16", vmax=3000)
+    st = oracle.stats(vol)
+    t = dev(vol)
+    for r in (7, 8):
+        prm = oracle.derive_params(st, r)
+        for f in FILTERS:
+            assert_same(host(ctx.filter_volume(t, f, r)), oracle.filter_volume(vol, f, r, params=prm),
+                        f"max radius filter {f} r={r}")
+
+
+def test_constant_volumes(ctx):
+    for dt, c in (("u8", 0), ("u8", 255), ("u16", 4095), ("u16", 65535)):
+        vol = np.full((11, 9, 10), c, phantoms.dtype_of(dt))
+        t = dev(vol)
+        for f in FILTERS:
+            got = host(ctx.filter_volume(t, f, 2))
+            assert (got == (0 if f == oracle.ENTROPY else c)).all(), (dt, c, f)
+
+
+def test_roi_matches_crop(ctx):
+    vol = phantoms.insect_phantom((77, 45, 39), 21, "u16")
+    st = oracle.stats(vol)
+    t = dev(vol)
+    for roi in ((0, 0, 0, 77, 45, 39), (5, 3, 7, 33, 20, 11), (70, 40, 30, 7, 5, 9), (13, 0, 0, 1, 1, 1)):
+        x0, y0, z0, bx, by, bz = roi
+        for f in FILTERS:
+            prm = oracle.derive_params(st, 2)
+            got = host(ctx.filter_roi(t, f, 2, (x0, y0, z0), (bx, by, bz)))
+            want = oracle.filter_volume(vol, f, 2, params=prm, roi=roi)
+            assert_same(got, want, f"roi {roi} filter {f}")
+
+
+def test_entropy_call(ctx):
+    for vol in (phantoms.P1(), phantoms.random_volume((30, 20, 10), 4, "u16"), np.full((4, 4, 4), 9, np.uint8)):
+        H = ctx.entropy(dev(vol))
+        want = oracle.image_entropy(oracle.histogram(vol))
+        assert abs(H - want) <= H_TOL * max(1.0, want)
+
+
+def test_multi_host_buffers(ctx):
+    vol = phantoms.insect_phantom((48, 40, 33), 15, "u16")
+    st = oracle.stats(vol)
+    outs, H = ctx.filter_multi_host(vol, FILTERS, 2)
+    prm = oracle.derive_params(st, 2)
+    assert abs(H[0] - oracle.image_entropy(st.hist)) <= H_TOL * max(1, H[0])
+    for i, f in enumerate(FILTERS):
+        want = oracle.filter_volume(vol, f, 2, params=prm)
+        assert_same(outs[i], want, f"host multi filter {f}")
+        assert abs(H[i + 1] - oracle.image_entropy(oracle.histogram(want))) <= H_TOL * max(1, H[i + 1])
+
+
+def test_batched_mixed(lnf):
+    specs = phantoms.batch_volume_specs(n=6, seed=1000, lo=20, hi=60)
+    vols = [phantoms.batch_volume(s) for s in specs]
+    with lnf.Context(autotune=True) as c:
+        tv = [dev(v) for v in vols]
+        jobs, wants = [], []
+        Hs = torch.zeros(12, dtype=torch.float64, device="cuda")
+        k = 0
+        for s, v, t in zip(specs, vols, tv):
+            st = oracle.stats(v)
+            for f in (oracle.OURS, (k % 5)):
+                prm = oracle.derive_params(st, s["radius"])
+                roi = None
+                if k % 3 == 2:
+                    nz, ny, nx = v.shape
+                    roi = (1, 2, 3, nx // 2, ny // 3, nz // 2)
+                out = torch.empty((roi[5], roi[4], roi[3]) if roi else v.shape, dtype=t.dtype, device="cuda")
+                j = {"in": t, "out": out, "filter": f, "radius": s["radius"], "entropy": Hs[k:k + 1]}
+                if roi:
+                    j["roi_origin"], j["roi_dims"] = roi[:3], roi[3:]
+                jobs.append(j)
+                wants.append(oracle.filter_volume(v, f, s["radius"], params=prm, roi=roi))
+                k += 1
+        for rep in range(2):   # the second run replays the captured graph
+            for j in jobs:
+                j["out"].zero_()
+            c.filter_batch(jobs)
+            Hh = host(Hs)
+            for i, (j, w) in enumerate(zip(jobs, wants)):
+                assert_same(host(j["out"]), w, f"batch job {i} rep {rep}")
+                hw = oracle.image_entropy(oracle.histogram(w))
+                assert abs(Hh[i] - hw) <= H_TOL * max(1.0, hw), (i, Hh[i], hw)
+
+
+def test_invalid_arguments(ctx, lnf):
+    t = dev(np.zeros((4, 4, 4), np.uint8))
+    with pytest.raises(lnf.LnfError):
+        ctx.filter_volume(t, 5, 1)
+    with pytest.raises(lnf.LnfError):
+        ctx.filter_volume(t, 0, 9)
+    with pytest.raises(lnf.LnfError):
+        ctx.filter_volume(t, 0, -1)
+    with pytest.raises(lnf.LnfError):
+        ctx.filter_volume(t, 0, 1, out=t)       # in-place is rejected
+    with pytest.raises(lnf.LnfError):
+        ctx.filter_roi(t, 0, 1, (2, 2, 2), (3, 1, 1))
+
+
+# ----------------------------------------------------------------------------- full sizes
+
+def _sample_points(dims, n, seed):
+    nx, ny, nz = dims
+    rng = np.random.default_rng(seed)
+    corners = [(x, y, z) for x in (0, 1, nx - 2, nx - 1) for y in (0, ny - 1) for z in (0, 2, nz - 1)]
+    pts = np.stack([rng.integers(0, nx, n), rng.integers(0, ny, n), rng.integers(0, nz, n)], axis=1)
+    return np.concatenate([np.array(corners), pts]).astype(np.int64)
+
+
+def _check_sampled(vol, outs, filters, r, prm, seed):
+    nz, ny, nx = vol.shape
+    pts = _sample_points((nx, ny, nz), 3000, seed)
+    for f, o in zip(filters, outs):
+        want = oracle.filter_points(vol, f, r, pts, prm)
+        got = o[pts[:, 2], pts[:, 1], pts[:, 0]]
+        bad = np.nonzero(got != want)[0]
+        assert bad.size == 0, (f, pts[bad[:5]], got[bad[:5]], want[bad[:5]])
+
+
+def _check_hist_property(out, Hgot):
+    # the fused output histogram must be the histogram of the output
+    h = np.bincount(out.reshape(-1).astype(np.int64))
+    hw = oracle.image_entropy(h)
+    assert abs(Hgot - hw) <= H_TOL * max(1.0, hw)
+
+
+def test_full_512_u16_all_filters_r2(ctx):
+    """The 512^3 uint16 insect phantom, all five filters at radius 2, entropy of
+    input and outputs, in the launch configuration the benchmark times."""
+    vol = phantoms.P2()
+    st = oracle.stats(vol)
+    prm = oracle.derive_params(st, 2)
+    t = dev(vol)
+    outs, H = ctx.filter_multi(t, FILTERS, 2)
+    Hh = host(H)
+    p = ctx.params()
+    assert p["threshold"] == prm["T"] and p["sigma_band"] == prm["delta"] and p["okada_td"] == prm["td"]
+    assert abs(Hh[0] - oracle.image_entropy(st.hist)) <= H_TOL * Hh[0]
+    outs_h = [host(o) for o in outs]
+    _check_sampled(vol, outs_h, FILTERS, 2, prm, 5)
+    for o, h in zip(outs_h, Hh[1:]):
+        _check_hist_property(o, h)
+
+
+def test_full_1024_u8_ours_radius_sweep(ctx):
+    vol = phantoms.P3()
+    st = oracle.stats(vol)
+    t = dev(vol)
+    for r in (1, 2, 3, 4):
+        prm = oracle.derive_params(st, r)
+        outs, H = ctx.filter_multi(t, [oracle.OURS], r)
+        o = host(outs[0])
+        _check_sampled(vol, [o], [oracle.OURS], r, prm, 10 + r)
+        _check_hist_property(o, float(host(H)[1]))
+        del outs, o
+        torch.cuda.empty_cache()
