@@ -216,6 +216,10 @@ def main():
     ap.add_argument("--impl", default="lnf", choices=["lnf", "reference"])
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--mode", default="plain", choices=["plain", "batched", "served"],
+                    help="plain: the 512^3 five-filter step (default); batched / served: the delivery forms")
+    ap.add_argument("--duration", type=float, default=10.0, help="served: seconds of Poisson arrivals")
+    ap.add_argument("--rate", type=float, default=200.0, help="served: requests per second")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -228,6 +232,10 @@ def main():
         if rank == 0:
             run_reference(args)
         return
+    if args.mode == "batched":
+        return run_batched(args)
+    if args.mode == "served":
+        return run_served(args)
 
     import numpy as np
     import torch
@@ -360,6 +368,145 @@ def main():
     ctx.close()
     if world > 1:
         dist.destroy_process_group()
+
+
+# ----------------------------------------------------------------------------- delivery forms
+
+def run_batched(args):
+    """64 uneven volumes (96..384 per axis, half uint8 half uint16), the paper's
+    filter at r in {1, 2}: one persistent graph-captured launch (lnf_filter_batch)
+    against the per-volume launch loop (lnf_filter_volume per volume)."""
+    import torch
+    import phantoms
+    import paper_1807_03119_gb300 as lnf
+    from paper_1807_03119_gb300 import builder
+    builder.build()
+    lnf.load()
+    specs = phantoms.batch_volume_specs(64)
+    vols = [torch.from_numpy(phantoms.batch_volume(s)).cuda() for s in specs]
+    outs = [torch.empty_like(v) for v in vols]
+    nvox = sum(v.numel() for v in vols)
+    ctx = lnf.Context(autotune=True)
+    jobs = [{"in": v, "out": o, "filter": lnf.OURS, "radius": s["radius"]} for v, o, s in zip(vols, outs, specs)]
+
+    def batched():
+        ctx.filter_batch(jobs)
+
+    def loop():
+        for v, o, s in zip(vols, outs, specs):
+            ctx.filter_volume(v, lnf.OURS, s["radius"], out=o)
+
+    res = {}
+    for name, fn in (("batched", batched), ("loop", loop)):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.steps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / args.steps
+        res[name] = {"ms_per_batch": ms, "gvox_s": nvox / (ms / 1e3) / 1e9}
+    line = {"metric": "batched vs per-volume loop, GVoxel/s", "mode": "batched",
+            "value": res["batched"]["gvox_s"], "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "higher_is_better": True, "dtype": "u8+u16", "data": "synthetic",
+            "config": {"workload": "64 uneven volumes 96..384 per axis, half uint8 half uint16, paper's filter r in {1,2}",
+                       "voxels_per_batch": nvox},
+            "batched": res["batched"], "per_volume_loop": res["loop"],
+            "speedup": res["loop"]["ms_per_batch"] / res["batched"]["ms_per_batch"]}
+    print(json.dumps(line))
+    ctx.close()
+
+
+def run_served(args):
+    """8 resident uint16 volumes (128..768 per side), a Poisson request stream
+    (args.rate per second) of full-volume or ROI requests with random filter and
+    r in {1,2,3}, admitted under a 40 GiB budget: p50/p99 latency and throughput,
+    against serial plain calls on the same requests."""
+    import numpy as np
+    import torch
+    import phantoms
+    import paper_1807_03119_gb300 as lnf
+    from paper_1807_03119_gb300 import builder
+    builder.build()
+    lnf.load()
+    sizes = [int(np.random.default_rng(2000 + i).integers(128, 769)) for i in range(8)]
+    vols = [phantoms.insect_phantom((n, n, n), 2000 + i, "u16") for i, n in enumerate(sizes)]
+    rng = np.random.default_rng(42)
+    n_req = int(args.rate * args.duration)
+    gaps = rng.exponential(1.0 / args.rate, n_req)
+    reqs = []
+    for k in range(n_req):
+        vi = int(rng.integers(0, 8))
+        n = sizes[vi]
+        f = int(rng.integers(0, 5))
+        r = int(rng.integers(1, 4))
+        if rng.random() < 0.5:
+            reqs.append((vi, f, r, None))
+        else:
+            d = [int(rng.integers(32, min(256, n) + 1)) for _ in range(3)]
+            o = [int(rng.integers(0, n - d[a] + 1)) for a in range(3)]
+            reqs.append((vi, f, r, (o, d)))
+    ctx = lnf.Context(hbm_budget_bytes=40 << 30, max_inflight=64)
+    ids = [ctx.register_volume(torch.from_numpy(v).cuda()) for v in vols]
+    now = ctx.lib.lnf_now
+    # warm-up: one request per filter
+    for f in range(5):
+        t = ctx.submit(ids[0], f, 1)
+        ctx.wait(t)
+        ctx.release(t)
+    tickets = []
+    t0 = now()
+    t_next = t0
+    for k, (vi, f, r, roi) in enumerate(reqs):
+        t_next += gaps[k]
+        while now() < t_next:
+            pass
+        arr = now()
+        if roi:
+            tk = ctx.submit(ids[vi], f, r, roi_origin=roi[0], roi_dims=roi[1], arrival_time=arr)
+        else:
+            tk = ctx.submit(ids[vi], f, r, arrival_time=arr)
+        tickets.append((tk, arr))
+    lat = []
+    t_last = 0.0
+    vox = 0
+    for (tk, arr), (vi, f, r, roi) in zip(tickets, reqs):
+        res = ctx.wait(tk, 600.0)
+        lat.append(res.t_finish - arr)
+        t_last = max(t_last, res.t_finish)
+        vox += (np.prod(roi[1]) if roi else sizes[vi] ** 3)
+        ctx.release(tk)
+    served_s = t_last - t0
+    lat = np.array(lat) * 1e3
+    # serial plain calls on the same requests (device buffers, one sync per request)
+    dvols = [torch.from_numpy(v).cuda() for v in vols]
+    torch.cuda.synchronize()
+    ts = time.perf_counter()
+    for vi, f, r, roi in reqs:
+        if roi:
+            o = ctx.filter_roi(dvols[vi], f, r, tuple(roi[0]), tuple(roi[1]))
+        else:
+            o = ctx.filter_volume(dvols[vi], f, r)
+        torch.cuda.synchronize()
+        del o
+    serial_s = time.perf_counter() - ts
+    line = {"metric": "served p50/p99 ms and GVoxel/s vs serial plain calls", "mode": "served",
+            "value": vox / served_s / 1e9, "unit": UNIT, "n_gpus": 1, "higher_is_better": True,
+            "dtype": "u16", "data": "synthetic",
+            "config": {"workload": "8 resident uint16 volumes 128..768 per side, Poisson arrivals, "
+                                   "half full-volume half ROI 32..256, random filter, r in {1,2,3}, 40 GiB budget",
+                       "rate_per_s": args.rate, "duration_s": args.duration, "requests": n_req, "sizes": sizes},
+            "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                           "max": float(lat.max())},
+            "served": {"seconds": served_s, "gvox_s": vox / served_s / 1e9},
+            "serial_plain": {"seconds": serial_s, "gvox_s": vox / serial_s / 1e9},
+            "offered_gvox_s": vox / args.duration / 1e9}
+    print(json.dumps(line))
+    ctx.close()
 
 
 if __name__ == "__main__":
