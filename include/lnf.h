@@ -182,6 +182,29 @@ lnf_status lnf_entropy(lnf_ctx *ctx, const void *vol, const int64_t dims[3], int
  */
 lnf_status lnf_get_params(lnf_ctx *ctx, lnf_params *out, uint32_t *weights);
 
+/*
+ * Image entropy of a volume, like lnf_entropy, for callers that must not
+ * allocate device memory: no cudaMalloc, cudaFree or allocating library call
+ * is made, and no lnf_ctx is needed (creating one allocates).  Typical users:
+ * a render or acquisition loop that cannot take the device-wide stall an
+ * allocation can cause, or code running while another component owns all of
+ * the GPU's free memory.  The paper has no counterpart; it is a delivery
+ * variant of the histogram + entropy steps.
+ *   vol        device buffer of nx*ny*nz uint8/uint16 voxels (x-fastest)
+ *   d_entropy  DEVICE pointer to one double that receives H
+ *   stream     cudaStream_t the three kernels are enqueued on (NULL = default)
+ * Scratch: one file-scope device array of 65536 uint32 counters (256 KiB),
+ * present on every GPU that loads the library until the process exits.  The
+ * first call on a device (with that device current) looks up the array's
+ * address; make it before any stream capture.  Every call zeroes and reuses
+ * the same array, so calls that overlap on the GPU race: order them on one
+ * stream.  Returns LNF_EINVAL for null pointers, a bad dtype, dims < 1 or more
+ * than 2^32 - 1 voxels (the counters are 32-bit), LNF_ECUDA if a launch fails.
+ * Asynchronous: read *d_entropy after synchronising the stream.
+ */
+lnf_status lnf_entropy_noalloc(const void *vol, const int64_t dims[3], int dtype, double *d_entropy,
+                               void *stream);
+
 /* ------------------------------------------------------------------ batched */
 
 /* One filter job of a batch.  All pointers are device pointers. */
