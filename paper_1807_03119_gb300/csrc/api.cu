@@ -412,6 +412,25 @@ lnf_status lnf_make_job(lnf_ctx *ctx, FilterPack &pk, int idx, int filter, int r
     return LNF_OK;
 }
 
+// Encode a 3D TMA map of the volume with box {box_w, box_h, 1}; false when the
+// volume does not meet TMA's alignment rules or encoding fails.
+bool lnf_encode_box(lnf_ctx *ctx, const void *in, int nx, int ny, int nz, int dtype, unsigned box_w,
+                    unsigned box_h, CUtensorMap *map)
+{
+    const size_t es = esize(dtype);
+    if (!ctx->encode || ctx->no_tma || (reinterpret_cast<uintptr_t>(in) & 15) != 0 || ((size_t)nx * es) % 16 != 0 ||
+        box_w > 256 || box_h > 256 || (box_w * es) % 16 != 0)
+        return false;
+    cuuint64_t gdim[3] = {(cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)nz};
+    cuuint64_t gstr[2] = {(cuuint64_t)((size_t)nx * es), (cuuint64_t)((size_t)nx * ny * es)};
+    cuuint32_t box[3] = {box_w, box_h, 1};
+    cuuint32_t estr[3] = {1, 1, 1};
+    return ctx->encode(map, dtype == LNF_U8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_UINT16, 3,
+                       const_cast<void *>(in), gdim, gstr, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                       CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                       CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 // Assign item ranges and launch the generic kernel over the pack.
 lnf_status lnf_run_pack(lnf_ctx *ctx, FilterPack &pk, int persistent, cudaStream_t stream)
 {

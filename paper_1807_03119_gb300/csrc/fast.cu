@@ -1,14 +1,653 @@
-// Specialised filter kernels for the hot configurations (filled in below the
-// generic path; lnf_fast_dispatch routes a job to one when it covers it).
+// Specialised kernel for the paper's filter (Eq. 2-3) at radius 1..4 with the
+// diagonal clusters at distance sqrt(3) (offset d = 1), for whole volumes
+// whose row pitch allows TMA.  lnf_fast_dispatch routes such jobs here; every
+// other job goes to the generic kernel (filter.cu).
+//
+// Algebra (exact, integer): with the line sums Lx, Ly, Lz of M = 2r+1 voxels,
+//   G = Lx + Ly + Lz                       (the unnormalised cluster S at a voxel)
+//   U = G + T_x T_y T_z G                  (S_0 plus the eight diagonal clusters)
+// where T_a f(c) = f(c - e_a) + f(c + e_a).  With C = T_x T_y G,
+//   U(z) = G(z) + C(z-1) + C(z+1),
+// and the output is round(U / 27M), gated by P0 >= T and U >= 27M T.
+//
+// Mapping: a CTA owns a 128 x 32 output tile and marches along z over a chunk
+// of planes; the input planes (tile + halo) stream into a ring of shared
+// memory slots by TMA.  Each lane owns 4 consecutive columns of 4 rows.
+//   * z: Lz is a running sum held in registers (one term in, one out per
+//     step); the output needs two accumulators per voxel, A = G(z-1) + C(z-2)
+//     and B = C(z-1), so the z direction costs no shared memory at all.
+//   * y: Ly is a running sum along the lane's rows; the corner sum T_y needs
+//     the V = T_x G rows above and below, exchanged through shared memory
+//     between the warps of the CTA (the CTA's own edge rows are computed by
+//     its first and last warp).
+//   * x: Lx from the row words; T_x by warp shuffles, plus one extra column
+//     pair at each end of the warp (lanes 0 and 31).
+// Line sums are formed on packed pairs of 16-bit lanes (two voxels per 32-bit
+// add) whenever 3M * max <= 65535, which keeps every lane exact; otherwise
+// the same code runs on unpacked 32-bit pairs.
 #include "lnf_ctx.h"
+
+#include <algorithm>
+#include <cstring>
+
+namespace {
+
+constexpr int kWarps = 8;
+constexpr int kThreads = kWarps * 32;
+constexpr int kRows = 4;                  // rows per lane
+constexpr int kTX = 128;                  // 32 lanes x 4 columns
+constexpr int kTY = kWarps * kRows;       // 32
+constexpr int kPF = 2;                    // planes prefetched beyond the ones in use
+constexpr int kHistWin = 4096;
+
+__device__ __forceinline__ int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
+
+// ------------------------------------------------------------------ packed pairs
+
+// two adjacent voxels in the 16-bit lanes of one register (exact while every
+// final lane value stays within 0..65535)
+struct Narrow {
+    typedef u32 P;
+    static __device__ __forceinline__ P word(u32 w) { return w; }
+    static __device__ __forceinline__ P shift(P a, P b) { return __funnelshift_r(a, b, 16); }   // (a.hi, b.lo)
+    static __device__ __forceinline__ P add3(P a, P b, P c) { return a + b + c; }
+    static __device__ __forceinline__ P addsub(P a, P b, P c) { return a + b - c; }
+    static __device__ __forceinline__ P zero() { return 0u; }
+    static __device__ __forceinline__ u32 lo(P a) { return a & 0xFFFFu; }
+    static __device__ __forceinline__ u32 hi(P a) { return a >> 16; }
+};
+
+// the same pair unpacked into two 32-bit registers (any 16-bit data)
+struct Wide {
+    struct P {
+        u32 l, h;
+    };
+    static __device__ __forceinline__ P word(u32 w) { return P{w & 0xFFFFu, w >> 16}; }
+    static __device__ __forceinline__ P shift(P a, P b) { return P{a.h, b.l}; }
+    static __device__ __forceinline__ P add3(P a, P b, P c) { return P{a.l + b.l + c.l, a.h + b.h + c.h}; }
+    static __device__ __forceinline__ P addsub(P a, P b, P c) { return P{a.l + b.l - c.l, a.h + b.h - c.h}; }
+    static __device__ __forceinline__ P zero() { return P{0u, 0u}; }
+    static __device__ __forceinline__ u32 lo(P a) { return a.l; }
+    static __device__ __forceinline__ u32 hi(P a) { return a.h; }
+};
+
+// loads from a shared-memory row (byte pointer) at element column `col`
+template <typename T>
+struct Ld;
+
+template <>
+struct Ld<uint16_t> {
+    // columns col..col+3 as two words (col multiple of 4)
+    static __device__ __forceinline__ void quad(const unsigned char *row, int col, u32 &a, u32 &b)
+    {
+        const uint2 w = *reinterpret_cast<const uint2 *>(row + col * 2);
+        a = w.x;
+        b = w.y;
+    }
+    // columns col, col+1 as one word (col even)
+    static __device__ __forceinline__ u32 pair(const unsigned char *row, int col)
+    {
+        return *reinterpret_cast<const u32 *>(row + col * 2);
+    }
+};
+
+template <>
+struct Ld<uint8_t> {
+    static __device__ __forceinline__ void quad(const unsigned char *row, int col, u32 &a, u32 &b)
+    {
+        const u32 w = *reinterpret_cast<const u32 *>(row + col);
+        a = __byte_perm(w, 0u, 0x4140);
+        b = __byte_perm(w, 0u, 0x4342);
+    }
+    static __device__ __forceinline__ u32 pair(const unsigned char *row, int col)
+    {
+        const u32 w = *reinterpret_cast<const unsigned short *>(row + col);
+        return __byte_perm(w, 0u, 0x4140);
+    }
+};
+
+// ------------------------------------------------------------------ geometry
+
+template <typename T, int R>
+struct FGeo {
+    static constexpr int H = R + 1;                        // halo in y and z
+    static constexpr int XH = 16 / sizeof(T);              // x halo (16 bytes)
+    static constexpr int PW = kTX + 2 * XH;                // plane width (elements)
+    static constexpr int PH = kTY + 2 * H;                 // plane height
+    static constexpr int ROWB = PW * sizeof(T);            // row bytes (multiple of 16)
+    static constexpr int PBYTES = ((PW * PH * (int)sizeof(T)) + 127) / 128 * 128;
+    static constexpr int NP = 2 * R + 2 + kPF;             // ring slots
+    static constexpr int M = 2 * R + 1;
+    static constexpr int RING = NP * PBYTES;
+    static constexpr int XBUF = (2 * kWarps + 2) * kTX * 4;    // exchanged V rows
+    static constexpr int HIST = (sizeof(T) == 1 ? 256 : kHistWin) * 4;
+    static constexpr int SMEM = 128 + RING + XBUF + HIST + NP * 8 + 64;
+};
+
+// fix the out-of-volume cells of a freshly loaded plane by replicating the border
+template <typename T, int R>
+__device__ void fixup(unsigned char *pl, int px0, int py0, int nx, int ny)
+{
+    typedef FGeo<T, R> G;
+    T *p = reinterpret_cast<T *>(pl);
+    const int left = px0 < 0 ? min(-px0, G::PW) : 0;
+    const int right_start = max(0, min(G::PW, nx - px0));
+    const int ncol = left + (G::PW - right_start);
+    if (ncol > 0)
+        for (int e = threadIdx.x; e < ncol * G::PH; e += blockDim.x) {
+            const int row = e / ncol;
+            const int k = e - row * ncol;
+            const int col = k < left ? k : right_start + (k - left);
+            p[row * G::PW + col] = p[row * G::PW + clampi(px0 + col, 0, nx - 1) - px0];
+        }
+    __syncthreads();
+    const int top = py0 < 0 ? min(-py0, G::PH) : 0;
+    const int bot_start = max(0, min(G::PH, ny - py0));
+    const int nrow = top + (G::PH - bot_start);
+    if (nrow > 0)
+        for (int e = threadIdx.x; e < nrow * G::PW; e += blockDim.x) {
+            const int k = e / G::PW;
+            const int col = e - k * G::PW;
+            const int row = k < top ? k : bot_start + (k - top);
+            p[row * G::PW + col] = p[(clampi(py0 + row, 0, ny - 1) - py0) * G::PW + col];
+        }
+    __syncthreads();
+}
+
+// ------------------------------------------------------------------ per-row G
+
+__host__ __device__ constexpr int fl2(int o) { return o >= 0 ? o / 2 : -((-o + 1) / 2); }   // floor(o / 2)
+
+// sum over o = -R..R of the pair at column base+o, from the aligned words wd[k]
+// = pair at column base+2k (valid for k in [-(R+1)/2, (R+1)/2])
+template <int R, class PK>
+__device__ __forceinline__ typename PK::P window_sum(const typename PK::P *wd)
+{
+    typename PK::P acc = PK::zero();
+#pragma unroll
+    for (int o = -R; o <= R; o += 2) {
+        // two terms per add3: the pair at o and (if o < R) the one at o + 1
+        const typename PK::P t0 = (o & 1) == 0 ? wd[fl2(o)] : PK::shift(wd[fl2(o)], wd[fl2(o) + 1]);
+        if (o < R) {
+            const int o1 = o + 1;
+            const typename PK::P t1 =
+                (o1 & 1) == 0 ? wd[fl2(o1)] : PK::shift(wd[fl2(o1)], wd[fl2(o1) + 1]);
+            acc = PK::add3(acc, t0, t1);
+        } else {
+            acc = PK::add3(acc, t0, PK::zero());
+        }
+    }
+    return acc;
+}
+
+// Lx of the lane's pairs A (c0, c0+1), B (c0+2, c0+3) and of its edge pair E
+// (lane 0: c0-2; lane 31: c0+4; other lanes: a don't-care copy).
+template <typename T, int R, class PK>
+__device__ __forceinline__ void lx_pairs(const unsigned char *row, int c0, int lane,
+                                         typename PK::P &lxA, typename PK::P &lxB, typename PK::P &lxE)
+{
+    typedef typename PK::P P;
+    constexpr int A = (R + 1) / 2;
+    constexpr int JL = -A, JH = 1 + A;       // words every lane needs
+    P w[JH - JL + 3];                          // indices JL-1 .. JH+1
+    u32 q0, q1;
+    Ld<T>::quad(row, c0, q0, q1);
+    w[0 - JL + 1] = PK::word(q0);
+    w[1 - JL + 1] = PK::word(q1);
+#pragma unroll
+    for (int j = JL; j <= JH; ++j)
+        if (j != 0 && j != 1)
+            w[j - JL + 1] = PK::word(Ld<T>::pair(row, c0 + 2 * j));
+    const bool lane0 = lane == 0;
+    // the one outer word the edge lanes need
+    const P outer = PK::word(Ld<T>::pair(row, lane0 ? c0 + 2 * (JL - 1) : c0 + 2 * (JH + 1)));
+    w[0] = outer;
+    w[JH - JL + 2] = outer;
+    lxA = window_sum<R, PK>(&w[0 - JL + 1]);
+    lxB = window_sum<R, PK>(&w[1 - JL + 1]);
+    // E window: lane 0 around word -1, lane 31 around word 2 (same shape)
+    P ew[2 * A + 1];
+#pragma unroll
+    for (int k = -A; k <= A; ++k)
+        ew[k + A] = lane0 ? w[-1 + k - JL + 1] : w[2 + k - JL + 1];
+    lxE = window_sum<R, PK>(&ew[A]);
+}
+
+template <typename T, class PK>
+__device__ __forceinline__ void row_pairs(const unsigned char *row, int c0, int ce, typename PK::P &a,
+                                          typename PK::P &b, typename PK::P &e)
+{
+    u32 q0, q1;
+    Ld<T>::quad(row, c0, q0, q1);
+    a = PK::word(q0);
+    b = PK::word(q1);
+    e = PK::word(Ld<T>::pair(row, ce));
+}
+
+// ------------------------------------------------------------------ the kernel
+
+struct FastArgs {
+    const void *in;
+    void *out;
+    int nx, ny, nz;
+    int tiles_x, tiles_y, zchunks, zlen;
+    int total_items;
+    const DevParams *prm;
+    u64 *out_hist;
+    u32 *counter;
+    u32 *err;
+};
+
+template <typename T, int R, class PK>
+__device__ void ours_items(const FastArgs &a, const CUtensorMap *tmap, unsigned char *smem, int *s_item,
+                           int *s_abort, u32 &nonzero, u32 &written, u32 *hist, u32 hbase)
+{
+    using namespace lnfdev;
+    typedef FGeo<T, R> G;
+    typedef typename PK::P P;
+    unsigned char *ring = smem;
+    u32 *xbuf = reinterpret_cast<u32 *>(smem + G::RING);
+    u64 *bars = reinterpret_cast<u64 *>(smem + G::RING + G::XBUF + G::HIST);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const bool lane0 = lane == 0;
+    const int c0 = G::XH + 4 * lane;                                  // first own column (plane coords)
+    const int ce = lane0 ? G::XH - 2 : (lane == 31 ? G::XH + kTX : c0); // edge pair column
+    const int r0 = G::H + kRows * warp;                                // first own row (plane coords)
+    const u32 T_ = a.prm->T;
+    const u32 KT = 27u * G::M * T_;
+    constexpr u32 D2 = 54u * G::M, K = 27u * G::M;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < G::NP; ++s)
+            mbar_init(&bars[s], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    u32 uses[G::NP];   // completed phases per slot (same in every thread)
+#pragma unroll
+    for (int s = 0; s < G::NP; ++s)
+        uses[s] = 0;
+
+    for (;;) {
+        if (threadIdx.x == 0)
+            *s_item = (int)atomicAdd(a.counter, 1u);
+        __syncthreads();
+        const int item = *s_item;
+        __syncthreads();
+        if (item >= a.total_items || *s_abort)
+            break;
+        const int tx = item % a.tiles_x;
+        const int rest = item / a.tiles_x;
+        const int ty = rest % a.tiles_y;
+        const int zc = rest / a.tiles_y;
+        const int x0 = tx * kTX, y0 = ty * kTY;
+        const int z0 = zc * a.zlen, z1 = min(a.nz, z0 + a.zlen);
+        const int px0 = x0 - G::XH, py0 = y0 - G::H;
+        const bool border = px0 < 0 || px0 + G::PW > a.nx || py0 < 0 || py0 + G::PH > a.ny;
+        // plane p <-> z = z0 - 1 - R + p; G planes g = z0-1 .. z1 (steps s = 0 .. z1-z0+1)
+        const int nplanes = (z1 - z0 + 2) + 2 * R;
+        const int nsteps = z1 - z0 + 2;
+        const u32 pbytes = G::PW * G::PH * sizeof(T);
+
+        auto issue = [&](int p) {   // thread 0 only
+            const int slot = p % G::NP;
+            fence_proxy_async_smem();
+            mbar_arrive_expect_tx(&bars[slot], pbytes);
+            tma_load_3d(ring + slot * G::PBYTES, tmap, &bars[slot], px0, py0, clampi(z0 - 1 - R + p, 0, a.nz - 1));
+        };
+        if (threadIdx.x == 0)
+            for (int p = 0; p < min(G::NP, nplanes); ++p)
+                issue(p);
+        // per-slot phase of the plane p: uses[slot] counts completed waits of that slot
+        auto wait_plane = [&](int p) -> bool {
+            const int slot = p % G::NP;
+            const bool ok = mbar_wait_bounded(&bars[slot], uses[slot] & 1u, a.err);
+            uses[slot] += 1;
+            return ok;
+        };
+
+        // per-thread state
+        P lzA[kRows], lzB[kRows], lzE[kRows], lzxA, lzxB, lzxE;   // running z line sums
+        u32 accA[kRows][4], accB[kRows][4];                         // z accumulators
+        const bool has_extra = warp == 0 || warp == kWarps - 1;
+        const int rx = warp == 0 ? r0 - 1 : r0 + kRows;             // extra row (CTA edge)
+        bool ok = true;
+
+        for (int s = 0; s < nsteps; ++s) {
+            // planes needed: s-1 (old) .. s+2R (new)
+            const int pfirst = s == 0 ? 0 : s + 2 * R;
+            for (int p = pfirst; p <= s + 2 * R; ++p)
+                if (!wait_plane(p))
+                    *s_abort = 1;
+            __syncthreads();
+            if (*s_abort) {
+                ok = false;
+                break;
+            }
+            if (border)
+                for (int p = pfirst; p <= s + 2 * R; ++p)
+                    fixup<T, R>(ring + (p % G::NP) * G::PBYTES, px0, py0, a.nx, a.ny);
+            const unsigned char *pg = ring + ((s + R) % G::NP) * G::PBYTES;   // G plane g = z0-1+s
+            const unsigned char *pn = ring + ((s + 2 * R) % G::NP) * G::PBYTES;
+            const unsigned char *po = ring + (((s + G::NP - 1) % G::NP)) * G::PBYTES;
+
+            // ---- Lz: initialise at the first step, then one plane in, one out
+            if (s == 0) {
+#pragma unroll
+                for (int i = 0; i < kRows; ++i) {
+                    lzA[i] = PK::zero();
+                    lzB[i] = PK::zero();
+                    lzE[i] = PK::zero();
+                }
+                lzxA = lzxB = lzxE = PK::zero();
+#pragma unroll
+                for (int d = 0; d <= 2 * R; ++d) {
+                    const unsigned char *pl = ring + (d % G::NP) * G::PBYTES;
+#pragma unroll
+                    for (int i = 0; i < kRows; ++i) {
+                        P qa, qb, qe;
+                        row_pairs<T, PK>(pl + (r0 + i) * G::ROWB, c0, ce, qa, qb, qe);
+                        lzA[i] = PK::add3(lzA[i], qa, PK::zero());
+                        lzB[i] = PK::add3(lzB[i], qb, PK::zero());
+                        lzE[i] = PK::add3(lzE[i], qe, PK::zero());
+                    }
+                    if (has_extra) {
+                        P qa, qb, qe;
+                        row_pairs<T, PK>(pl + rx * G::ROWB, c0, ce, qa, qb, qe);
+                        lzxA = PK::add3(lzxA, qa, PK::zero());
+                        lzxB = PK::add3(lzxB, qb, PK::zero());
+                        lzxE = PK::add3(lzxE, qe, PK::zero());
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int i = 0; i < kRows; ++i) {
+                    P na, nb, ne, oa, ob, oe;
+                    row_pairs<T, PK>(pn + (r0 + i) * G::ROWB, c0, ce, na, nb, ne);
+                    row_pairs<T, PK>(po + (r0 + i) * G::ROWB, c0, ce, oa, ob, oe);
+                    lzA[i] = PK::addsub(lzA[i], na, oa);
+                    lzB[i] = PK::addsub(lzB[i], nb, ob);
+                    lzE[i] = PK::addsub(lzE[i], ne, oe);
+                }
+                if (has_extra) {
+                    P na, nb, ne, oa, ob, oe;
+                    row_pairs<T, PK>(pn + rx * G::ROWB, c0, ce, na, nb, ne);
+                    row_pairs<T, PK>(po + rx * G::ROWB, c0, ce, oa, ob, oe);
+                    lzxA = PK::addsub(lzxA, na, oa);
+                    lzxB = PK::addsub(lzxB, nb, ob);
+                    lzxE = PK::addsub(lzxE, ne, oe);
+                }
+            }
+
+            // ---- G and V = T_x G for the own rows (and the CTA edge row)
+            u32 g[kRows][4], v[kRows][4];
+            P lyA = PK::zero(), lyB = PK::zero(), lyE = PK::zero();
+#pragma unroll
+            for (int d = -R; d <= R; ++d) {
+                P qa, qb, qe;
+                row_pairs<T, PK>(pg + (r0 + d) * G::ROWB, c0, ce, qa, qb, qe);
+                lyA = PK::add3(lyA, qa, PK::zero());
+                lyB = PK::add3(lyB, qb, PK::zero());
+                lyE = PK::add3(lyE, qe, PK::zero());
+            }
+#pragma unroll
+            for (int i = 0; i < kRows; ++i) {
+                if (i > 0) {
+                    P na, nb, ne, oa, ob, oe;
+                    row_pairs<T, PK>(pg + (r0 + i + R) * G::ROWB, c0, ce, na, nb, ne);
+                    row_pairs<T, PK>(pg + (r0 + i - R - 1) * G::ROWB, c0, ce, oa, ob, oe);
+                    lyA = PK::addsub(lyA, na, oa);
+                    lyB = PK::addsub(lyB, nb, ob);
+                    lyE = PK::addsub(lyE, ne, oe);
+                }
+                P lxA, lxB, lxE;
+                lx_pairs<T, R, PK>(pg + (r0 + i) * G::ROWB, c0, lane, lxA, lxB, lxE);
+                const P gA = PK::add3(lxA, lyA, lzA[i]);
+                const P gB = PK::add3(lxB, lyB, lzB[i]);
+                const P gE = PK::add3(lxE, lyE, lzE[i]);
+                g[i][0] = PK::lo(gA);
+                g[i][1] = PK::hi(gA);
+                g[i][2] = PK::lo(gB);
+                g[i][3] = PK::hi(gB);
+                const u32 ge = lane0 ? PK::hi(gE) : PK::lo(gE);
+                const u32 gl = __shfl_up_sync(0xFFFFFFFFu, g[i][3], 1);
+                const u32 gr = __shfl_down_sync(0xFFFFFFFFu, g[i][0], 1);
+                v[i][0] = (lane0 ? ge : gl) + g[i][1];
+                v[i][1] = g[i][0] + g[i][2];
+                v[i][2] = g[i][1] + g[i][3];
+                v[i][3] = g[i][2] + (lane == 31 ? ge : gr);
+            }
+            if (has_extra) {   // warp-uniform
+                P lyxA = PK::zero(), lyxB = PK::zero(), lyxE = PK::zero();
+#pragma unroll
+                for (int d = -R; d <= R; ++d) {
+                    P qa, qb, qe;
+                    row_pairs<T, PK>(pg + (rx + d) * G::ROWB, c0, ce, qa, qb, qe);
+                    lyxA = PK::add3(lyxA, qa, PK::zero());
+                    lyxB = PK::add3(lyxB, qb, PK::zero());
+                    lyxE = PK::add3(lyxE, qe, PK::zero());
+                }
+                P lxA, lxB, lxE;
+                lx_pairs<T, R, PK>(pg + rx * G::ROWB, c0, lane, lxA, lxB, lxE);
+                const P gA = PK::add3(lxA, lyxA, lzxA);
+                const P gB = PK::add3(lxB, lyxB, lzxB);
+                const P gE = PK::add3(lxE, lyxE, lzxE);
+                const u32 x0v = PK::lo(gA), x1v = PK::hi(gA), x2v = PK::lo(gB), x3v = PK::hi(gB);
+                const u32 ge = lane0 ? PK::hi(gE) : PK::lo(gE);
+                const u32 gl = __shfl_up_sync(0xFFFFFFFFu, x3v, 1);
+                const u32 gr = __shfl_down_sync(0xFFFFFFFFu, x0v, 1);
+                uint4 vx;
+                vx.x = (lane0 ? ge : gl) + x1v;
+                vx.y = x0v + x2v;
+                vx.z = x1v + x3v;
+                vx.w = x2v + (lane == 31 ? ge : gr);
+                const int slot = warp == 0 ? 2 * kWarps : 2 * kWarps + 1;
+                reinterpret_cast<uint4 *>(xbuf + slot * kTX)[lane] = vx;
+            }
+            reinterpret_cast<uint4 *>(xbuf + (2 * warp) * kTX)[lane] = make_uint4(v[0][0], v[0][1], v[0][2], v[0][3]);
+            reinterpret_cast<uint4 *>(xbuf + (2 * warp + 1) * kTX)[lane] =
+                make_uint4(v[kRows - 1][0], v[kRows - 1][1], v[kRows - 1][2], v[kRows - 1][3]);
+            __syncthreads();
+            const int up_slot = warp == 0 ? 2 * kWarps : 2 * (warp - 1) + 1;
+            const int dn_slot = warp == kWarps - 1 ? 2 * kWarps + 1 : 2 * (warp + 1);
+            const uint4 vu = reinterpret_cast<const uint4 *>(xbuf + up_slot * kTX)[lane];
+            const uint4 vd = reinterpret_cast<const uint4 *>(xbuf + dn_slot * kTX)[lane];
+
+            // ---- C = T_y V; outputs at z = g - 1 once three G planes exist
+            const int zout = z0 - 2 + s;   // = g - 1
+            const bool emit = s >= 2;
+            const unsigned char *pc = ring + ((s + R - 1) % G::NP) * G::PBYTES;   // plane z = g - 1
+#pragma unroll
+            for (int i = 0; i < kRows; ++i) {
+                u32 c[4];
+                const u32 up[4] = {vu.x, vu.y, vu.z, vu.w};
+                const u32 dn[4] = {vd.x, vd.y, vd.z, vd.w};
+#pragma unroll
+                for (int k = 0; k < 4; ++k)
+                    c[k] = (i == 0 ? up[k] : v[i - 1][k]) + (i == kRows - 1 ? dn[k] : v[i + 1][k]);
+                if (emit) {
+                    const int y = y0 + kRows * warp + i;
+                    const int x = x0 + 4 * lane;
+                    u32 q0, q1;
+                    Ld<T>::quad(pc + (r0 + i) * G::ROWB, c0, q0, q1);
+                    const u32 p0[4] = {q0 & 0xFFFFu, q0 >> 16, q1 & 0xFFFFu, q1 >> 16};
+                    u32 f[4];
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        const u32 U = accA[i][k] + c[k];
+                        f[k] = (p0[k] >= T_ && U >= KT) ? (2u * U + K) / D2 : 0u;
+                    }
+                    if (y < a.ny && x < a.nx) {
+                        const size_t o = ((size_t)zout * a.ny + y) * a.nx + x;
+                        if (sizeof(T) == 2) {
+                            *reinterpret_cast<uint2 *>(static_cast<uint16_t *>(a.out) + o) =
+                                make_uint2(f[0] | (f[1] << 16), f[2] | (f[3] << 16));
+                        } else {
+                            *reinterpret_cast<u32 *>(static_cast<uint8_t *>(a.out) + o) =
+                                f[0] | (f[1] << 8) | (f[2] << 16) | (f[3] << 24);
+                        }
+                        written += 4;
+                        if (hist) {
+                            const bool nz = (f[0] | f[1] | f[2] | f[3]) != 0;
+                            if (__any_sync(__activemask(), nz)) {
+#pragma unroll
+                                for (int k = 0; k < 4; ++k)
+                                    if (f[k]) {
+                                        ++nonzero;
+                                        const u32 bin = f[k] - hbase;
+                                        if (bin < (u32)(sizeof(T) == 1 ? 256 : kHistWin))
+                                            atomicAdd(&hist[bin], 1u);
+                                        else
+                                            atomicAdd(&a.out_hist[f[k]], 1ull);
+                                    }
+                            }
+                        }
+                    }
+                }
+                // advance the z accumulators: A <- B + G(g), B <- C(g)
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    accA[i][k] = (s == 0 ? 0u : accB[i][k]) + g[i][k];
+                    accB[i][k] = c[k];
+                }
+            }
+            __syncthreads();   // every thread is done with plane s-1 and the exchange rows
+            if (threadIdx.x == 0 && s >= 1 && s - 1 + G::NP < nplanes)
+                issue(s - 1 + G::NP);
+        }
+        if (!ok) {
+            if (threadIdx.x == 0) {
+                const u64 t0 = global_ns();
+                while (global_ns() - t0 < 2000000ull) {
+                }
+            }
+            __syncthreads();
+            break;
+        }
+        // all issued planes were waited for; re-arm the barriers for the next item
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            for (int sl = 0; sl < G::NP; ++sl) {
+                mbar_inval(&bars[sl]);
+                mbar_init(&bars[sl], 1);
+            }
+            fence_mbar_init();
+        }
+#pragma unroll
+        for (int sl = 0; sl < G::NP; ++sl)
+            uses[sl] = 0;
+        __syncthreads();
+    }
+}
+
+template <typename T, int R>
+__global__ void __launch_bounds__(kThreads, 2) k_ours_fast(const __grid_constant__ CUtensorMap tmap, const FastArgs a)
+{
+    typedef FGeo<T, R> G;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    unsigned char *smem = smem_raw + ((128 - (lnfdev::smem_u32(smem_raw) & 127)) & 127);
+    __shared__ int s_item, s_abort;
+    u32 *hist = reinterpret_cast<u32 *>(smem + G::RING + G::XBUF);
+    constexpr int bins = sizeof(T) == 1 ? 256 : kHistWin;
+    for (int i = threadIdx.x; i < bins; i += blockDim.x)
+        hist[i] = 0;
+    if (threadIdx.x == 0)
+        s_abort = 0;
+    __syncthreads();
+    const u32 hbase = sizeof(T) == 1 ? 0u : a.prm->minv;
+    u32 nonzero = 0, written = 0;
+    const u32 M = 2 * R + 1;
+    const bool narrow = 3u * M * a.prm->maxv <= 65535u;
+    if (narrow)
+        ours_items<T, R, Narrow>(a, &tmap, smem, &s_item, &s_abort, nonzero, written, a.out_hist ? hist : nullptr,
+                                 hbase);
+    else
+        ours_items<T, R, Wide>(a, &tmap, smem, &s_item, &s_abort, nonzero, written, a.out_hist ? hist : nullptr,
+                               hbase);
+    if (a.out_hist) {
+        __syncthreads();
+        for (int i = threadIdx.x; i < bins; i += blockDim.x)
+            if (hist[i])
+                atomicAdd(&a.out_hist[hbase + i], (u64)hist[i]);
+        // zero outputs = outputs written - nonzero outputs
+        u32 zeros = written - nonzero;
+        for (int o = 16; o > 0; o >>= 1)
+            zeros += __shfl_xor_sync(0xFFFFFFFFu, zeros, o);
+        if ((threadIdx.x & 31) == 0 && zeros)
+            atomicAdd(&a.out_hist[0], (u64)zeros);
+    }
+}
+
+template <typename T, int R>
+lnf_status launch(lnf_ctx *ctx, const FilterJob &j, cudaStream_t st, u64 *out_hist, int *handled)
+{
+    typedef FGeo<T, R> G;
+    // this kernel's own descriptor: box = its tile + halo
+    CUtensorMap map;
+    if (!lnf_encode_box(ctx, j.in, j.nx, j.ny, j.nz, j.dtype, G::PW, G::PH, &map))
+        return LNF_OK;   // not handled: the generic kernel runs instead
+    const CUtensorMap *tmap = &map;
+    FastArgs a;
+    std::memset(&a, 0, sizeof a);
+    a.in = j.in;
+    a.out = j.out;
+    a.nx = j.nx;
+    a.ny = j.ny;
+    a.nz = j.nz;
+    a.tiles_x = (j.nx + kTX - 1) / kTX;
+    a.tiles_y = (j.ny + kTY - 1) / kTY;
+    a.zlen = ctx->fast_zlen > 0 ? ctx->fast_zlen : 16;
+    a.zchunks = (j.nz + a.zlen - 1) / a.zlen;
+    a.total_items = a.tiles_x * a.tiles_y * a.zchunks;
+    a.prm = j.prm;
+    a.out_hist = out_hist;
+    a.counter = ctx->d_counter + 8;
+    a.err = ctx->d_err;
+    if (cudaFuncSetAttribute(k_ours_fast<T, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, G::SMEM) != cudaSuccess)
+        return lnf_fail(ctx, LNF_ECUDA, "fast kernel: shared memory attribute");
+    int occ = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_ours_fast<T, R>, kThreads, G::SMEM);
+    if (occ < 1)
+        occ = 1;
+    const int grid = std::min(a.total_items, ctx->num_sms * occ);
+    if (cudaMemsetAsync(a.counter, 0, sizeof(u32), st) != cudaSuccess)
+        return lnf_fail(ctx, LNF_ECUDA, "fast kernel: counter reset");
+    k_ours_fast<T, R><<<grid, kThreads, G::SMEM, st>>>(*tmap, a);
+    if (cudaGetLastError() != cudaSuccess)
+        return lnf_fail(ctx, LNF_ECUDA, "fast kernel launch failed");
+    *handled = 1;
+    return LNF_OK;
+}
+
+}  // namespace
 
 lnf_status lnf_fast_dispatch(lnf_ctx *ctx, const FilterJob &job, const CUtensorMap *tmap, cudaStream_t stream,
                              int *handled)
 {
-    (void)ctx;
-    (void)job;
-    (void)tmap;
-    (void)stream;
     *handled = 0;
-    return LNF_OK;
+    if (job.filter != LNF_OURS)
+        return lnf_fast2_dispatch(ctx, job, tmap, stream, handled);
+    if (!tmap || job.offset != 1 || job.radius < 1 || job.radius > 4)
+        return LNF_OK;
+    if (job.ox || job.oy || job.oz || job.bx != job.nx || job.by != job.ny || job.bz != job.nz)
+        return LNF_OK;
+    lnf_status s = LNF_OK;
+    u64 *oh = job.out_hist;
+    if (job.dtype == LNF_U8) {
+        switch (job.radius) {
+        case 1: s = launch<uint8_t, 1>(ctx, job, stream, oh, handled); break;
+        case 2: s = launch<uint8_t, 2>(ctx, job, stream, oh, handled); break;
+        case 3: s = launch<uint8_t, 3>(ctx, job, stream, oh, handled); break;
+        default: s = launch<uint8_t, 4>(ctx, job, stream, oh, handled); break;
+        }
+    } else {
+        switch (job.radius) {
+        case 1: s = launch<uint16_t, 1>(ctx, job, stream, oh, handled); break;
+        case 2: s = launch<uint16_t, 2>(ctx, job, stream, oh, handled); break;
+        case 3: s = launch<uint16_t, 3>(ctx, job, stream, oh, handled); break;
+        default: s = launch<uint16_t, 4>(ctx, job, stream, oh, handled); break;
+        }
+    }
+    return s;
 }

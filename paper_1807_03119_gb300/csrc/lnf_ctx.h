@@ -26,7 +26,9 @@ struct VolScratch {
     u32 *lut = nullptr;
 };
 
-struct BatchEntry;      // batch.cu
+struct BatchEntry;      lnf_status lnf_fast2_dispatch(lnf_ctx *ctx, const FilterJob &job, const CUtensorMap *tmap, cudaStream_t stream,
+                              int *handled);
+// batch.cu
 struct Server;          // serve.cu
 
 struct lnf_ctx {
@@ -34,7 +36,8 @@ struct lnf_ctx {
     cudaStream_t stream = nullptr;
     int device = 0;
     int num_sms = 1;
-    int zchunk = 64;            // z chunk length of a work item
+    int zchunk = 64;            // z chunk length of a work item (generic kernel)
+    int fast_zlen = 16;         // z chunk length of a work item (specialised kernels)
     bool no_tma = false;        // testing: force plain loads
     bool no_fast = false;       // testing: force the generic kernel
     VolScratch vs;              // scratch of plain calls
@@ -78,6 +81,8 @@ lnf_status lnf_analyze(lnf_ctx *ctx, const void *in, const int64_t dims[3], int 
 lnf_status lnf_make_job(lnf_ctx *ctx, FilterPack &pk, int idx, int filter, int radius, const void *in, void *out,
                         const int64_t dims[3], int dtype, const int64_t *roi_o, const int64_t *roi_d,
                         const VolScratch &vs, u64 *out_hist);
+bool lnf_encode_box(lnf_ctx *ctx, const void *in, int nx, int ny, int nz, int dtype, unsigned box_w,
+                    unsigned box_h, CUtensorMap *map);
 lnf_status lnf_run_pack(lnf_ctx *ctx, FilterPack &pk, int persistent, cudaStream_t stream);
 lnf_status lnf_run_pack_counter(lnf_ctx *ctx, FilterPack &pk, int persistent, cudaStream_t stream, u32 *counter);
 lnf_status lnf_run_one(lnf_ctx *ctx, int filter, int radius, const void *in, void *out, const int64_t dims[3],
@@ -89,6 +94,8 @@ void lnf_prof_end(lnf_ctx *ctx, int rec, const char *name, cudaStream_t st, int 
 // fast.cu: run the job through a specialised kernel if one covers it (*handled = 1)
 lnf_status lnf_fast_dispatch(lnf_ctx *ctx, const FilterJob &job, const CUtensorMap *tmap, cudaStream_t stream,
                              int *handled);
+lnf_status lnf_fast2_dispatch(lnf_ctx *ctx, const FilterJob &job, const CUtensorMap *tmap, cudaStream_t stream,
+                              int *handled);
 // batch.cu
 void lnf_batch_cache_clear(lnf_ctx *ctx);
 // serve.cu

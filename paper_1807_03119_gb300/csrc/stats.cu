@@ -106,18 +106,30 @@ __device__ void stats_body(const T *vol, u64 n, u64 *hist, DevStats *st, u64 cta
         stats_value<T>(vol[i], sh, hist, a);
     const uint4 *v4 = reinterpret_cast<const uint4 *>(vol + head);
     const u64 nv = (n - head) * sizeof(T) / 16;
-    for (u64 i = gtid; i < nv; i += gsz) {
-        uint4 w = __ldcs(v4 + i);   // streamed once: do not keep in L2
-        u32 words[4] = {w.x, w.y, w.z, w.w};
+    // four independent 16-byte loads in flight per thread before any is consumed
+    constexpr int kU = 4;
+    for (u64 i = gtid; i < nv; i += kU * gsz) {
+        uint4 w[kU];
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            if (sizeof(T) == 1) {
+        for (int u = 0; u < kU; ++u) {
+            const u64 j = i + u * gsz;
+            w[u] = j < nv ? __ldcs(v4 + j) : make_uint4(0, 0, 0, 0);
+        }
 #pragma unroll
-                for (int b = 0; b < 4; ++b)
-                    stats_value<T>((words[k] >> (8 * b)) & 0xFFu, sh, hist, a);
-            } else {
-                stats_value<T>(words[k] & 0xFFFFu, sh, hist, a);
-                stats_value<T>(words[k] >> 16, sh, hist, a);
+        for (int u = 0; u < kU; ++u) {
+            if (i + u * gsz >= nv)
+                break;
+            const u32 words[4] = {w[u].x, w[u].y, w[u].z, w[u].w};
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                if (sizeof(T) == 1) {
+#pragma unroll
+                    for (int b = 0; b < 4; ++b)
+                        stats_value<T>((words[k] >> (8 * b)) & 0xFFu, sh, hist, a);
+                } else {
+                    stats_value<T>(words[k] & 0xFFFFu, sh, hist, a);
+                    stats_value<T>(words[k] >> 16, sh, hist, a);
+                }
             }
         }
     }

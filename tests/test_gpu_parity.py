@@ -33,6 +33,7 @@ def lnf():
 def ctx(lnf):
     c = lnf.Context()
     yield c
+    c.params()   # raises LNF_ETIMEOUT if any bounded device wait gave up during the module
     c.close()
 
 
@@ -338,3 +339,33 @@ def test_full_1024_u8_ours_radius_sweep(ctx):
         _check_hist_property(o, float(host(H)[1]))
         del outs, o
         torch.cuda.empty_cache()
+
+
+# ----------------------------------------------------------------------------- specialised kernels
+
+FAST_CASES = [
+    ((272, 72, 40), "u16", "narrow"),   # 3 x-tiles and 3 y-tiles (ragged), 3 z chunks
+    ((272, 72, 40), "u16", "wide"),     # full 16-bit range: unpacked pairs
+    ((288, 40, 33), "u8", "narrow"),
+    ((128, 32, 17), "u16", "narrow"),   # exactly one tile
+    ((16, 8, 5), "u16", "wide"),        # smaller than a tile in every direction
+    ((32, 130, 7), "u8", "narrow"),
+]
+
+
+@pytest.mark.parametrize("dims,dt,kind", FAST_CASES)
+def test_fast_ours_matches_oracle(ctx, dims, dt, kind):
+    if kind == "narrow":
+        vol = (phantoms.insect_phantom(dims, 41, dt) if dt == "u16"
+               else phantoms.ellipsoid_phantom(dims, 41, dt))
+    else:
+        vol = phantoms.random_volume(dims, 42, dt, p_extreme=0.2)
+    st = oracle.stats(vol)
+    t = dev(vol)
+    for r in (1, 2, 3, 4):
+        prm = oracle.derive_params(st, r)
+        outs, H = ctx.filter_multi(t, [oracle.OURS], r)
+        want = oracle.filter_volume(vol, oracle.OURS, r, params=prm)
+        assert_same(host(outs[0]), want, f"fast ours r={r} {dims} {dt} {kind}")
+        hw = oracle.image_entropy(oracle.histogram(want))
+        assert abs(float(host(H)[1]) - hw) <= H_TOL * max(1.0, hw)
