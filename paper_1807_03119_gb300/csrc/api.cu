@@ -112,7 +112,9 @@ static lnf_status alloc_scratch(lnf_ctx *ctx, VolScratch &vs)
     CK(cudaMalloc(&vs.st, sizeof(DevStats)));
     CK(cudaMalloc(&vs.prm, sizeof(DevParams)));
     CK(cudaMalloc(&vs.lut, sizeof(u32) * LNF_LEVELS_U16));
+    CK(cudaMalloc(&vs.pscr, lnf_param_scratch_bytes()));
     CK(cudaMemset(vs.prm, 0, sizeof(DevParams)));
+    CK(cudaMemset(vs.pscr, 0, lnf_param_scratch_bytes()));
     return LNF_OK;
 }
 
@@ -122,6 +124,7 @@ static void free_scratch(VolScratch &vs)
     cudaFree(vs.st);
     cudaFree(vs.prm);
     cudaFree(vs.lut);
+    cudaFree(vs.pscr);
     vs = VolScratch{};
 }
 
@@ -176,12 +179,15 @@ extern "C" lnf_status lnf_create(const lnf_config *cfg_in, lnf_ctx **out)
         if (cudaMalloc(&ctx->out_hist, sizeof(u64) * LNF_LEVELS_U16 * LNF_MAX_PACK) != cudaSuccess ||
             cudaMalloc(&ctx->d_H, sizeof(double) * (LNF_MAX_PACK + 1)) != cudaSuccess ||
             cudaMalloc(&ctx->d_err, sizeof(u32)) != cudaSuccess ||
-            cudaMalloc(&ctx->d_counter, sizeof(u32) * 16) != cudaSuccess) {
+            cudaMalloc(&ctx->d_counter, sizeof(u32) * 16) != cudaSuccess ||
+            cudaMalloc(&ctx->d_ent_part, sizeof(double) * LNF_ENT_SPLIT * LNF_MAX_ENT) != cudaSuccess ||
+            cudaMalloc(&ctx->d_ent_done, sizeof(u32) * LNF_MAX_ENT) != cudaSuccess) {
             s = LNF_ENOMEM;
             break;
         }
         cudaMemset(ctx->d_err, 0, sizeof(u32));
         cudaMemset(ctx->d_counter, 0, sizeof(u32) * 16);
+        cudaMemset(ctx->d_ent_done, 0, sizeof(u32) * LNF_MAX_ENT);
         void *fn = nullptr;
         cudaDriverEntryPointQueryResult q;
         if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) ==
@@ -221,6 +227,8 @@ extern "C" void lnf_destroy(lnf_ctx *ctx)
     cudaFree(ctx->d_H);
     cudaFree(ctx->d_err);
     cudaFree(ctx->d_counter);
+    cudaFree(ctx->d_ent_part);
+    cudaFree(ctx->d_ent_done);
     cudaFree(ctx->st_in);
     for (void *p : ctx->st_out)
         cudaFree(p);
@@ -353,7 +361,7 @@ lnf_status lnf_analyze(lnf_ctx *ctx, const void *in, const int64_t dims[3], int 
     CK(lnf_launch_stats(in, n, dtype, vs.hist, vs.st, ctx->num_sms, stream));
     lnf_prof_end(ctx, rec, "stats", stream, 1);
     rec = lnf_prof_begin(ctx, stream);
-    CK(lnf_launch_params(vs.hist, vs.st, lnf_param_cfg(ctx->cfg), vs.prm, vs.lut, stream));
+    CK(lnf_launch_params(vs.hist, vs.st, lnf_param_cfg(ctx->cfg), vs.prm, vs.lut, vs.pscr, dtype, stream));
     lnf_prof_end(ctx, rec, "params", stream, 1);
     return LNF_OK;
 }
@@ -575,7 +583,7 @@ extern "C" lnf_status lnf_filter_multi(lnf_ctx *ctx, int radius, const void *in,
             ep.levels[i] = levels;
         }
         const int rec = lnf_prof_begin(ctx, st);
-        CK(lnf_launch_entropy_pack(ep, st));
+        CK(lnf_launch_entropy_pack(ep, ctx->d_ent_part, ctx->d_ent_done, st));
         lnf_prof_end(ctx, rec, "entropy", st, 1);
     }
     return LNF_OK;

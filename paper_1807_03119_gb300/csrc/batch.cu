@@ -98,6 +98,7 @@ lnf_status lnf_enqueue_batch(lnf_ctx *ctx, const lnf_job *jobs, int n, int zchun
         sj.st = ctx->pool[v].st;
         sj.prm = ctx->pool[v].prm;
         sj.lut = ctx->pool[v].lut;
+        sj.pscr = ctx->pool[v].pscr;
     }
     const int per = std::max(1, (2 * ctx->num_sms + sp.n_jobs - 1) / sp.n_jobs);
     CK(lnf_launch_stats_init_batched(sp, st));
@@ -135,7 +136,7 @@ lnf_status lnf_enqueue_batch(lnf_ctx *ctx, const lnf_job *jobs, int n, int zchun
     ctx->zchunk = zsave;
     if ((s = lnf_run_pack(ctx, pk, 1, st)) != LNF_OK)
         return s;
-    CK(lnf_launch_entropy_pack(ep, st));
+    CK(lnf_launch_entropy_pack(ep, ctx->d_ent_part, ctx->d_ent_done, st));
     if (scratch_out) {
         scratch_out->clear();
         for (int i = 0; i < n; ++i)

@@ -264,10 +264,6 @@ __device__ void ours_items(const FastArgs &a, const CUtensorMap *tmap, unsigned 
         fence_mbar_init();
     }
     __syncthreads();
-    u32 uses[G::NP];   // completed phases per slot (same in every thread)
-#pragma unroll
-    for (int s = 0; s < G::NP; ++s)
-        uses[s] = 0;
 
     for (;;) {
         if (threadIdx.x == 0)
@@ -299,12 +295,9 @@ __device__ void ours_items(const FastArgs &a, const CUtensorMap *tmap, unsigned 
         if (threadIdx.x == 0)
             for (int p = 0; p < min(G::NP, nplanes); ++p)
                 issue(p);
-        // per-slot phase of the plane p: uses[slot] counts completed waits of that slot
+        // plane p is the (p / NP)-th load into its slot since the barriers were initialised
         auto wait_plane = [&](int p) -> bool {
-            const int slot = p % G::NP;
-            const bool ok = mbar_wait_bounded(&bars[slot], uses[slot] & 1u, a.err);
-            uses[slot] += 1;
-            return ok;
+            return mbar_wait_bounded(&bars[p % G::NP], (u32)((p / G::NP) & 1), a.err);
         };
 
         // per-thread state
@@ -534,9 +527,6 @@ __device__ void ours_items(const FastArgs &a, const CUtensorMap *tmap, unsigned 
             }
             fence_mbar_init();
         }
-#pragma unroll
-        for (int sl = 0; sl < G::NP; ++sl)
-            uses[sl] = 0;
         __syncthreads();
     }
 }

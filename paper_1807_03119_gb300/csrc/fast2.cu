@@ -244,10 +244,6 @@ __device__ void box_items(const Args2 &a, const CUtensorMap *tmap, unsigned char
         fence_mbar_init();
     }
     __syncthreads();
-    u32 uses[G::NP];
-#pragma unroll
-    for (int s = 0; s < G::NP; ++s)
-        uses[s] = 0;
 
     for (;;) {
         if (threadIdx.x == 0)
@@ -280,10 +276,8 @@ __device__ void box_items(const Args2 &a, const CUtensorMap *tmap, unsigned char
         for (int s = 0; s < z1 - z0; ++s) {
             const int pfirst = s == 0 ? 0 : s + 2 * R;
             for (int p = pfirst; p <= s + 2 * R; ++p) {
-                const int slot = p % G::NP;
-                if (!mbar_wait_bounded(&bars[slot], uses[slot] & 1u, a.err))
+                if (!mbar_wait_bounded(&bars[p % G::NP], (u32)((p / G::NP) & 1), a.err))
                     *s_abort = 1;
-                uses[slot] += 1;
             }
             __syncthreads();
             if (*s_abort) {
@@ -416,9 +410,6 @@ __device__ void box_items(const Args2 &a, const CUtensorMap *tmap, unsigned char
             }
             fence_mbar_init();
         }
-#pragma unroll
-        for (int sl = 0; sl < G::NP; ++sl)
-            uses[sl] = 0;
         __syncthreads();
     }
 }
@@ -458,10 +449,6 @@ __device__ void tap_items(const Args2 &a, const CUtensorMap *tmap, unsigned char
         fence_mbar_init();
     }
     __syncthreads();
-    u32 uses[G::NP];
-#pragma unroll
-    for (int s = 0; s < G::NP; ++s)
-        uses[s] = 0;
 
     for (;;) {
         if (threadIdx.x == 0)
@@ -494,10 +481,8 @@ __device__ void tap_items(const Args2 &a, const CUtensorMap *tmap, unsigned char
         for (int s = 0; s < z1 - z0; ++s) {
             const int pfirst = s == 0 ? 0 : s + 2 * R;
             for (int p = pfirst; p <= s + 2 * R; ++p) {
-                const int slot = p % G::NP;
-                if (!mbar_wait_bounded(&bars[slot], uses[slot] & 1u, a.err))
+                if (!mbar_wait_bounded(&bars[p % G::NP], (u32)((p / G::NP) & 1), a.err))
                     *s_abort = 1;
-                uses[slot] += 1;
             }
             __syncthreads();
             if (*s_abort) {
@@ -543,7 +528,7 @@ __device__ void tap_items(const Args2 &a, const CUtensorMap *tmap, unsigned char
                 }
             };
             if (FILTER == LNF_SIGMA) {
-#pragma unroll
+#pragma unroll 1
                 for (int dz = -R; dz <= R; ++dz) {
                     const unsigned char *pl = ring + ((s + R + dz) % G::NP) * G::PBYTES;
 #pragma unroll
@@ -641,9 +626,6 @@ __device__ void tap_items(const Args2 &a, const CUtensorMap *tmap, unsigned char
             }
             fence_mbar_init();
         }
-#pragma unroll
-        for (int sl = 0; sl < G::NP; ++sl)
-            uses[sl] = 0;
         __syncthreads();
     }
 }
@@ -661,7 +643,8 @@ struct K2Smem {
 };
 
 template <typename T, int R, int FILTER>
-__global__ void __launch_bounds__(kThreads, 1) k_fast2(const __grid_constant__ CUtensorMap tmap, const Args2 a)
+__global__ void __launch_bounds__(kThreads, K2Smem<T, R, FILTER>::BOX ? 1 : 2)
+    k_fast2(const __grid_constant__ CUtensorMap tmap, const Args2 a)
 {
     typedef K2Smem<T, R, FILTER> S;
     extern __shared__ __align__(128) unsigned char smem_raw[];

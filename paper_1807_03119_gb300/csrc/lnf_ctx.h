@@ -24,6 +24,7 @@ struct VolScratch {
     DevStats *st = nullptr;
     DevParams *prm = nullptr;
     u32 *lut = nullptr;
+    void *pscr = nullptr;       // parameter-derivation scratch (zeroed once)
 };
 
 struct BatchEntry;      lnf_status lnf_fast2_dispatch(lnf_ctx *ctx, const FilterJob &job, const CUtensorMap *tmap, cudaStream_t stream,
@@ -46,6 +47,8 @@ struct lnf_ctx {
     double *d_H = nullptr;
     u32 *d_err = nullptr;
     u32 *d_counter = nullptr;
+    double *d_ent_part = nullptr;   // entropy reduction partials (LNF_ENT_SPLIT x LNF_MAX_ENT)
+    u32 *d_ent_done = nullptr;      // entropy reduction tickets (LNF_MAX_ENT)
     PFN_encodeTiled encode = nullptr;
     FilterPack pack;            // host staging of the kernel-parameter pack
     // host-buffer entry points: device staging

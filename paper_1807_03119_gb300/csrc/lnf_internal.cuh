@@ -176,8 +176,11 @@ __device__ __forceinline__ void prefetch_tmap(const CUtensorMap *map)
 cudaError_t lnf_launch_stats(const void *vol, u64 n, int dtype, u64 *hist, DevStats *st, int num_sms,
                              cudaStream_t stream);
 cudaError_t lnf_launch_stats_init(u64 *hist, u32 levels, DevStats *st, u64 n, cudaStream_t stream);
+// parameter derivation: two launches over chunks of 1024 grey levels; pscr is
+// per-volume device scratch of lnf_param_scratch_bytes() bytes, zeroed once
 cudaError_t lnf_launch_params(const u64 *hist, const DevStats *st, const ParamCfg &cfg, DevParams *prm,
-                              u32 *lut, cudaStream_t stream);
+                              u32 *lut, void *pscr, int dtype, cudaStream_t stream);
+size_t lnf_param_scratch_bytes();
 cudaError_t lnf_launch_entropy(const u64 *hist, u32 levels, u64 n, double *H, cudaStream_t stream);
 cudaError_t lnf_launch_zero(u64 *p, u64 count, cudaStream_t stream);
 
@@ -191,6 +194,7 @@ struct StatsJob {
     DevStats *st;
     DevParams *prm;
     u32 *lut;
+    void *pscr;     // parameter scratch (lnf_param_scratch_bytes)
 };
 struct StatsPack {
     int n_jobs;
@@ -210,7 +214,9 @@ struct EntropyPack {
     double *H[LNF_MAX_ENT];
     u32 levels[LNF_MAX_ENT];
 };
-cudaError_t lnf_launch_entropy_pack(const EntropyPack &pk, cudaStream_t stream);
+// part: LNF_ENT_SPLIT * LNF_MAX_ENT doubles, done: LNF_MAX_ENT counters (zeroed once, reset by the kernel)
+#define LNF_ENT_SPLIT 16
+cudaError_t lnf_launch_entropy_pack(const EntropyPack &pk, double *part, u32 *done, cudaStream_t stream);
 
 // Filter launch helpers (filter.cu).
 int lnf_halo(int filter, int radius, int offset);

@@ -82,6 +82,8 @@ struct Server {
     u64 *hists = nullptr;               // max_inflight output histograms (65536 bins)
     double *d_H = nullptr;              // max_inflight entropies (device)
     double *h_H = nullptr;              // pinned mirror
+    double *ent_part = nullptr;         // entropy reduction partials, one block per stream
+    u32 *ent_done = nullptr;            // entropy reduction tickets, one block per stream
     std::vector<int> free_slots;
     FilterPack pack;                    // the scheduler's own parameter pack
     std::string last_err;
@@ -215,7 +217,8 @@ lnf_status launch_wave(Server *s, Wave *w)
     lnf_status r = lnf_run_pack_counter(ctx, pk, 1, st, ctx->d_counter + 1 + w->stream_idx);
     if (r != LNF_OK)
         return r;
-    if (lnf_launch_entropy_pack(ep, st) != cudaSuccess)
+    if (lnf_launch_entropy_pack(ep, s->ent_part + (size_t)w->stream_idx * LNF_ENT_SPLIT * LNF_MAX_ENT,
+                                s->ent_done + (size_t)w->stream_idx * LNF_MAX_ENT, st) != cudaSuccess)
         return lnf_fail(ctx, LNF_ECUDA, "serving: entropy launch failed");
     for (Req *q : w->reqs) {
         if (q->r.out_host)
@@ -301,6 +304,9 @@ lnf_status ensure_server(lnf_ctx *ctx)
     ok = ok && cudaMalloc(&s->hists, sizeof(u64) * LNF_LEVELS_U16 * slots) == cudaSuccess;
     ok = ok && cudaMalloc(&s->d_H, sizeof(double) * slots) == cudaSuccess;
     ok = ok && cudaHostAlloc(&s->h_H, sizeof(double) * slots, cudaHostAllocDefault) == cudaSuccess;
+    ok = ok && cudaMalloc(&s->ent_part, sizeof(double) * kStreams * LNF_ENT_SPLIT * LNF_MAX_ENT) == cudaSuccess;
+    ok = ok && cudaMalloc(&s->ent_done, sizeof(u32) * kStreams * LNF_MAX_ENT) == cudaSuccess;
+    ok = ok && cudaMemset(s->ent_done, 0, sizeof(u32) * kStreams * LNF_MAX_ENT) == cudaSuccess;
     if (ok) {
         cudaMemPool_t pool;
         if (cudaDeviceGetDefaultMemPool(&pool, ctx->device) == cudaSuccess) {
@@ -315,6 +321,8 @@ lnf_status ensure_server(lnf_ctx *ctx)
         cudaFree(s->hists);
         cudaFree(s->d_H);
         cudaFreeHost(s->h_H);
+        cudaFree(s->ent_part);
+        cudaFree(s->ent_done);
         delete s;
         return lnf_fail(ctx, LNF_ENOMEM, "serving: could not allocate the scheduler's buffers");
     }
@@ -357,12 +365,15 @@ void lnf_serve_shutdown(lnf_ctx *ctx)
         cudaFree(kv.second.vs.st);
         cudaFree(kv.second.vs.prm);
         cudaFree(kv.second.vs.lut);
+        cudaFree(kv.second.vs.pscr);
     }
     for (auto st : s->streams)
         cudaStreamDestroy(st);
     cudaFree(s->hists);
     cudaFree(s->d_H);
     cudaFreeHost(s->h_H);
+    cudaFree(s->ent_part);
+    cudaFree(s->ent_done);
     delete s;
     ctx->srv = nullptr;
 }
@@ -414,7 +425,9 @@ extern "C" lnf_status lnf_volume_register(lnf_ctx *ctx, const void *src, int src
         cudaMalloc(&v.vs.hist, sizeof(u64) * LNF_LEVELS_U16) != cudaSuccess ||
         cudaMalloc(&v.vs.st, sizeof(DevStats)) != cudaSuccess ||
         cudaMalloc(&v.vs.prm, sizeof(DevParams)) != cudaSuccess ||
-        cudaMalloc(&v.vs.lut, sizeof(u32) * LNF_LEVELS_U16) != cudaSuccess) {
+        cudaMalloc(&v.vs.lut, sizeof(u32) * LNF_LEVELS_U16) != cudaSuccess ||
+        cudaMalloc(&v.vs.pscr, lnf_param_scratch_bytes()) != cudaSuccess ||
+        cudaMemset(v.vs.pscr, 0, lnf_param_scratch_bytes()) != cudaSuccess) {
         cudaFree(v.d_vol);
         return undo(lnf_fail(ctx, LNF_ENOMEM, "resident volume scratch allocation failed"));
     }
@@ -452,6 +465,7 @@ extern "C" lnf_status lnf_volume_unregister(lnf_ctx *ctx, int vol_id)
     cudaFree(v.vs.st);
     cudaFree(v.vs.prm);
     cudaFree(v.vs.lut);
+    cudaFree(v.vs.pscr);
     return LNF_OK;
 }
 

@@ -266,73 +266,158 @@ __device__ __forceinline__ bool otsu_better(const OtsuJ &a, const OtsuJ &b)
     return c > 0 || (c == 0 && a.t < b.t);
 }
 
-struct ParamsSmem {
-    u64 n[1024];
-    u64 s[1024];
-    u128 q[1024];
-    u64 fnum[1024];
-    u64 fden[1024];
-    u32 t[1024];
-    double d[1024];
+// ---- parameter derivation over chunks of 1024 grey levels (a 16-bit
+// histogram has 64 chunks, an 8-bit one a single chunk of 256 levels)
+constexpr int kChunk = 1024;
+constexpr int kPThreads = 256;
+
+struct ParamPartial {          // one per chunk
+    u128 q;                    // best Otsu candidate of the chunk (see OtsuJ)
+    u64 fnum, fden;
+    u32 t, pad;
+    u64 hw;                    // sum of h[v] w[v] over the chunk
+    double H;                  // sum of -p log2 p over the chunk
 };
 
-__device__ void params_body(const u64 *hist, const DevStats *st, const ParamCfg &cfg, DevParams *prm, u32 *lut,
-                            ParamsSmem &sm)
+struct ParamScratch {
+    u64 tot_n[LNF_LEVELS_U16 / kChunk];
+    u64 tot_s[LNF_LEVELS_U16 / kChunk];
+    ParamPartial part[LNF_LEVELS_U16 / kChunk];
+    u32 done;                  // chunks finished (reset by the last one)
+    u32 pad[3];
+};
+
+__device__ __forceinline__ int n_chunks(u32 levels) { return (int)((levels + kChunk - 1) / kChunk); }
+
+// pass 1: per chunk, count and sum of its levels
+__device__ void chunk_totals(const u64 *hist, u32 levels, ParamScratch *ps, int c)
+{
+    __shared__ u64 rn[kPThreads / 32], rs[kPThreads / 32];
+    u64 n = 0, s = 0;
+    for (int i = threadIdx.x; i < kChunk; i += blockDim.x) {
+        const u32 v = c * kChunk + i;
+        if (v < levels) {
+            const u64 h = hist[v];
+            n += h;
+            s += h * v;
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        n += __shfl_xor_sync(0xFFFFFFFFu, n, o);
+        s += __shfl_xor_sync(0xFFFFFFFFu, s, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        rn[threadIdx.x >> 5] = n;
+        rs[threadIdx.x >> 5] = s;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        u64 tn = 0, ts = 0;
+        for (int w = 0; w < kPThreads / 32; ++w) {
+            tn += rn[w];
+            ts += rs[w];
+        }
+        ps->tot_n[c] = tn;
+        ps->tot_s[c] = ts;
+    }
+}
+
+struct PSmem {
+    u64 h[kChunk];
+    u64 pn[kPThreads], ps[kPThreads];
+    u128 q[kPThreads];
+    u64 fnum[kPThreads], fden[kPThreads];
+    u32 t[kPThreads];
+    u64 hw[kPThreads];
+    double d[kPThreads];
+    int last;
+};
+
+// pass 2: per chunk, the Otsu candidates, the weights and partial sums; the
+// last chunk to finish reduces all chunks and writes the parameter block.
+__device__ void chunk_params(const u64 *hist, const DevStats *st, const ParamCfg &cfg, DevParams *prm, u32 *lut,
+                             ParamScratch *ps, int c, PSmem &sm)
 {
     const int tid = threadIdx.x;
-    const int nt = blockDim.x;    // 1024
     const u32 L = st->levels;
     const u64 N = st->N, S = st->S, Q = st->Q;
-    const int chunk = (L + nt - 1) / nt;
-    const int b0 = min((int)L, tid * chunk), b1 = min((int)L, b0 + chunk);
-
-    // 1. exclusive scan of (count, sum) over the bins
-    u64 ln = 0, ls = 0;
-    for (int v = b0; v < b1; ++v) {
-        const u64 h = hist[v];
-        ln += h;
-        ls += h * (u64)v;
+    const int nc = n_chunks(L);
+    // prefix of the chunks before this one
+    u64 n0 = 0, s0 = 0;
+    for (int k = 0; k < c; ++k) {
+        n0 += ps->tot_n[k];
+        s0 += ps->tot_s[k];
     }
-    sm.n[tid] = ln;
-    sm.s[tid] = ls;
+    for (int i = tid; i < kChunk; i += blockDim.x) {
+        const u32 v = c * kChunk + i;
+        sm.h[i] = v < L ? hist[v] : 0ull;
+    }
     __syncthreads();
-    for (int off = 1; off < nt; off <<= 1) {   // Hillis-Steele inclusive scan
+    // each thread owns 4 consecutive levels of the chunk
+    constexpr int PER = kChunk / kPThreads;
+    u64 ln = 0, ls = 0;
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+        const u32 v = c * kChunk + tid * PER + k;
+        ln += sm.h[tid * PER + k];
+        ls += sm.h[tid * PER + k] * v;
+    }
+    sm.pn[tid] = ln;
+    sm.ps[tid] = ls;
+    __syncthreads();
+    for (int off = 1; off < kPThreads; off <<= 1) {
         u64 an = 0, as = 0;
         if (tid >= off) {
-            an = sm.n[tid - off];
-            as = sm.s[tid - off];
+            an = sm.pn[tid - off];
+            as = sm.ps[tid - off];
         }
         __syncthreads();
-        sm.n[tid] += an;
-        sm.s[tid] += as;
+        sm.pn[tid] += an;
+        sm.ps[tid] += as;
         __syncthreads();
     }
-    u64 n0 = sm.n[tid] - ln, s0 = sm.s[tid] - ls;
-    __syncthreads();
-
-    // 2. Otsu (Eq. 1): candidates t = v + 1 for every occupied level v; an
-    //    empty level v gives J(v+1) = J(v), which can never win a tie.
+    u64 cn = n0 + sm.pn[tid] - ln, cs = s0 + sm.ps[tid] - ls;
+    // Otsu (Eq. 1) candidates t = v + 1 at occupied levels v
     OtsuJ best;
     best.t = 0;
     best.q = 0;
     best.fnum = 0;
     best.fden = 1;
-    for (int v = b0; v < b1; ++v) {
-        const u64 h = hist[v];
-        n0 += h;
-        s0 += h * (u64)v;
-        if (h == 0 || v + 1 > (int)L - 1 || n0 == 0 || n0 == N)
-            continue;
-        OtsuJ j = otsu_j(n0, s0, N, S, (u32)(v + 1));
-        if (otsu_better(j, best))
-            best = j;
+    const u64 lgN = log2_fixed40(N);
+    u64 hw = 0;
+    double hsum = 0.0;
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+        const u32 v = c * kChunk + tid * PER + k;
+        const u64 h = sm.h[tid * PER + k];
+        cn += h;
+        cs += h * v;
+        u32 w = 0;
+        if (h) {
+            if (v + 1 <= L - 1 && cn != N) {
+                OtsuJ j = otsu_j(cn, cs, N, S, v + 1);
+                if (otsu_better(j, best))
+                    best = j;
+            }
+            // entropy weight (Eq. 7, fixed point) and the Shannon term
+            const u64 D = lgN - log2_fixed40(h);
+            const u128 num = (((u128)h * D) << 22) + ((u128)N << 39);
+            w = (u32)(num / ((u128)N << 40));
+            const double p = (double)h / (double)N;
+            hsum += -p * log2(p);
+        }
+        if (v < L)
+            lut[v] = w;
+        hw += h * (u64)w;
     }
     sm.q[tid] = best.q;
     sm.fnum[tid] = best.fnum;
     sm.fden[tid] = best.fden;
     sm.t[tid] = best.t;
+    sm.hw[tid] = hw;
+    sm.d[tid] = hsum;
     __syncthreads();
-    for (int off = nt / 2; off > 0; off >>= 1) {
+    for (int off = kPThreads / 2; off > 0; off >>= 1) {
         if (tid < off) {
             OtsuJ a{sm.q[tid], sm.fnum[tid], sm.fden[tid], sm.t[tid]};
             OtsuJ b{sm.q[tid + off], sm.fnum[tid + off], sm.fden[tid + off], sm.t[tid + off]};
@@ -342,77 +427,102 @@ __device__ void params_body(const u64 *hist, const DevStats *st, const ParamCfg 
                 sm.fden[tid] = b.fden;
                 sm.t[tid] = b.t;
             }
-        }
-        __syncthreads();
-    }
-    const u32 t_otsu = sm.t[0] ? sm.t[0] : st->minv;   // single level: T = that level
-    __syncthreads();
-
-    // 3. entropy weights (Eq. 7, fixed point) and sum_v h[v] w[v]
-    const u64 lgN = log2_fixed40(N);
-    u64 hw = 0;
-    double hsum = 0.0;
-    for (int v = b0; v < b1; ++v) {
-        const u64 h = hist[v];
-        u32 w = 0;
-        if (h) {
-            const u64 D = lgN - log2_fixed40(h);
-            const u128 num = (((u128)h * D) << 22) + ((u128)N << 39);
-            w = (u32)(num / ((u128)N << 40));
-            const double p = (double)h / (double)N;
-            hsum += -p * log2(p);
-        }
-        lut[v] = w;
-        hw += h * (u64)w;
-    }
-    sm.n[tid] = hw;
-    sm.d[tid] = hsum;
-    __syncthreads();
-    for (int off = nt / 2; off > 0; off >>= 1) {
-        if (tid < off) {
-            sm.n[tid] += sm.n[tid + off];
+            sm.hw[tid] += sm.hw[tid + off];
             sm.d[tid] += sm.d[tid + off];
         }
         __syncthreads();
     }
-
     if (tid == 0) {
-        // 4. sigma band and Okada threshold from the population variance
-        const u128 var_num = (u128)N * Q - (u128)S * S;   // N^2 sigma^2
-        const u128 nn = (u128)N * N;
-        const u128 k2 = (u128)cfg.sigma_k * (u128)cfg.sigma_k;
-        const u64 delta = isqrt_u128((k2 * var_num) / nn);
-        const u64 sig = isqrt_u128(var_num / nn);
-        DevParams p;
-        p.N = N;
-        p.S = S;
-        p.Q = Q;
-        p.minv = st->minv;
-        p.maxv = st->maxv;
-        p.T = cfg.threshold_mode == 0 ? t_otsu : (cfg.threshold_mode == 1 ? cfg.threshold_value : 0u);
-        p.delta = delta > 0xFFFFFFFFull ? 0xFFFFFFFFu : (u32)delta;
-        p.td = cfg.okada_td >= 0 ? cfg.okada_td : (long long)(sig + 1);
-        p.hw_sum = sm.n[0];
-        p.te_cfg = cfg.entropy_te;
-        p.levels = L;
-        p.valid = 1;
-        p.H_in = sm.d[0];
-        *prm = p;
+        ParamPartial &pp = ps->part[c];
+        pp.q = sm.q[0];
+        pp.fnum = sm.fnum[0];
+        pp.fden = sm.fden[0];
+        pp.t = sm.t[0];
+        pp.hw = sm.hw[0];
+        pp.H = sm.d[0];
+        __threadfence();
+        const u32 ticket = atomicAdd(&ps->done, 1u);
+        sm.last = ticket == (u32)nc - 1;
     }
+    __syncthreads();
+    if (!sm.last || tid != 0)
+        return;
+    // the last chunk: reduce the chunks in order, then the scalar parameters
+    __threadfence();
+    OtsuJ b;
+    b.t = 0;
+    b.q = 0;
+    b.fnum = 0;
+    b.fden = 1;
+    u64 hws = 0;
+    double Hs = 0.0;
+    for (int k = 0; k < nc; ++k) {
+        // written by other CTAs of this launch: read past L1
+        const ParamPartial *pp = &ps->part[k];
+        const u64 *q64 = reinterpret_cast<const u64 *>(&pp->q);
+        OtsuJ j;
+        j.q = ((u128)__ldcg(q64 + 1) << 64) | (u128)__ldcg(q64);
+        j.fnum = __ldcg(&pp->fnum);
+        j.fden = __ldcg(&pp->fden);
+        j.t = __ldcg(&pp->t);
+        if (otsu_better(j, b))
+            b = j;
+        hws += __ldcg(&pp->hw);
+        Hs += __ldcg(&pp->H);
+    }
+    ps->done = 0;
+    const u32 t_otsu = b.t ? b.t : st->minv;   // single level: T = that level
+    const u128 var_num = (u128)N * Q - (u128)S * S;   // N^2 sigma^2
+    const u128 nn = (u128)N * N;
+    const u128 k2 = (u128)cfg.sigma_k * (u128)cfg.sigma_k;
+    const u64 delta = isqrt_u128((k2 * var_num) / nn);
+    const u64 sig = isqrt_u128(var_num / nn);
+    DevParams p;
+    p.N = N;
+    p.S = S;
+    p.Q = Q;
+    p.minv = st->minv;
+    p.maxv = st->maxv;
+    p.T = cfg.threshold_mode == 0 ? t_otsu : (cfg.threshold_mode == 1 ? cfg.threshold_value : 0u);
+    p.delta = delta > 0xFFFFFFFFull ? 0xFFFFFFFFu : (u32)delta;
+    p.td = cfg.okada_td >= 0 ? cfg.okada_td : (long long)(sig + 1);
+    p.hw_sum = hws;
+    p.te_cfg = cfg.entropy_te;
+    p.levels = L;
+    p.valid = 1;
+    p.H_in = Hs;
+    *prm = p;
 }
 
-__global__ void __launch_bounds__(1024) k_params(const u64 *hist, const DevStats *st, ParamCfg cfg, DevParams *prm,
-                                                 u32 *lut)
+__global__ void __launch_bounds__(kPThreads) k_param_totals(const u64 *hist, const DevStats *st, ParamScratch *ps)
 {
-    extern __shared__ __align__(16) unsigned char psm[];
-    params_body(hist, st, cfg, prm, lut, *reinterpret_cast<ParamsSmem *>(psm));
+    if ((int)blockIdx.x < n_chunks(st->levels))
+        chunk_totals(hist, st->levels, ps, blockIdx.x);
 }
 
-__global__ void __launch_bounds__(1024) k_params_batched(const __grid_constant__ StatsPack pk, ParamCfg cfg)
+__global__ void __launch_bounds__(kPThreads) k_params(const u64 *hist, const DevStats *st, ParamCfg cfg,
+                                                      DevParams *prm, u32 *lut, ParamScratch *ps)
 {
-    extern __shared__ __align__(16) unsigned char psm[];
-    const StatsJob &j = pk.jobs[blockIdx.x];
-    params_body(j.hist, j.st, cfg, j.prm, j.lut, *reinterpret_cast<ParamsSmem *>(psm));
+    __shared__ PSmem sm;
+    if ((int)blockIdx.x < n_chunks(st->levels))
+        chunk_params(hist, st, cfg, prm, lut, ps, blockIdx.x, sm);
+}
+
+__global__ void __launch_bounds__(kPThreads) k_param_totals_batched(const __grid_constant__ StatsPack pk)
+{
+    const StatsJob &j = pk.jobs[blockIdx.y];
+    const u32 levels = j.dtype == 0 ? LNF_LEVELS_U8 : LNF_LEVELS_U16;
+    if ((int)blockIdx.x < n_chunks(levels))
+        chunk_totals(j.hist, levels, reinterpret_cast<ParamScratch *>(j.pscr), blockIdx.x);
+}
+
+__global__ void __launch_bounds__(kPThreads) k_params_batched(const __grid_constant__ StatsPack pk, ParamCfg cfg)
+{
+    __shared__ PSmem sm;
+    const StatsJob &j = pk.jobs[blockIdx.y];
+    const u32 levels = j.dtype == 0 ? LNF_LEVELS_U8 : LNF_LEVELS_U16;
+    if ((int)blockIdx.x < n_chunks(levels))
+        chunk_params(j.hist, j.st, cfg, j.prm, j.lut, reinterpret_cast<ParamScratch *>(j.pscr), blockIdx.x, sm);
 }
 
 // ------------------------------------------------------------------ entropy
@@ -446,11 +556,47 @@ __global__ void __launch_bounds__(1024) k_entropy(const u64 *hist, u32 levels, u
     entropy_body(hist, levels, n, H, sd);
 }
 
-__global__ void __launch_bounds__(1024) k_entropy_pack(const __grid_constant__ EntropyPack pk)
+// one histogram per blockIdx.y, split over gridDim.x CTAs; partial sums in
+// `part` (gridDim.x doubles per histogram), the last CTA of each histogram
+// adds them in order and writes H
+__global__ void __launch_bounds__(256) k_entropy_pack(const __grid_constant__ EntropyPack pk, double *part,
+                                                      u32 *done)
 {
-    __shared__ double sd[1024];
-    const int i = blockIdx.x;
-    entropy_body(pk.hist[i], pk.levels[i], pk.n[i], pk.H[i], sd);
+    __shared__ double sd[256];
+    __shared__ int last;
+    const int i = blockIdx.y;
+    const u64 *h = pk.hist[i];
+    const u32 levels = pk.levels[i];
+    const double Nd = (double)pk.n[i];
+    double acc = 0.0;
+    for (u32 v = blockIdx.x * blockDim.x + threadIdx.x; v < levels; v += gridDim.x * blockDim.x) {
+        const u64 c = h[v];
+        if (c) {
+            const double p = (double)c / Nd;
+            acc += -p * log2(p);
+        }
+    }
+    sd[threadIdx.x] = acc;
+    __syncthreads();
+    for (int off = blockDim.x / 2; off > 0; off >>= 1) {
+        if (threadIdx.x < off)
+            sd[threadIdx.x] += sd[threadIdx.x + off];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        part[i * gridDim.x + blockIdx.x] = sd[0];
+        __threadfence();
+        last = atomicAdd(&done[i], 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (last && threadIdx.x == 0) {
+        __threadfence();
+        double H = 0.0;
+        for (u32 b = 0; b < gridDim.x; ++b)
+            H += __ldcg(&part[i * gridDim.x + b]);
+        *pk.H[i] = H;
+        done[i] = 0;
+    }
 }
 
 size_t stats_smem_bytes(int dtype)
@@ -502,14 +648,15 @@ cudaError_t lnf_launch_stats(const void *vol, u64 n, int dtype, u64 *hist, DevSt
     return cudaGetLastError();
 }
 
+size_t lnf_param_scratch_bytes() { return sizeof(ParamScratch); }
+
 cudaError_t lnf_launch_params(const u64 *hist, const DevStats *st, const ParamCfg &cfg, DevParams *prm, u32 *lut,
-                              cudaStream_t stream)
+                              void *pscr, int dtype, cudaStream_t stream)
 {
-    const int smem = (int)sizeof(ParamsSmem);
-    cudaError_t e = cudaFuncSetAttribute(k_params, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e != cudaSuccess)
-        return e;
-    k_params<<<1, 1024, smem, stream>>>(hist, st, cfg, prm, lut);
+    const int nc = dtype == 0 ? 1 : LNF_LEVELS_U16 / kChunk;
+    ParamScratch *ps = static_cast<ParamScratch *>(pscr);
+    k_param_totals<<<nc, kPThreads, 0, stream>>>(hist, st, ps);
+    k_params<<<nc, kPThreads, 0, stream>>>(hist, st, cfg, prm, lut, ps);
     return cudaGetLastError();
 }
 
@@ -545,18 +692,17 @@ cudaError_t lnf_launch_params_batched(const StatsPack &pk, const ParamCfg &cfg, 
 {
     if (pk.n_jobs <= 0)
         return cudaSuccess;
-    const int smem = (int)sizeof(ParamsSmem);
-    cudaError_t e = cudaFuncSetAttribute(k_params_batched, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e != cudaSuccess)
-        return e;
-    k_params_batched<<<pk.n_jobs, 1024, smem, stream>>>(pk, cfg);
+    dim3 grid(LNF_LEVELS_U16 / kChunk, pk.n_jobs);
+    k_param_totals_batched<<<grid, kPThreads, 0, stream>>>(pk);
+    k_params_batched<<<grid, kPThreads, 0, stream>>>(pk, cfg);
     return cudaGetLastError();
 }
 
-cudaError_t lnf_launch_entropy_pack(const EntropyPack &pk, cudaStream_t stream)
+cudaError_t lnf_launch_entropy_pack(const EntropyPack &pk, double *part, u32 *done, cudaStream_t stream)
 {
     if (pk.count <= 0)
         return cudaSuccess;
-    k_entropy_pack<<<pk.count, 1024, 0, stream>>>(pk);
+    dim3 grid(LNF_ENT_SPLIT, pk.count);
+    k_entropy_pack<<<grid, 256, 0, stream>>>(pk, part, done);
     return cudaGetLastError();
 }
