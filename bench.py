@@ -220,6 +220,9 @@ def main():
                     help="plain: the 512^3 five-filter step (default); batched / served: the delivery forms")
     ap.add_argument("--duration", type=float, default=10.0, help="served: seconds of Poisson arrivals")
     ap.add_argument("--rate", type=float, default=200.0, help="served: requests per second")
+    ap.add_argument("--dims", type=int, nargs=3, default=None,
+                    help="profiling: a smaller phantom of the same workload (nx ny nz); not a bench line")
+    ap.add_argument("--no-e2e", action="store_true", help="profiling: skip the host-buffer leg")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -253,7 +256,12 @@ def main():
         dist.barrier()
     lnf.load()
 
-    vol = phantoms.P2(seed=2 + rank)   # each rank filters its own volume (weak scaling)
+    global N_VOX
+    if args.dims:
+        vol = phantoms.P2(seed=2 + rank, dims=tuple(args.dims))
+        N_VOX = int(vol.size)
+    else:
+        vol = phantoms.P2(seed=2 + rank)   # each rank filters its own volume (weak scaling)
     t = torch.from_numpy(vol).cuda()
     filters = [lnf.MEAN, lnf.SIGMA, lnf.ENTROPY, lnf.OKADA, lnf.OURS]
     outs = [torch.empty_like(t) for _ in filters]
@@ -293,25 +301,30 @@ def main():
         ms = float(tt.item())
     value = world * 5 * N_VOX / (ms / 1e3) / 1e9
 
+    if args.no_e2e:
+        args.e2e_steps = 0
     # end to end through the host-buffer entry point, from pinned host memory
     pin_in = torch.from_numpy(vol).pin_memory()
     pin_outs = [torch.empty(vol.shape, dtype=torch.uint16).pin_memory() for _ in filters]
     in_np = pin_in.numpy()
     outs_np = [o.numpy() for o in pin_outs]
-    ctx.filter_multi_host(in_np, filters, RADIUS, outs=outs_np)   # staging allocation
+    if args.e2e_steps > 0:
+        ctx.filter_multi_host(in_np, filters, RADIUS, outs=outs_np)   # staging allocation
     if world > 1:
         dist.barrier()
     t0 = time.perf_counter()
     for _ in range(args.e2e_steps):
         ctx.filter_multi_host(in_np, filters, RADIUS, outs=outs_np)
-    e2e_s = (time.perf_counter() - t0) / args.e2e_steps
+    e2e_s = (time.perf_counter() - t0) / max(1, args.e2e_steps) if args.e2e_steps > 0 else float("nan")
     if world > 1:
         tt = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         e2e_s = float(tt.item())
-    e2e = {"value": world * 5 * N_VOX / e2e_s / 1e9, "unit": UNIT,
-           "h2d_bytes_per_step": N_VOX * ES, "d2h_bytes_per_step": 5 * N_VOX * ES + 8 * 6,
-           "ms_per_step": e2e_s * 1e3}
+    e2e = None
+    if args.e2e_steps > 0:
+        e2e = {"value": world * 5 * N_VOX / e2e_s / 1e9, "unit": UNIT,
+               "h2d_bytes_per_step": N_VOX * ES, "d2h_bytes_per_step": 5 * N_VOX * ES + 8 * 6,
+               "ms_per_step": e2e_s * 1e3}
 
     if rank != 0:
         ctx.close()

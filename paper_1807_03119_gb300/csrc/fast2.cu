@@ -32,11 +32,10 @@ constexpr int kTX = 128;
 constexpr int kTY = kWarps * kRows;
 constexpr int kPF = 2;
 constexpr int kHistWin = 4096;
-constexpr int kLutWin = 4096;
 
 __device__ __forceinline__ int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
 
-template <typename T, int R>
+template <typename T, int R, int PF = kPF>
 struct Geo2 {
     static constexpr int H = R;                            // halo in y and z
     static constexpr int XH = 16 / sizeof(T);              // x halo, 16 bytes (>= R for R <= 8)
@@ -44,7 +43,7 @@ struct Geo2 {
     static constexpr int PH = kTY + 2 * H;
     static constexpr int ROWB = PW * sizeof(T);
     static constexpr int PBYTES = ((PW * PH * (int)sizeof(T)) + 127) / 128 * 128;
-    static constexpr int NP = 2 * R + 2 + kPF;
+    static constexpr int NP = 2 * R + 2 + PF;
     static constexpr int M = 2 * R + 1;
     static constexpr int RING = NP * PBYTES;
     // box kernel: Bz plane of (kTY + 2R) rows x (kTX + 8) u32, own cells at column offset 4
@@ -120,6 +119,8 @@ struct Args2 {
     u64 *out_hist;
     u32 *counter;
     u32 *err;
+    u32 one;        // always 1; a multiplier the compiler cannot fold, so that adds
+                    // written as multiply-adds issue on the FMA pipe (see tap_items)
 };
 
 // shared histogram of nonzero outputs (window [hbase, hbase + bins)), zero count by difference
@@ -164,9 +165,12 @@ __device__ __forceinline__ void store4(const Args2 &a, int z, int y, int x, cons
 
 // ------------------------------------------------------------------ box kernel body
 
+constexpr int kBoxPF = 1;            // box kernel: one plane prefetched (two CTAs per SM fit)
+constexpr int kBoxWin = 2048;        // box kernel (entropy): histogram / weight windows
+
 template <typename T, int R, bool ENT>
 struct BoxBody {
-    typedef Geo2<T, R> G;
+    typedef Geo2<T, R, kBoxPF> G;
     // per-thread state
     u32 bz[kRows][4];
     u32 hz[G::HS];
@@ -181,7 +185,7 @@ struct BoxBody {
         if (!ENT)
             return v;
         const u32 o = v - lut_base;
-        return o < (u32)kLutWin ? lut_sh[o] : __ldg(lut_g + v);
+        return o < (u32)kBoxWin ? lut_sh[o] : __ldg(lut_g + v);
     }
 };
 
@@ -190,7 +194,7 @@ __device__ void box_items(const Args2 &a, const CUtensorMap *tmap, unsigned char
                           Hist2 &hist, const u32 *lut_sh, u32 lut_base)
 {
     using namespace lnfdev;
-    typedef Geo2<T, R> G;
+    typedef Geo2<T, R, kBoxPF> G;
     unsigned char *ring = smem;
     u32 *bzp = reinterpret_cast<u32 *>(smem + G::RING);
     u64 *bars = reinterpret_cast<u64 *>(smem + G::RING + G::BZ);
@@ -517,11 +521,32 @@ __device__ void tap_items(const Args2 &a, const CUtensorMap *tmap, unsigned char
                     acc[i][k] = 0;
                     cnt[i][k] = 0;
                 }
-            auto take = [&](int i, int k, u32 v) {
-                if (v - lo[i][k] <= wd[i][k]) {
-                    if (TP::PACK) {
-                        acc[i][k] += (v << TP::CS) | 1u;
-                    } else {
+            // per tap and voxel: d = v - lo (multiply-add: FMA pipe), in-band test
+            // (compare: ALU pipe), accumulate (alternately FMA and ALU pipe), so
+            // that the integer work is split between the two half-rate pipes
+            const u32 one = a.one;
+            u32 nlo[kRows][4];
+#pragma unroll
+            for (int i = 0; i < kRows; ++i)
+#pragma unroll
+                for (int k = 0; k < 4; ++k)
+                    nlo[i][k] = 0u - lo[i][k];
+            auto take = [&](int i, int k, u32 v, u32 pv) {
+                if (TP::PACK) {
+                    // d = v - lo: a plain add (ALU) for even voxels, a multiply-add by
+                    // the runtime 1 (FMA pipe) for odd ones; the in-band test is a
+                    // compare (ALU) and the accumulate a predicated multiply-add (FMA)
+                    u32 d;
+                    if (k & 1)
+                        asm("mad.lo.u32 %0, %1, %2, %3;" : "=r"(d) : "r"(v), "r"(one), "r"(nlo[i][k]));
+                    else
+                        d = v + nlo[i][k];
+                    asm(
+                        "{\n\t.reg .pred p;\n\tsetp.le.u32 p, %1, %2;\n\t@p mad.lo.u32 %0, %3, %4, %0;\n\t}"
+                        : "+r"(acc[i][k])
+                        : "r"(d), "r"(wd[i][k]), "r"(pv), "r"(one));
+                } else {
+                    if (v - lo[i][k] <= wd[i][k]) {
                         acc[i][k] += v;
                         cnt[i][k] += 1;
                     }
@@ -533,11 +558,14 @@ __device__ void tap_items(const Args2 &a, const CUtensorMap *tmap, unsigned char
                     const unsigned char *pl = ring + ((s + R + dz) % G::NP) * G::PBYTES;
 #pragma unroll
                     for (int rr = 0; rr < kRows + 2 * R; ++rr) {   // rows r0 - R .. r0 + 3 + R
-                        u32 v[12];
+                        u32 v[12], pv[12];
                         const unsigned char *row = pl + (r0 - R + rr) * G::ROWB;
                         ld4<T>(row, c0 - 4, v);
                         ld4<T>(row, c0, v + 4);
                         ld4<T>(row, c0 + 4, v + 8);
+#pragma unroll
+                        for (int e = 0; e < 12; ++e)
+                            pv[e] = TP::PACK ? ((v[e] << TP::CS) | 1u) : v[e];
 #pragma unroll
                         for (int i = 0; i < kRows; ++i) {
                             const int dy = rr - R - i;
@@ -547,7 +575,7 @@ __device__ void tap_items(const Args2 &a, const CUtensorMap *tmap, unsigned char
                             for (int k = 0; k < 4; ++k)
 #pragma unroll
                                 for (int dx = -R; dx <= R; ++dx)
-                                    take(i, k, v[4 + k + dx]);
+                                    take(i, k, v[4 + k + dx], pv[4 + k + dx]);
                         }
                     }
                 }
@@ -561,11 +589,12 @@ __device__ void tap_items(const Args2 &a, const CUtensorMap *tmap, unsigned char
                     ld4<T>(row, c0 + 4, v + 8);
 #pragma unroll
                     for (int k = 0; k < 4; ++k) {
-                        take(i, k, v[4 + k]);   // the centre itself
+                        auto pk = [&](u32 x) { return TP::PACK ? ((x << TP::CS) | 1u) : x; };
+                        take(i, k, v[4 + k], pk(v[4 + k]));   // the centre itself
 #pragma unroll
                         for (int t = 1; t <= R; ++t) {
-                            take(i, k, v[4 + k - t]);
-                            take(i, k, v[4 + k + t]);
+                            take(i, k, v[4 + k - t], pk(v[4 + k - t]));
+                            take(i, k, v[4 + k + t], pk(v[4 + k + t]));
                         }
                     }
                 }
@@ -581,8 +610,8 @@ __device__ void tap_items(const Args2 &a, const CUtensorMap *tmap, unsigned char
                             ld4<T>(plz + (r0 + i) * G::ROWB, c0, vz);
 #pragma unroll
                             for (int k = 0; k < 4; ++k) {
-                                take(i, k, vy[k]);
-                                take(i, k, vz[k]);
+                                take(i, k, vy[k], TP::PACK ? ((vy[k] << TP::CS) | 1u) : vy[k]);
+                                take(i, k, vz[k], TP::PACK ? ((vz[k] << TP::CS) | 1u) : vz[k]);
                             }
                         }
                     }
@@ -634,10 +663,12 @@ __device__ void tap_items(const Args2 &a, const CUtensorMap *tmap, unsigned char
 
 template <typename T, int R, int FILTER>
 struct K2Smem {
-    typedef Geo2<T, R> G;
     static constexpr bool BOX = FILTER == LNF_MEAN || FILTER == LNF_ENTROPY;
-    static constexpr int HISTB = (sizeof(T) == 1 ? 256 : kHistWin) * 4;
-    static constexpr int LUTB = FILTER == LNF_ENTROPY ? (sizeof(T) == 1 ? 256 : kLutWin) * 4 : 0;
+    typedef Geo2<T, R, BOX ? kBoxPF : kPF> G;
+    static constexpr int HWIN = sizeof(T) == 1 ? 256 : (FILTER == LNF_ENTROPY ? kBoxWin : kHistWin);
+    static constexpr int LWIN = sizeof(T) == 1 ? 256 : kBoxWin;
+    static constexpr int HISTB = HWIN * 4;
+    static constexpr int LUTB = FILTER == LNF_ENTROPY ? LWIN * 4 : 0;
     static constexpr int MAIN = G::RING + (BOX ? G::BZ : 0) + G::NP * 8;
     static constexpr int TOTAL = 128 + MAIN + 64 + HISTB + LUTB;
 };
@@ -652,7 +683,7 @@ __global__ void __launch_bounds__(kThreads, K2Smem<T, R, FILTER>::BOX ? 1 : 2)
     __shared__ int s_item, s_abort;
     u32 *hsh = reinterpret_cast<u32 *>(smem + S::MAIN + 64);
     u32 *lut_sh = reinterpret_cast<u32 *>(smem + S::MAIN + 64 + S::HISTB);
-    const u32 bins = sizeof(T) == 1 ? 256u : (u32)kHistWin;
+    const u32 bins = (u32)S::HWIN;
     Hist2 h;
     h.sh = hsh;
     h.bins = bins;
@@ -666,7 +697,7 @@ __global__ void __launch_bounds__(kThreads, K2Smem<T, R, FILTER>::BOX ? 1 : 2)
     u32 lut_base = 0;
     if (FILTER == LNF_ENTROPY) {
         lut_base = sizeof(T) == 1 ? 0u : a.prm->minv;
-        const int nl = sizeof(T) == 1 ? 256 : kLutWin;
+        const int nl = S::LWIN;
         for (int i = threadIdx.x; i < nl; i += blockDim.x)
             lut_sh[i] = (lut_base + i < (sizeof(T) == 1 ? 256u : 65536u)) ? a.lut[lut_base + i] : 0u;
     }
@@ -696,7 +727,7 @@ template <typename T, int R, int FILTER>
 lnf_status launch2(lnf_ctx *ctx, const FilterJob &j, cudaStream_t st, int *handled)
 {
     typedef K2Smem<T, R, FILTER> S;
-    typedef Geo2<T, R> G;
+    typedef typename S::G G;
     CUtensorMap map;   // this kernel's own descriptor: box = its tile + halo
     if (!lnf_encode_box(ctx, j.in, j.nx, j.ny, j.nz, j.dtype, G::PW, G::PH, &map))
         return LNF_OK;
@@ -718,6 +749,7 @@ lnf_status launch2(lnf_ctx *ctx, const FilterJob &j, cudaStream_t st, int *handl
     a.out_hist = j.out_hist;
     a.counter = ctx->d_counter + 9;
     a.err = ctx->d_err;
+    a.one = 1u;
     if (cudaFuncSetAttribute(k_fast2<T, R, FILTER>, cudaFuncAttributeMaxDynamicSharedMemorySize, S::TOTAL) !=
         cudaSuccess)
         return lnf_fail(ctx, LNF_ECUDA, "fast2 kernel: shared memory attribute (%d bytes)", S::TOTAL);

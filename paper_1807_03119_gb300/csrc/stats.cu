@@ -189,15 +189,15 @@ __global__ void __launch_bounds__(kStatsThreads) k_stats_batched(const __grid_co
 
 // ------------------------------------------------------------------ exact helpers
 
-// floor(sqrt(x)) bit by bit
+// floor(sqrt(x)) for x < 2^112: an FP64 estimate, then exact integer correction
 __device__ u64 isqrt_u128(u128 x)
 {
-    u64 r = 0;
-    for (int b = 63; b >= 0; --b) {
-        u64 c = r | (1ull << b);
-        if ((u128)c * c <= x)
-            r = c;
-    }
+    const double xd = (double)(u64)(x >> 64) * 18446744073709551616.0 + (double)(u64)x;
+    u64 r = (u64)sqrt(xd);
+    while (r > 0 && (u128)r * r > x)
+        --r;
+    while ((u128)(r + 1) * (r + 1) <= x)
+        ++r;
     return r;
 }
 
@@ -445,31 +445,59 @@ __device__ void chunk_params(const u64 *hist, const DevStats *st, const ParamCfg
         sm.last = ticket == (u32)nc - 1;
     }
     __syncthreads();
-    if (!sm.last || tid != 0)
+    if (!sm.last)
         return;
-    // the last chunk: reduce the chunks in order, then the scalar parameters
+    // the last chunk: reduce the chunks (tree over the CTA, exact comparisons)
     __threadfence();
-    OtsuJ b;
-    b.t = 0;
-    b.q = 0;
-    b.fnum = 0;
-    b.fden = 1;
-    u64 hws = 0;
-    double Hs = 0.0;
-    for (int k = 0; k < nc; ++k) {
-        // written by other CTAs of this launch: read past L1
-        const ParamPartial *pp = &ps->part[k];
-        const u64 *q64 = reinterpret_cast<const u64 *>(&pp->q);
+    {
         OtsuJ j;
-        j.q = ((u128)__ldcg(q64 + 1) << 64) | (u128)__ldcg(q64);
-        j.fnum = __ldcg(&pp->fnum);
-        j.fden = __ldcg(&pp->fden);
-        j.t = __ldcg(&pp->t);
-        if (otsu_better(j, b))
-            b = j;
-        hws += __ldcg(&pp->hw);
-        Hs += __ldcg(&pp->H);
+        j.t = 0;
+        j.q = 0;
+        j.fnum = 0;
+        j.fden = 1;
+        u64 hwp = 0;
+        double Hp = 0.0;
+        if (tid < nc) {
+            // written by other CTAs of this launch: read past L1
+            const ParamPartial *pp = &ps->part[tid];
+            const u64 *q64 = reinterpret_cast<const u64 *>(&pp->q);
+            j.q = ((u128)__ldcg(q64 + 1) << 64) | (u128)__ldcg(q64);
+            j.fnum = __ldcg(&pp->fnum);
+            j.fden = __ldcg(&pp->fden);
+            j.t = __ldcg(&pp->t);
+            hwp = __ldcg(&pp->hw);
+            Hp = __ldcg(&pp->H);
+        }
+        __syncthreads();
+        sm.q[tid] = j.q;
+        sm.fnum[tid] = j.fnum;
+        sm.fden[tid] = j.fden;
+        sm.t[tid] = j.t;
+        sm.hw[tid] = hwp;
+        sm.d[tid] = Hp;
+        __syncthreads();
+        for (int off = kPThreads / 2; off > 0; off >>= 1) {
+            if (tid < off) {
+                OtsuJ a{sm.q[tid], sm.fnum[tid], sm.fden[tid], sm.t[tid]};
+                OtsuJ b2{sm.q[tid + off], sm.fnum[tid + off], sm.fden[tid + off], sm.t[tid + off]};
+                if (otsu_better(b2, a)) {
+                    sm.q[tid] = b2.q;
+                    sm.fnum[tid] = b2.fnum;
+                    sm.fden[tid] = b2.fden;
+                    sm.t[tid] = b2.t;
+                }
+                sm.hw[tid] += sm.hw[tid + off];
+                sm.d[tid] += sm.d[tid + off];
+            }
+            __syncthreads();
+        }
     }
+    if (tid != 0)
+        return;
+    OtsuJ b;
+    b.t = sm.t[0];
+    const u64 hws = sm.hw[0];
+    const double Hs = sm.d[0];
     ps->done = 0;
     const u32 t_otsu = b.t ? b.t : st->minv;   // single level: T = that level
     const u128 var_num = (u128)N * Q - (u128)S * S;   // N^2 sigma^2
