@@ -16,12 +16,11 @@
 //   * z: Lz is a running sum held in registers (one term in, one out per
 //     step); the output needs two accumulators per voxel, A = G(z-1) + C(z-2)
 //     and B = C(z-1), so the z direction costs no shared memory at all.
-//   * y: Ly is a running sum along the lane's rows; the corner sum T_y needs
-//     the V = T_x G rows above and below, exchanged through shared memory
-//     between the warps of the CTA (the CTA's own edge rows are computed by
-//     its first and last warp).
-//   * x: Lx from the row words; T_x by warp shuffles, plus one extra column
-//     pair at each end of the warp (lanes 0 and 31).
+//   * y: Ly is a running sum along the lane's rows.
+//   * x: Lx from the row words.
+//   * G of the tile goes to a shared G plane; the one-voxel ring around the
+//     tile (324 voxels) is computed voxel by voxel, spread over all threads;
+//     C = T_x T_y G is then read from the plane.  Two barriers per step.
 // Line sums are formed on packed pairs of 16-bit lanes (two voxels per 32-bit
 // add) whenever 3M * max <= 65535, which keeps every lane exact; otherwise
 // the same code runs on unpacked 32-bit pairs.
@@ -108,6 +107,13 @@ struct Ld<uint8_t> {
 
 // ------------------------------------------------------------------ geometry
 
+constexpr int kPFo = 1;                  // planes prefetched into shared memory (two CTAs per SM fit)
+constexpr int kL2Ahead = 6;              // planes prefetched into L2 beyond the shared-memory ring
+constexpr int kHistWinO = 2048;          // output histogram window (16-bit data)
+constexpr int kGW = kTX + 8;             // G plane row: columns -1 .. 128 at offsets 3 .. 132
+constexpr int kHalo = 2 * (kTX + 2) + 2 * kTY;   // voxels of the ring around the tile
+constexpr int kHS = (kHalo + kThreads - 1) / kThreads;
+
 template <typename T, int R>
 struct FGeo {
     static constexpr int H = R + 1;                        // halo in y and z
@@ -116,45 +122,55 @@ struct FGeo {
     static constexpr int PH = kTY + 2 * H;                 // plane height
     static constexpr int ROWB = PW * sizeof(T);            // row bytes (multiple of 16)
     static constexpr int PBYTES = ((PW * PH * (int)sizeof(T)) + 127) / 128 * 128;
-    static constexpr int NP = 2 * R + 2 + kPF;             // ring slots
+    static constexpr int NP = 2 * R + 2 + kPFo;            // ring slots
     static constexpr int M = 2 * R + 1;
     static constexpr int RING = NP * PBYTES;
-    static constexpr int XBUF = (2 * kWarps + 2) * kTX * 4;    // exchanged V rows
-    static constexpr int HIST = (sizeof(T) == 1 ? 256 : kHistWin) * 4;
-    static constexpr int SMEM = 128 + RING + XBUF + HIST + NP * 8 + 64;
+    static constexpr int GPLANE = (kTY + 2) * kGW * 4;
+    static constexpr int HIST = (sizeof(T) == 1 ? 256 : kHistWinO) * 4;
+    static constexpr int SMEM = 128 + RING + GPLANE + HIST + NP * 8 + 64;
 };
 
-// fix the out-of-volume cells of a freshly loaded plane by replicating the border
+// fix the out-of-volume cells of a freshly loaded plane by replicating the
+// border; only the halo the kernel reads (H columns / rows on each side) is fixed
 template <typename T, int R>
 __device__ void fixup(unsigned char *pl, int px0, int py0, int nx, int ny)
 {
     typedef FGeo<T, R> G;
     T *p = reinterpret_cast<T *>(pl);
-    const int left = px0 < 0 ? min(-px0, G::PW) : 0;
-    const int right_start = max(0, min(G::PW, nx - px0));
-    const int ncol = left + (G::PW - right_start);
-    if (ncol > 0)
-        for (int e = threadIdx.x; e < ncol * G::PH; e += blockDim.x) {
-            const int row = e / ncol;
-            const int k = e - row * ncol;
-            const int col = k < left ? k : right_start + (k - left);
-            p[row * G::PW + col] = p[row * G::PW + clampi(px0 + col, 0, nx - 1) - px0];
+    constexpr int HC = G::H;                       // columns read left of XH / right of XH + kTX - 1
+    constexpr int NC = 2 * HC;
+    const bool fix_l = px0 + G::XH - HC < 0, fix_r = px0 + G::XH + kTX + HC > nx;
+    if (fix_l || fix_r || px0 + G::XH + kTX > nx)
+        for (int e = threadIdx.x; e < NC * G::PH; e += blockDim.x) {
+            const int row = e / NC;               // constant divisor
+            const int k = e - row * NC;
+            const int col = k < HC ? G::XH - HC + k : G::XH + kTX + (k - HC);
+            const int vx = px0 + col;
+            if (vx < 0 || vx >= nx)
+                p[row * G::PW + col] = p[row * G::PW + clampi(vx, 0, nx - 1) - px0];
+        }
+    // columns inside the tile but beyond the volume (a ragged last tile)
+    if (px0 + G::XH + kTX > nx)
+        for (int e = threadIdx.x; e < kTX * G::PH; e += blockDim.x) {
+            const int row = e / kTX;
+            const int col = G::XH + (e - row * kTX);
+            if (px0 + col >= nx)
+                p[row * G::PW + col] = p[row * G::PW + nx - 1 - px0];
         }
     __syncthreads();
     const int top = py0 < 0 ? min(-py0, G::PH) : 0;
-    const int bot_start = max(0, min(G::PH, ny - py0));
-    const int nrow = top + (G::PH - bot_start);
-    if (nrow > 0)
-        for (int e = threadIdx.x; e < nrow * G::PW; e += blockDim.x) {
-            const int k = e / G::PW;
-            const int col = e - k * G::PW;
-            const int row = k < top ? k : bot_start + (k - top);
-            p[row * G::PW + col] = p[(clampi(py0 + row, 0, ny - 1) - py0) * G::PW + col];
-        }
+    const int bot0 = max(top, min(G::PH, ny - py0));
+    const int nfix = top + (G::PH - bot0);
+    for (int e = threadIdx.x; e < nfix * G::PW; e += blockDim.x) {
+        const int k = e / G::PW;                  // constant divisor
+        const int col = e - k * G::PW;
+        const int row = k < top ? k : bot0 + (k - top);
+        p[row * G::PW + col] = p[(clampi(py0 + row, 0, ny - 1) - py0) * G::PW + col];
+    }
     __syncthreads();
 }
 
-// ------------------------------------------------------------------ per-row G
+// ------------------------------------------------------------------ per-row sums
 
 __host__ __device__ constexpr int fl2(int o) { return o >= 0 ? o / 2 : -((-o + 1) / 2); }   // floor(o / 2)
 
@@ -180,48 +196,39 @@ __device__ __forceinline__ typename PK::P window_sum(const typename PK::P *wd)
     return acc;
 }
 
-// Lx of the lane's pairs A (c0, c0+1), B (c0+2, c0+3) and of its edge pair E
-// (lane 0: c0-2; lane 31: c0+4; other lanes: a don't-care copy).
+// Lx of the lane's pairs A (c0, c0+1) and B (c0+2, c0+3)
 template <typename T, int R, class PK>
-__device__ __forceinline__ void lx_pairs(const unsigned char *row, int c0, int lane,
-                                         typename PK::P &lxA, typename PK::P &lxB, typename PK::P &lxE)
+__device__ __forceinline__ void lx_pairs(const unsigned char *row, int c0, typename PK::P &lxA, typename PK::P &lxB)
 {
     typedef typename PK::P P;
     constexpr int A = (R + 1) / 2;
-    constexpr int JL = -A, JH = 1 + A;       // words every lane needs
-    P w[JH - JL + 3];                          // indices JL-1 .. JH+1
+    constexpr int JL = -A, JH = 1 + A;
+    P w[JH - JL + 1];
     u32 q0, q1;
     Ld<T>::quad(row, c0, q0, q1);
-    w[0 - JL + 1] = PK::word(q0);
-    w[1 - JL + 1] = PK::word(q1);
+    w[0 - JL] = PK::word(q0);
+    w[1 - JL] = PK::word(q1);
 #pragma unroll
     for (int j = JL; j <= JH; ++j)
         if (j != 0 && j != 1)
-            w[j - JL + 1] = PK::word(Ld<T>::pair(row, c0 + 2 * j));
-    const bool lane0 = lane == 0;
-    // the one outer word the edge lanes need
-    const P outer = PK::word(Ld<T>::pair(row, lane0 ? c0 + 2 * (JL - 1) : c0 + 2 * (JH + 1)));
-    w[0] = outer;
-    w[JH - JL + 2] = outer;
-    lxA = window_sum<R, PK>(&w[0 - JL + 1]);
-    lxB = window_sum<R, PK>(&w[1 - JL + 1]);
-    // E window: lane 0 around word -1, lane 31 around word 2 (same shape)
-    P ew[2 * A + 1];
-#pragma unroll
-    for (int k = -A; k <= A; ++k)
-        ew[k + A] = lane0 ? w[-1 + k - JL + 1] : w[2 + k - JL + 1];
-    lxE = window_sum<R, PK>(&ew[A]);
+            w[j - JL] = PK::word(Ld<T>::pair(row, c0 + 2 * j));
+    lxA = window_sum<R, PK>(&w[0 - JL]);
+    lxB = window_sum<R, PK>(&w[1 - JL]);
 }
 
 template <typename T, class PK>
-__device__ __forceinline__ void row_pairs(const unsigned char *row, int c0, int ce, typename PK::P &a,
-                                          typename PK::P &b, typename PK::P &e)
+__device__ __forceinline__ void quad_pairs(const unsigned char *row, int c0, typename PK::P &a, typename PK::P &b)
 {
     u32 q0, q1;
     Ld<T>::quad(row, c0, q0, q1);
     a = PK::word(q0);
     b = PK::word(q1);
-    e = PK::word(Ld<T>::pair(row, ce));
+}
+
+template <typename T>
+__device__ __forceinline__ u32 ld1(const unsigned char *row, int col)
+{
+    return sizeof(T) == 2 ? (u32) reinterpret_cast<const uint16_t *>(row)[col] : (u32)row[col];
 }
 
 // ------------------------------------------------------------------ the kernel
@@ -246,17 +253,41 @@ __device__ void ours_items(const FastArgs &a, const CUtensorMap *tmap, unsigned 
     typedef FGeo<T, R> G;
     typedef typename PK::P P;
     unsigned char *ring = smem;
-    u32 *xbuf = reinterpret_cast<u32 *>(smem + G::RING);
-    u64 *bars = reinterpret_cast<u64 *>(smem + G::RING + G::XBUF + G::HIST);
+    u32 *gp = reinterpret_cast<u32 *>(smem + G::RING);                      // G plane
+    u64 *bars = reinterpret_cast<u64 *>(smem + G::RING + G::GPLANE + G::HIST);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const bool lane0 = lane == 0;
-    const int c0 = G::XH + 4 * lane;                                  // first own column (plane coords)
-    const int ce = lane0 ? G::XH - 2 : (lane == 31 ? G::XH + kTX : c0); // edge pair column
-    const int r0 = G::H + kRows * warp;                                // first own row (plane coords)
+    const int c0 = G::XH + 4 * lane;                   // first own column (plane coords)
+    const int r0 = G::H + kRows * warp;                // first own row (plane coords)
+    const int gr0 = 1 + kRows * warp;                  // first own row in the G plane
+    const int gc0 = 4 + 4 * lane;                      // first own column in the G plane
     const u32 T_ = a.prm->T;
     const u32 KT = 27u * G::M * T_;
-    constexpr u32 D2 = 54u * G::M, K = 27u * G::M;
+    // round(U / 27M) half up = floor((2U + 27M) / 54M) = floor((U + (27M - 1)/2) / 27M)
+    // (27M is odd); U < 27M * 65536 for any 16-bit input
+    typedef ExactDiv<27ull * G::M, 27ull * G::M * 65536ull> Div;
+    constexpr unsigned long long HALF = (27ull * G::M - 1) / 2;
+    const u32 hbins = sizeof(T) == 1 ? 256u : (u32)kHistWinO;
+
+    // the ring voxels this thread computes G for (tile coordinates, -1 .. 128 / 32)
+    int hrow[kHS], hcol[kHS];
+    bool hval[kHS];
+#pragma unroll
+    for (int j = 0; j < kHS; ++j) {
+        const int d = threadIdx.x + j * kThreads;
+        hval[j] = d < kHalo;
+        int row = 0, col = 0;
+        if (d < 2 * (kTX + 2)) {
+            row = d < kTX + 2 ? -1 : kTY;
+            col = d % (kTX + 2) - 1;
+        } else if (d < kHalo) {
+            const int e = d - 2 * (kTX + 2);
+            row = e >> 1;
+            col = (e & 1) ? kTX : -1;
+        }
+        hrow[j] = row;
+        hcol[j] = col;
+    }
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < G::NP; ++s)
@@ -292,26 +323,33 @@ __device__ void ours_items(const FastArgs &a, const CUtensorMap *tmap, unsigned 
             mbar_arrive_expect_tx(&bars[slot], pbytes);
             tma_load_3d(ring + slot * G::PBYTES, tmap, &bars[slot], px0, py0, clampi(z0 - 1 - R + p, 0, a.nz - 1));
         };
-        if (threadIdx.x == 0)
+        auto prefetch = [&](int p) {   // thread 0 only: plane p into L2
+            if (p < nplanes)
+                tma_prefetch_3d(tmap, max(px0, 0), max(py0, 0), clampi(z0 - 1 - R + p, 0, a.nz - 1));
+        };
+        if (threadIdx.x == 0) {
             for (int p = 0; p < min(G::NP, nplanes); ++p)
                 issue(p);
-        // plane p is the (p / NP)-th load into its slot since the barriers were initialised
-        auto wait_plane = [&](int p) -> bool {
-            return mbar_wait_bounded(&bars[p % G::NP], (u32)((p / G::NP) & 1), a.err);
-        };
+            for (int p = G::NP; p < G::NP + kL2Ahead; ++p)
+                prefetch(p);
+        }
 
-        // per-thread state
-        P lzA[kRows], lzB[kRows], lzE[kRows], lzxA, lzxB, lzxE;   // running z line sums
-        u32 accA[kRows][4], accB[kRows][4];                         // z accumulators
-        const bool has_extra = warp == 0 || warp == kWarps - 1;
-        const int rx = warp == 0 ? r0 - 1 : r0 + kRows;             // extra row (CTA edge)
+        P lzA[kRows], lzB[kRows];                 // running z line sums of the own pairs
+        u32 lzh[kHS];                             // ... and of the ring voxels
+        u32 accA[kRows][4], accB[kRows][4];       // z accumulators
+#pragma unroll
+        for (int i = 0; i < kRows; ++i)
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+                accB[i][k] = 0;
         bool ok = true;
 
         for (int s = 0; s < nsteps; ++s) {
-            // planes needed: s-1 (old) .. s+2R (new)
+            // planes needed: s-1 (old) .. s+2R (new); plane p is the (p / NP)-th
+            // load into its slot since the barriers were initialised
             const int pfirst = s == 0 ? 0 : s + 2 * R;
             for (int p = pfirst; p <= s + 2 * R; ++p)
-                if (!wait_plane(p))
+                if (!mbar_wait_bounded(&bars[p % G::NP], (u32)((p / G::NP) & 1), a.err))
                     *s_abort = 1;
             __syncthreads();
             if (*s_abort) {
@@ -323,7 +361,7 @@ __device__ void ours_items(const FastArgs &a, const CUtensorMap *tmap, unsigned 
                     fixup<T, R>(ring + (p % G::NP) * G::PBYTES, px0, py0, a.nx, a.ny);
             const unsigned char *pg = ring + ((s + R) % G::NP) * G::PBYTES;   // G plane g = z0-1+s
             const unsigned char *pn = ring + ((s + 2 * R) % G::NP) * G::PBYTES;
-            const unsigned char *po = ring + (((s + G::NP - 1) % G::NP)) * G::PBYTES;
+            const unsigned char *po = ring + ((s + G::NP - 1) % G::NP) * G::PBYTES;
 
             // ---- Lz: initialise at the first step, then one plane in, one out
             if (s == 0) {
@@ -331,134 +369,108 @@ __device__ void ours_items(const FastArgs &a, const CUtensorMap *tmap, unsigned 
                 for (int i = 0; i < kRows; ++i) {
                     lzA[i] = PK::zero();
                     lzB[i] = PK::zero();
-                    lzE[i] = PK::zero();
                 }
-                lzxA = lzxB = lzxE = PK::zero();
 #pragma unroll
+                for (int j = 0; j < kHS; ++j)
+                    lzh[j] = 0;
                 for (int d = 0; d <= 2 * R; ++d) {
                     const unsigned char *pl = ring + (d % G::NP) * G::PBYTES;
 #pragma unroll
                     for (int i = 0; i < kRows; ++i) {
-                        P qa, qb, qe;
-                        row_pairs<T, PK>(pl + (r0 + i) * G::ROWB, c0, ce, qa, qb, qe);
+                        P qa, qb;
+                        quad_pairs<T, PK>(pl + (r0 + i) * G::ROWB, c0, qa, qb);
                         lzA[i] = PK::add3(lzA[i], qa, PK::zero());
                         lzB[i] = PK::add3(lzB[i], qb, PK::zero());
-                        lzE[i] = PK::add3(lzE[i], qe, PK::zero());
                     }
-                    if (has_extra) {
-                        P qa, qb, qe;
-                        row_pairs<T, PK>(pl + rx * G::ROWB, c0, ce, qa, qb, qe);
-                        lzxA = PK::add3(lzxA, qa, PK::zero());
-                        lzxB = PK::add3(lzxB, qb, PK::zero());
-                        lzxE = PK::add3(lzxE, qe, PK::zero());
-                    }
+#pragma unroll
+                    for (int j = 0; j < kHS; ++j)
+                        lzh[j] += ld1<T>(pl + (G::H + hrow[j]) * G::ROWB, G::XH + hcol[j]);
                 }
             } else {
 #pragma unroll
                 for (int i = 0; i < kRows; ++i) {
-                    P na, nb, ne, oa, ob, oe;
-                    row_pairs<T, PK>(pn + (r0 + i) * G::ROWB, c0, ce, na, nb, ne);
-                    row_pairs<T, PK>(po + (r0 + i) * G::ROWB, c0, ce, oa, ob, oe);
+                    P na, nb, oa, ob;
+                    quad_pairs<T, PK>(pn + (r0 + i) * G::ROWB, c0, na, nb);
+                    quad_pairs<T, PK>(po + (r0 + i) * G::ROWB, c0, oa, ob);
                     lzA[i] = PK::addsub(lzA[i], na, oa);
                     lzB[i] = PK::addsub(lzB[i], nb, ob);
-                    lzE[i] = PK::addsub(lzE[i], ne, oe);
                 }
-                if (has_extra) {
-                    P na, nb, ne, oa, ob, oe;
-                    row_pairs<T, PK>(pn + rx * G::ROWB, c0, ce, na, nb, ne);
-                    row_pairs<T, PK>(po + rx * G::ROWB, c0, ce, oa, ob, oe);
-                    lzxA = PK::addsub(lzxA, na, oa);
-                    lzxB = PK::addsub(lzxB, nb, ob);
-                    lzxE = PK::addsub(lzxE, ne, oe);
+#pragma unroll
+                for (int j = 0; j < kHS; ++j) {
+                    const int rr = (G::H + hrow[j]) * G::ROWB, cc = G::XH + hcol[j];
+                    lzh[j] += ld1<T>(pn + rr, cc) - ld1<T>(po + rr, cc);
                 }
             }
 
-            // ---- G and V = T_x G for the own rows (and the CTA edge row)
-            u32 g[kRows][4], v[kRows][4];
-            P lyA = PK::zero(), lyB = PK::zero(), lyE = PK::zero();
+            // ---- G of the own voxels (packed pairs) -> registers and the G plane
+            u32 g[kRows][4];
+            P lyA = PK::zero(), lyB = PK::zero();
 #pragma unroll
             for (int d = -R; d <= R; ++d) {
-                P qa, qb, qe;
-                row_pairs<T, PK>(pg + (r0 + d) * G::ROWB, c0, ce, qa, qb, qe);
+                P qa, qb;
+                quad_pairs<T, PK>(pg + (r0 + d) * G::ROWB, c0, qa, qb);
                 lyA = PK::add3(lyA, qa, PK::zero());
                 lyB = PK::add3(lyB, qb, PK::zero());
-                lyE = PK::add3(lyE, qe, PK::zero());
             }
 #pragma unroll
             for (int i = 0; i < kRows; ++i) {
                 if (i > 0) {
-                    P na, nb, ne, oa, ob, oe;
-                    row_pairs<T, PK>(pg + (r0 + i + R) * G::ROWB, c0, ce, na, nb, ne);
-                    row_pairs<T, PK>(pg + (r0 + i - R - 1) * G::ROWB, c0, ce, oa, ob, oe);
+                    P na, nb, oa, ob;
+                    quad_pairs<T, PK>(pg + (r0 + i + R) * G::ROWB, c0, na, nb);
+                    quad_pairs<T, PK>(pg + (r0 + i - R - 1) * G::ROWB, c0, oa, ob);
                     lyA = PK::addsub(lyA, na, oa);
                     lyB = PK::addsub(lyB, nb, ob);
-                    lyE = PK::addsub(lyE, ne, oe);
                 }
-                P lxA, lxB, lxE;
-                lx_pairs<T, R, PK>(pg + (r0 + i) * G::ROWB, c0, lane, lxA, lxB, lxE);
+                P lxA, lxB;
+                lx_pairs<T, R, PK>(pg + (r0 + i) * G::ROWB, c0, lxA, lxB);
                 const P gA = PK::add3(lxA, lyA, lzA[i]);
                 const P gB = PK::add3(lxB, lyB, lzB[i]);
-                const P gE = PK::add3(lxE, lyE, lzE[i]);
                 g[i][0] = PK::lo(gA);
                 g[i][1] = PK::hi(gA);
                 g[i][2] = PK::lo(gB);
                 g[i][3] = PK::hi(gB);
-                const u32 ge = lane0 ? PK::hi(gE) : PK::lo(gE);
-                const u32 gl = __shfl_up_sync(0xFFFFFFFFu, g[i][3], 1);
-                const u32 gr = __shfl_down_sync(0xFFFFFFFFu, g[i][0], 1);
-                v[i][0] = (lane0 ? ge : gl) + g[i][1];
-                v[i][1] = g[i][0] + g[i][2];
-                v[i][2] = g[i][1] + g[i][3];
-                v[i][3] = g[i][2] + (lane == 31 ? ge : gr);
+                *reinterpret_cast<uint4 *>(gp + (gr0 + i) * kGW + gc0) = make_uint4(g[i][0], g[i][1], g[i][2], g[i][3]);
             }
-            if (has_extra) {   // warp-uniform
-                P lyxA = PK::zero(), lyxB = PK::zero(), lyxE = PK::zero();
+            // ---- G of the ring voxels, one voxel at a time
 #pragma unroll
-                for (int d = -R; d <= R; ++d) {
-                    P qa, qb, qe;
-                    row_pairs<T, PK>(pg + (rx + d) * G::ROWB, c0, ce, qa, qb, qe);
-                    lyxA = PK::add3(lyxA, qa, PK::zero());
-                    lyxB = PK::add3(lyxB, qb, PK::zero());
-                    lyxE = PK::add3(lyxE, qe, PK::zero());
-                }
-                P lxA, lxB, lxE;
-                lx_pairs<T, R, PK>(pg + rx * G::ROWB, c0, lane, lxA, lxB, lxE);
-                const P gA = PK::add3(lxA, lyxA, lzxA);
-                const P gB = PK::add3(lxB, lyxB, lzxB);
-                const P gE = PK::add3(lxE, lyxE, lzxE);
-                const u32 x0v = PK::lo(gA), x1v = PK::hi(gA), x2v = PK::lo(gB), x3v = PK::hi(gB);
-                const u32 ge = lane0 ? PK::hi(gE) : PK::lo(gE);
-                const u32 gl = __shfl_up_sync(0xFFFFFFFFu, x3v, 1);
-                const u32 gr = __shfl_down_sync(0xFFFFFFFFu, x0v, 1);
-                uint4 vx;
-                vx.x = (lane0 ? ge : gl) + x1v;
-                vx.y = x0v + x2v;
-                vx.z = x1v + x3v;
-                vx.w = x2v + (lane == 31 ? ge : gr);
-                const int slot = warp == 0 ? 2 * kWarps : 2 * kWarps + 1;
-                reinterpret_cast<uint4 *>(xbuf + slot * kTX)[lane] = vx;
+            for (int j = 0; j < kHS; ++j) {
+                if (!hval[j])
+                    continue;
+                const int pr = G::H + hrow[j], pc = G::XH + hcol[j];
+                u32 gx = lzh[j];
+#pragma unroll
+                for (int d = -R; d <= R; ++d)
+                    gx += ld1<T>(pg + pr * G::ROWB, pc + d) + ld1<T>(pg + (pr + d) * G::ROWB, pc);
+                gp[(1 + hrow[j]) * kGW + 4 + hcol[j]] = gx;
             }
-            reinterpret_cast<uint4 *>(xbuf + (2 * warp) * kTX)[lane] = make_uint4(v[0][0], v[0][1], v[0][2], v[0][3]);
-            reinterpret_cast<uint4 *>(xbuf + (2 * warp + 1) * kTX)[lane] =
-                make_uint4(v[kRows - 1][0], v[kRows - 1][1], v[kRows - 1][2], v[kRows - 1][3]);
             __syncthreads();
-            const int up_slot = warp == 0 ? 2 * kWarps : 2 * (warp - 1) + 1;
-            const int dn_slot = warp == kWarps - 1 ? 2 * kWarps + 1 : 2 * (warp + 1);
-            const uint4 vu = reinterpret_cast<const uint4 *>(xbuf + up_slot * kTX)[lane];
-            const uint4 vd = reinterpret_cast<const uint4 *>(xbuf + dn_slot * kTX)[lane];
+            // plane s-1 (the oldest) is no longer read: refill its slot
+            if (threadIdx.x == 0 && s >= 1 && s - 1 + G::NP < nplanes) {
+                issue(s - 1 + G::NP);
+                prefetch(s - 1 + G::NP + kL2Ahead);
+            }
 
-            // ---- C = T_y V; outputs at z = g - 1 once three G planes exist
-            const int zout = z0 - 2 + s;   // = g - 1
+            // ---- C = T_x T_y G from the G plane; outputs at z = g - 1 once three G planes exist
+            u32 tx_[kRows + 2][4];
+#pragma unroll
+            for (int rr = 0; rr < kRows + 2; ++rr) {   // G rows gr0 - 1 .. gr0 + kRows
+                const u32 *row = gp + (gr0 - 1 + rr) * kGW + gc0;
+                const uint4 m = *reinterpret_cast<const uint4 *>(row);
+                const u32 l = row[-1], r = row[4];
+                tx_[rr][0] = l + m.y;
+                tx_[rr][1] = m.x + m.z;
+                tx_[rr][2] = m.y + m.w;
+                tx_[rr][3] = m.z + r;
+            }
+            const int zout = z0 - 2 + s;
             const bool emit = s >= 2;
             const unsigned char *pc = ring + ((s + R - 1) % G::NP) * G::PBYTES;   // plane z = g - 1
 #pragma unroll
             for (int i = 0; i < kRows; ++i) {
                 u32 c[4];
-                const u32 up[4] = {vu.x, vu.y, vu.z, vu.w};
-                const u32 dn[4] = {vd.x, vd.y, vd.z, vd.w};
 #pragma unroll
                 for (int k = 0; k < 4; ++k)
-                    c[k] = (i == 0 ? up[k] : v[i - 1][k]) + (i == kRows - 1 ? dn[k] : v[i + 1][k]);
+                    c[k] = tx_[i][k] + tx_[i + 2][k];
                 if (emit) {
                     const int y = y0 + kRows * warp + i;
                     const int x = x0 + 4 * lane;
@@ -469,7 +481,7 @@ __device__ void ours_items(const FastArgs &a, const CUtensorMap *tmap, unsigned 
 #pragma unroll
                     for (int k = 0; k < 4; ++k) {
                         const u32 U = accA[i][k] + c[k];
-                        f[k] = (p0[k] >= T_ && U >= KT) ? (2u * U + K) / D2 : 0u;
+                        f[k] = (p0[k] >= T_ && U >= KT) ? Div::template div_add<HALF>(U) : 0u;
                     }
                     if (y < a.ny && x < a.nx) {
                         const size_t o = ((size_t)zout * a.ny + y) * a.nx + x;
@@ -489,9 +501,9 @@ __device__ void ours_items(const FastArgs &a, const CUtensorMap *tmap, unsigned 
                                     if (f[k]) {
                                         ++nonzero;
                                         const u32 bin = f[k] - hbase;
-                                        if (bin < (u32)(sizeof(T) == 1 ? 256 : kHistWin))
+                                        if (bin < hbins)
                                             atomicAdd(&hist[bin], 1u);
-                                        else
+                                        else if (f[k] < 65536u)   // always true for valid outputs
                                             atomicAdd(&a.out_hist[f[k]], 1ull);
                                     }
                             }
@@ -501,13 +513,12 @@ __device__ void ours_items(const FastArgs &a, const CUtensorMap *tmap, unsigned 
                 // advance the z accumulators: A <- B + G(g), B <- C(g)
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
-                    accA[i][k] = (s == 0 ? 0u : accB[i][k]) + g[i][k];
+                    accA[i][k] = accB[i][k] + g[i][k];
                     accB[i][k] = c[k];
                 }
             }
-            __syncthreads();   // every thread is done with plane s-1 and the exchange rows
-            if (threadIdx.x == 0 && s >= 1 && s - 1 + G::NP < nplanes)
-                issue(s - 1 + G::NP);
+            // the next step's first barrier orders these G-plane reads before
+            // that step's G-plane writes
         }
         if (!ok) {
             if (threadIdx.x == 0) {
@@ -538,14 +549,15 @@ __global__ void __launch_bounds__(kThreads, 2) k_ours_fast(const __grid_constant
     extern __shared__ __align__(128) unsigned char smem_raw[];
     unsigned char *smem = smem_raw + ((128 - (lnfdev::smem_u32(smem_raw) & 127)) & 127);
     __shared__ int s_item, s_abort;
-    u32 *hist = reinterpret_cast<u32 *>(smem + G::RING + G::XBUF);
-    constexpr int bins = sizeof(T) == 1 ? 256 : kHistWin;
+    u32 *hist = reinterpret_cast<u32 *>(smem + G::RING + G::GPLANE);
+    constexpr int bins = sizeof(T) == 1 ? 256 : kHistWinO;
     for (int i = threadIdx.x; i < bins; i += blockDim.x)
         hist[i] = 0;
     if (threadIdx.x == 0)
         s_abort = 0;
     __syncthreads();
-    const u32 hbase = sizeof(T) == 1 ? 0u : a.prm->minv;
+    // nonzero outputs are >= T (the gate), so the window starts there
+    const u32 hbase = sizeof(T) == 1 ? 0u : max(a.prm->T, a.prm->minv);
     u32 nonzero = 0, written = 0;
     const u32 M = 2 * R + 1;
     const bool narrow = 3u * M * a.prm->maxv <= 65535u;

@@ -32,6 +32,7 @@ constexpr int kTX = 128;
 constexpr int kTY = kWarps * kRows;
 constexpr int kPF = 2;
 constexpr int kHistWin = 4096;
+constexpr int kL2Ahead = 6;              // planes prefetched into L2 beyond the shared-memory ring
 
 __device__ __forceinline__ int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
 
@@ -146,7 +147,7 @@ __device__ __forceinline__ void hist4(Hist2 &h, const u32 f[4])
                 const u32 b = f[k] - h.base;
                 if (b < h.bins)
                     atomicAdd(&h.sh[b], 1u);
-                else
+                else if (f[k] < 65536u)   // always true for valid outputs
                     atomicAdd(&h.gh[f[k]], 1ull);
             }
     }
@@ -204,6 +205,7 @@ __device__ void box_items(const Args2 &a, const CUtensorMap *tmap, unsigned char
     const DevParams &P = *a.prm;
     const u32 T_ = P.T;
     constexpr u32 M3 = (u32)(G::M * G::M * G::M);
+    typedef ExactDiv<M3, (unsigned long long)M3 * 65536ull> MDiv;
     u32 te = 0;
     if (ENT) {
         if (P.te_cfg == -2)
@@ -273,9 +275,16 @@ __device__ void box_items(const Args2 &a, const CUtensorMap *tmap, unsigned char
             mbar_arrive_expect_tx(&bars[slot], pbytes);
             tma_load_3d(ring + slot * G::PBYTES, tmap, &bars[slot], px0, py0, clampi(z0 - R + p, 0, a.nz - 1));
         };
-        if (threadIdx.x == 0)
+        auto prefetch = [&](int p) {   // thread 0 only: plane p into L2
+            if (p < nplanes)
+                tma_prefetch_3d(tmap, max(px0, 0), max(py0, 0), clampi(z0 - R + p, 0, a.nz - 1));
+        };
+        if (threadIdx.x == 0) {
             for (int p = 0; p < min(G::NP, nplanes); ++p)
                 issue(p);
+            for (int p = G::NP; p < G::NP + kL2Ahead; ++p)
+                prefetch(p);
+        }
         bool ok = true;
         for (int s = 0; s < z1 - z0; ++s) {
             const int pfirst = s == 0 ? 0 : s + 2 * R;
@@ -343,6 +352,11 @@ __device__ void box_items(const Args2 &a, const CUtensorMap *tmap, unsigned char
                 if (j < G::HS - 1 || hvalid_last)
                     bzp[(R + B.hrow[j]) * G::BW + 4 + B.hcol[j]] = B.hz[j];
             __syncthreads();
+            // plane s-1 was last read by the z line sums above: refill its slot
+            if (threadIdx.x == 0 && s >= 1 && s - 1 + G::NP < nplanes) {
+                issue(s - 1 + G::NP);
+                prefetch(s - 1 + G::NP + kL2Ahead);
+            }
             // ---- 2D box of Bz over the lane's 4 x 4 voxels
             u32 box[kRows][4];
 #pragma unroll
@@ -384,8 +398,9 @@ __device__ void box_items(const Args2 &a, const CUtensorMap *tmap, unsigned char
                 for (int k = 0; k < 4; ++k) {
                     if (ENT)
                         f[k] = (p0[k] >= T_ && (pass_all || box[i][k] > te)) ? p0[k] : 0u;
-                    else
-                        f[k] = (p0[k] >= T_ && box[i][k] >= M3 * T_) ? (2u * box[i][k] + M3) / (2u * M3) : 0u;
+                    else   // round(B / M^3) half up = floor((B + (M^3 - 1)/2) / M^3), M^3 odd
+                        f[k] = (p0[k] >= T_ && box[i][k] >= M3 * T_) ? MDiv::template div_add<(M3 - 1) / 2>(box[i][k])
+                                                                     : 0u;
                 }
                 const int y = y0 + kRows * warp + i, x = x0 + 4 * lane;
                 if (y < a.ny && x < a.nx) {
@@ -393,9 +408,8 @@ __device__ void box_items(const Args2 &a, const CUtensorMap *tmap, unsigned char
                     hist4(hist, f);
                 }
             }
-            __syncthreads();   // plane s-1 and the Bz plane are free again
-            if (threadIdx.x == 0 && s >= 1 && s - 1 + G::NP < nplanes)
-                issue(s - 1 + G::NP);
+            // the next step's first barrier orders these Bz-plane reads before
+            // that step's Bz-plane writes
         }
         if (!ok) {
             if (threadIdx.x == 0) {
@@ -432,7 +446,7 @@ struct TapPack {
 
 template <typename T, int R, int FILTER>
 __device__ void tap_items(const Args2 &a, const CUtensorMap *tmap, unsigned char *smem, int *s_item, int *s_abort,
-                          Hist2 &hist)
+                          Hist2 &hist, const u32 *recip)
 {
     using namespace lnfdev;
     typedef Geo2<T, R> G;
@@ -478,9 +492,16 @@ __device__ void tap_items(const Args2 &a, const CUtensorMap *tmap, unsigned char
             mbar_arrive_expect_tx(&bars[slot], pbytes);
             tma_load_3d(ring + slot * G::PBYTES, tmap, &bars[slot], px0, py0, clampi(z0 - R + p, 0, a.nz - 1));
         };
-        if (threadIdx.x == 0)
+        auto prefetch = [&](int p) {   // thread 0 only: plane p into L2
+            if (p < nplanes)
+                tma_prefetch_3d(tmap, max(px0, 0), max(py0, 0), clampi(z0 - R + p, 0, a.nz - 1));
+        };
+        if (threadIdx.x == 0) {
             for (int p = 0; p < min(G::NP, nplanes); ++p)
                 issue(p);
+            for (int p = G::NP; p < G::NP + kL2Ahead; ++p)
+                prefetch(p);
+        }
         bool ok = true;
         for (int s = 0; s < z1 - z0; ++s) {
             const int pfirst = s == 0 ? 0 : s + 2 * R;
@@ -492,6 +513,11 @@ __device__ void tap_items(const Args2 &a, const CUtensorMap *tmap, unsigned char
             if (*s_abort) {
                 ok = false;
                 break;
+            }
+            // plane s-1 was last read at step s-1, which every thread has finished
+            if (threadIdx.x == 0 && s >= 1 && s - 1 + G::NP < nplanes) {
+                issue(s - 1 + G::NP);
+                prefetch(s - 1 + G::NP + kL2Ahead);
             }
             if (border)
                 for (int p = pfirst; p <= s + 2 * R; ++p)
@@ -618,6 +644,10 @@ __device__ void tap_items(const Args2 &a, const CUtensorMap *tmap, unsigned char
                 }
             }
             // ---- gate, round, store, histogram
+            // round(sm / n) half up = floor((sm + floor(n/2)) / n) = (x * recip[n]) >> 32
+            // with recip[n] = ceil(2^32 / n): exact when x e < 2^32 (e = recip n - 2^32 < n);
+            // x < n 2^16 gives x e < n^2 2^16, so counts below 256 use the table
+            // and larger ones (sigma at radius >= 3) divide
             const int z = z0 + s;
 #pragma unroll
             for (int i = 0; i < kRows; ++i) {
@@ -626,7 +656,9 @@ __device__ void tap_items(const Args2 &a, const CUtensorMap *tmap, unsigned char
                 for (int k = 0; k < 4; ++k) {
                     const u32 n = TP::PACK ? (acc[i][k] & ((1u << TP::CS) - 1u)) : cnt[i][k];
                     const u32 sm = TP::PACK ? (acc[i][k] >> TP::CS) : acc[i][k];
-                    f[k] = (n && p0[i][k] >= T_ && (u64)sm >= (u64)n * T_) ? (2u * sm + n) / (2u * n) : 0u;
+                    const u32 x = sm + (n >> 1);
+                    const u32 q = n == 1 ? sm : (n < 256 ? __umulhi(x, recip[n]) : x / n);
+                    f[k] = (n && p0[i][k] >= T_ && (u64)sm >= (u64)n * T_) ? q : 0u;
                 }
                 const int y = y0 + kRows * warp + i, x = x0 + 4 * lane;
                 if (y < a.ny && x < a.nx) {
@@ -634,9 +666,6 @@ __device__ void tap_items(const Args2 &a, const CUtensorMap *tmap, unsigned char
                     hist4(hist, f);
                 }
             }
-            __syncthreads();
-            if (threadIdx.x == 0 && s >= 1 && s - 1 + G::NP < nplanes)
-                issue(s - 1 + G::NP);
         }
         if (!ok) {
             if (threadIdx.x == 0) {
@@ -668,7 +697,8 @@ struct K2Smem {
     static constexpr int HWIN = sizeof(T) == 1 ? 256 : (FILTER == LNF_ENTROPY ? kBoxWin : kHistWin);
     static constexpr int LWIN = sizeof(T) == 1 ? 256 : kBoxWin;
     static constexpr int HISTB = HWIN * 4;
-    static constexpr int LUTB = FILTER == LNF_ENTROPY ? LWIN * 4 : 0;
+    static constexpr int NTAB = (2 * R + 1) * (2 * R + 1) * (2 * R + 1) + 1;   // counts 0 .. M^3
+    static constexpr int LUTB = FILTER == LNF_ENTROPY ? LWIN * 4 : (BOX ? 0 : ((NTAB * 4 + 15) / 16) * 16);
     static constexpr int MAIN = G::RING + (BOX ? G::BZ : 0) + G::NP * 8;
     static constexpr int TOTAL = 128 + MAIN + 64 + HISTB + LUTB;
 };
@@ -701,6 +731,9 @@ __global__ void __launch_bounds__(kThreads, K2Smem<T, R, FILTER>::BOX ? 1 : 2)
         for (int i = threadIdx.x; i < nl; i += blockDim.x)
             lut_sh[i] = (lut_base + i < (sizeof(T) == 1 ? 256u : 65536u)) ? a.lut[lut_base + i] : 0u;
     }
+    if (!S::BOX)   // reciprocals of the voxel counts a tap filter can select
+        for (int n = threadIdx.x; n < S::NTAB; n += blockDim.x)
+            lut_sh[n] = (n <= 1 || n >= 256) ? 0u : (u32)((0x100000000ull + n - 1) / n);
     if (threadIdx.x == 0)
         s_abort = 0;
     __syncthreads();
@@ -709,7 +742,7 @@ __global__ void __launch_bounds__(kThreads, K2Smem<T, R, FILTER>::BOX ? 1 : 2)
     else if (FILTER == LNF_ENTROPY)
         box_items<T, R, true>(a, &tmap, smem, &s_item, &s_abort, h, lut_sh, lut_base);
     else
-        tap_items<T, R, FILTER>(a, &tmap, smem, &s_item, &s_abort, h);
+        tap_items<T, R, FILTER>(a, &tmap, smem, &s_item, &s_abort, h, lut_sh);
     if (a.out_hist) {
         __syncthreads();
         for (int i = threadIdx.x; i < (int)bins; i += blockDim.x)

@@ -72,7 +72,7 @@ __device__ __forceinline__ void hist_add(u32 *sh_hist, const HistState &hs, u64 
         u32 o = v - hs.base;
         if (o < (u32)kHistWin16)
             atomicAdd(&sh_hist[o], 1u);
-        else
+        else if (v < 65536u)   // always true for valid outputs
             atomicAdd(&gh[v], 1ull);
     }
 }

@@ -81,6 +81,33 @@ struct FilterPack {
 #define LNF_DERR_TIMEOUT 1u
 #define LNF_DERR_BADJOB 2u
 
+// ----------------------------------------------------------------- exact division
+// floor(x / D) for 0 <= x <= XMAX as one 64-bit multiply (and a shift):
+// q = (x * m) >> (32 + s) with m = ceil(2^(32+s) / D).  Writing x = qD + r,
+// x m / 2^(32+s) = x / D + x e / (D 2^(32+s)) with e = m D - 2^(32+s) < D, so
+// the floor is exact whenever XMAX * e < 2^(32+s) (Granlund and Montgomery,
+// "Division by invariant integers using multiplication", 1994); the smallest
+// such s is chosen at compile time and the condition is checked statically.
+template <unsigned long long D, unsigned long long XMAX>
+struct ExactDiv {
+    static constexpr unsigned long long mult(int s) { return ((1ull << (32 + s)) + D - 1) / D; }
+    static constexpr bool ok(int s)
+    {
+        return mult(s) < (1ull << 32) && (mult(s) * D - (1ull << (32 + s))) * XMAX < (1ull << (32 + s));
+    }
+    static constexpr int pick(int s) { return s > 20 ? -1 : (ok(s) ? s : pick(s + 1)); }
+    static constexpr int S = pick(0);
+    static_assert(S >= 0, "no exact 32-bit multiplier for this divisor and range");
+    static constexpr unsigned long long M = mult(S < 0 ? 0 : S);
+    // floor((x + add) / D); add is folded into the multiply-add
+    template <unsigned long long ADD>
+    static __device__ __forceinline__ unsigned int div_add(unsigned int x)
+    {
+        static_assert(ADD <= XMAX, "offset beyond the proven range");
+        return (unsigned int)(((unsigned long long)x * M + ADD * M) >> (32 + S));
+    }
+};
+
 // ----------------------------------------------------------------- PTX helpers
 namespace lnfdev {
 
@@ -162,6 +189,16 @@ __device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, u
         "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
         ::"r"(smem_u32(dst)), "l"(reinterpret_cast<u64>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
         : "memory");
+}
+
+// TMA: prefetch a 3D box of the tensor map into L2 (no shared memory, no
+// completion to wait for); used to keep DRAM reads in flight further ahead
+// than the shared-memory ring allows.
+__device__ __forceinline__ void tma_prefetch_3d(const CUtensorMap *map, int x, int y, int z)
+{
+    asm volatile("cp.async.bulk.prefetch.tensor.3d.L2.global [%0, {%1, %2, %3}];"
+                 ::"l"(reinterpret_cast<u64>(map)), "r"(x), "r"(y), "r"(z)
+                 : "memory");
 }
 
 __device__ __forceinline__ void prefetch_tmap(const CUtensorMap *map)
