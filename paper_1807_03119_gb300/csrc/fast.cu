@@ -13,14 +13,23 @@
 // Mapping: a CTA owns a 128 x 32 output tile and marches along z over a chunk
 // of planes; the input planes (tile + halo) stream into a ring of shared
 // memory slots by TMA.  Each lane owns 4 consecutive columns of 4 rows.
+// Shared-memory bandwidth is what bounds this kernel, so each value is read
+// from shared memory as few times as possible:
 //   * z: Lz is a running sum held in registers (one term in, one out per
 //     step); the output needs two accumulators per voxel, A = G(z-1) + C(z-2)
-//     and B = C(z-1), so the z direction costs no shared memory at all.
-//   * y: Ly is a running sum along the lane's rows.
-//   * x: Lx from the row words.
-//   * G of the tile goes to a shared G plane; the one-voxel ring around the
-//     tile (324 voxels) is computed voxel by voxel, spread over all threads;
-//     C = T_x T_y G is then read from the plane.  Two barriers per step.
+//     and B = C(z-1), so the z direction costs no shared memory beyond the
+//     new and the old plane.
+//   * y: a lane reads its rows and R rows on each side of the current plane
+//     once; Ly is a running sum down that window, and the lane's own rows
+//     are kept as P0 for the next step's outputs.
+//   * x: Lx takes the neighbouring columns from the adjacent lanes
+//     (shuffles); lanes 0 and 31 read the columns beyond the tile.
+//   * C = T_x T_y G: T_y from the lane's rows and the neighbouring warps'
+//     boundary rows (the only G values that pass through shared memory),
+//     T_x across lanes.  The one-voxel ring around the tile is computed by
+//     the first and last warp (rows above and below, vectorised) and by a
+//     few lanes per warp (the two ring columns, voxel by voxel).
+//     Two barriers per step.
 // Line sums are formed on packed pairs of 16-bit lanes (two voxels per 32-bit
 // add) whenever 3M * max <= 65535, which keeps every lane exact; otherwise
 // the same code runs on unpacked 32-bit pairs.
@@ -109,10 +118,7 @@ struct Ld<uint8_t> {
 
 constexpr int kPFo = 1;                  // planes prefetched into shared memory (two CTAs per SM fit)
 constexpr int kL2Ahead = 6;              // planes prefetched into L2 beyond the shared-memory ring
-constexpr int kHistWinO = 2048;          // output histogram window (16-bit data)
 constexpr int kGW = kTX + 8;             // G plane row: columns -1 .. 128 at offsets 3 .. 132
-constexpr int kHalo = 2 * (kTX + 2) + 2 * kTY;   // voxels of the ring around the tile
-constexpr int kHS = (kHalo + kThreads - 1) / kThreads;
 
 template <typename T, int R>
 struct FGeo {
@@ -126,7 +132,10 @@ struct FGeo {
     static constexpr int M = 2 * R + 1;
     static constexpr int RING = NP * PBYTES;
     static constexpr int GPLANE = (kTY + 2) * kGW * 4;
-    static constexpr int HIST = (sizeof(T) == 1 ? 256 : kHistWinO) * 4;
+    // output histogram window: all 8-bit levels; 4096 16-bit levels where two
+    // CTAs per SM still fit, else 2048
+    static constexpr int HWIN = sizeof(T) == 1 ? 256 : (R <= 2 ? 4096 : 2048);
+    static constexpr int HIST = (HWIN + 32) * 4;   // + one bin per lane counting zeros
     static constexpr int SMEM = 128 + RING + GPLANE + HIST + NP * 8 + 64;
 };
 
@@ -196,26 +205,6 @@ __device__ __forceinline__ typename PK::P window_sum(const typename PK::P *wd)
     return acc;
 }
 
-// Lx of the lane's pairs A (c0, c0+1) and B (c0+2, c0+3)
-template <typename T, int R, class PK>
-__device__ __forceinline__ void lx_pairs(const unsigned char *row, int c0, typename PK::P &lxA, typename PK::P &lxB)
-{
-    typedef typename PK::P P;
-    constexpr int A = (R + 1) / 2;
-    constexpr int JL = -A, JH = 1 + A;
-    P w[JH - JL + 1];
-    u32 q0, q1;
-    Ld<T>::quad(row, c0, q0, q1);
-    w[0 - JL] = PK::word(q0);
-    w[1 - JL] = PK::word(q1);
-#pragma unroll
-    for (int j = JL; j <= JH; ++j)
-        if (j != 0 && j != 1)
-            w[j - JL] = PK::word(Ld<T>::pair(row, c0 + 2 * j));
-    lxA = window_sum<R, PK>(&w[0 - JL]);
-    lxB = window_sum<R, PK>(&w[1 - JL]);
-}
-
 template <typename T, class PK>
 __device__ __forceinline__ void quad_pairs(const unsigned char *row, int c0, typename PK::P &a, typename PK::P &b)
 {
@@ -245,13 +234,60 @@ struct FastArgs {
     u32 *err;
 };
 
+// the ring-column cell (tile column -1 or kTX, tile row -1 .. kTY) a lane
+// computes: warp w takes tile rows 4w-1 .. 4w+2 (the last warp also kTY-1 and
+// kTY), two lanes per row, one per side; consecutive rows fall in distinct banks
+__device__ __forceinline__ bool ring_cell(int warp, int lane, int &row, int &col)
+{
+    const int j = lane >> 1;
+    row = kRows * warp - 1 + j;
+    col = (lane & 1) ? kTX : -1;
+    return j < (warp == kWarps - 1 ? kRows + 2 : kRows);
+}
+
+// Lx of the lane's pairs A (c0, c0+1) and B (c0+2, c0+3) of one row, from the
+// lane's own words w0, w1 and its neighbours' words (shuffles); lanes 0 and 31
+// take the words beyond the tile from the row itself: the quad at column ec,
+// which every lane of a half-warp shares (one broadcast read, no branch)
+template <typename T, int R, class PK>
+__device__ __forceinline__ void lx_lanes(const unsigned char *row, int ec, int lane, u32 w0, u32 w1,
+                                         typename PK::P &lxA, typename PK::P &lxB)
+{
+    typedef typename PK::P P;
+    constexpr int A = (R + 1) / 2;   // words needed on each side
+    u32 e0, e1;
+    Ld<T>::quad(row, ec, e0, e1);
+    u32 l1 = __shfl_up_sync(0xFFFFFFFFu, w1, 1), r0 = __shfl_down_sync(0xFFFFFFFFu, w0, 1);
+    if (lane == 0)
+        l1 = e1;
+    if (lane == 31)
+        r0 = e0;
+    P w[2 * A + 2];   // w[A + k] = pair at column c0 + 2k
+    w[A - 1] = PK::word(l1);
+    w[A] = PK::word(w0);
+    w[A + 1] = PK::word(w1);
+    w[A + 2] = PK::word(r0);
+    if (A == 2) {
+        u32 l0 = __shfl_up_sync(0xFFFFFFFFu, w0, 1), r1 = __shfl_down_sync(0xFFFFFFFFu, w1, 1);
+        if (lane == 0)
+            l0 = e0;
+        if (lane == 31)
+            r1 = e1;
+        w[0] = PK::word(l0);
+        w[2 * A + 1] = PK::word(r1);
+    }
+    lxA = window_sum<R, PK>(&w[A]);
+    lxB = window_sum<R, PK>(&w[A + 1]);
+}
+
 template <typename T, int R, class PK>
 __device__ void ours_items(const FastArgs &a, const CUtensorMap *tmap, unsigned char *smem, int *s_item,
-                           int *s_abort, u32 &nonzero, u32 &written, u32 *hist, u32 hbase)
+                           int *s_abort, u32 *hist, u32 hbase)
 {
     using namespace lnfdev;
     typedef FGeo<T, R> G;
     typedef typename PK::P P;
+    constexpr int NW = kRows + 2 * R;                 // rows a lane reads per plane: its own and R each side
     unsigned char *ring = smem;
     u32 *gp = reinterpret_cast<u32 *>(smem + G::RING);                      // G plane
     u64 *bars = reinterpret_cast<u64 *>(smem + G::RING + G::GPLANE + G::HIST);
@@ -261,33 +297,32 @@ __device__ void ours_items(const FastArgs &a, const CUtensorMap *tmap, unsigned 
     const int r0 = G::H + kRows * warp;                // first own row (plane coords)
     const int gr0 = 1 + kRows * warp;                  // first own row in the G plane
     const int gc0 = 4 + 4 * lane;                      // first own column in the G plane
+    // the quad beyond the tile (read by lanes 0 / 31, shared by their half-warps)
+    const int ec = lane < 16 ? G::XH - 4 : G::XH + kTX;
+    const int egc = lane < 16 ? 3 : 4 + kTX;           // ... and its ring column in the G plane
+    // the first and the last warp also compute the ring row above / below the tile
+    const bool xtop = warp == 0, xbot = warp == kWarps - 1;
+    const int xr = xtop ? r0 - 1 : r0 + kRows;         // plane row of that ring row
+    const int xly = xtop ? r0 - R - 1 : r0 + kRows + R;   // the row its Ly needs beyond the window
+    const int xg = xtop ? 0 : kTY + 1;                 // its G-plane row
+    int hr = 0, hc = 0;
+    const bool hv = ring_cell(warp, lane, hr, hc);     // ring-column cell of this lane, if any;
+    if (!hv)                                           // the others shadow lane 0 / 1 (same reads)
+        ring_cell(warp, lane & 1, hr, hc);
+    const int hpr = G::H + hr, hpc = G::XH + hc;       // ... in plane coordinates
+
     const u32 T_ = a.prm->T;
     const u32 KT = 27u * G::M * T_;
     // round(U / 27M) half up = floor((2U + 27M) / 54M) = floor((U + (27M - 1)/2) / 27M)
     // (27M is odd); U < 27M * 65536 for any 16-bit input
     typedef ExactDiv<27ull * G::M, 27ull * G::M * 65536ull> Div;
     constexpr unsigned long long HALF = (27ull * G::M - 1) / 2;
-    const u32 hbins = sizeof(T) == 1 ? 256u : (u32)kHistWinO;
-
-    // the ring voxels this thread computes G for (tile coordinates, -1 .. 128 / 32)
-    int hrow[kHS], hcol[kHS];
-    bool hval[kHS];
-#pragma unroll
-    for (int j = 0; j < kHS; ++j) {
-        const int d = threadIdx.x + j * kThreads;
-        hval[j] = d < kHalo;
-        int row = 0, col = 0;
-        if (d < 2 * (kTX + 2)) {
-            row = d < kTX + 2 ? -1 : kTY;
-            col = d % (kTX + 2) - 1;
-        } else if (d < kHalo) {
-            const int e = d - 2 * (kTX + 2);
-            row = e >> 1;
-            col = (e & 1) ? kTX : -1;
-        }
-        hrow[j] = row;
-        hcol[j] = col;
-    }
+    const u32 hbins = G::HWIN;
+    const u32 hlim = hbase + hbins;   // nonzero outputs lie in [hbase, 65535]
+    const u32 hzero = hbins + lane;   // this lane's zero bin (zeros never meet in one bin)
+    // outputs are averages, so none exceeds maxv: values above the window occur
+    // only when maxv >= hbase + hbins
+    const bool hcheck = a.prm->maxv >= hlim;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < G::NP; ++s)
@@ -335,22 +370,28 @@ __device__ void ours_items(const FastArgs &a, const CUtensorMap *tmap, unsigned 
         }
 
         P lzA[kRows], lzB[kRows];                 // running z line sums of the own pairs
-        u32 lzh[kHS];                             // ... and of the ring voxels
+        P lzxA = PK::zero(), lzxB = PK::zero();   // ... of the ring row (first / last warp)
+        u32 lzh = 0;                              // ... of the ring-column cell
         u32 accA[kRows][4], accB[kRows][4];       // z accumulators
 #pragma unroll
-        for (int i = 0; i < kRows; ++i)
+        for (int i = 0; i < kRows; ++i) {
 #pragma unroll
             for (int k = 0; k < 4; ++k)
                 accB[i][k] = 0;
+        }
         bool ok = true;
 
         for (int s = 0; s < nsteps; ++s) {
             // planes needed: s-1 (old) .. s+2R (new); plane p is the (p / NP)-th
             // load into its slot since the barriers were initialised
+            // one thread waits for the TMA completions; the barrier then
+            // orders the data before every thread's reads (and keeps the other
+            // warps off the issue slots while the planes arrive)
             const int pfirst = s == 0 ? 0 : s + 2 * R;
-            for (int p = pfirst; p <= s + 2 * R; ++p)
-                if (!mbar_wait_bounded(&bars[p % G::NP], (u32)((p / G::NP) & 1), a.err))
-                    *s_abort = 1;
+            if (threadIdx.x == 0)
+                for (int p = pfirst; p <= s + 2 * R; ++p)
+                    if (!mbar_wait_bounded(&bars[p % G::NP], (u32)((p / G::NP) & 1), a.err))
+                        *s_abort = 1;
             __syncthreads();
             if (*s_abort) {
                 ok = false;
@@ -370,9 +411,8 @@ __device__ void ours_items(const FastArgs &a, const CUtensorMap *tmap, unsigned 
                     lzA[i] = PK::zero();
                     lzB[i] = PK::zero();
                 }
-#pragma unroll
-                for (int j = 0; j < kHS; ++j)
-                    lzh[j] = 0;
+                lzxA = lzxB = PK::zero();
+                lzh = 0;
                 for (int d = 0; d <= 2 * R; ++d) {
                     const unsigned char *pl = ring + (d % G::NP) * G::PBYTES;
 #pragma unroll
@@ -382,9 +422,13 @@ __device__ void ours_items(const FastArgs &a, const CUtensorMap *tmap, unsigned 
                         lzA[i] = PK::add3(lzA[i], qa, PK::zero());
                         lzB[i] = PK::add3(lzB[i], qb, PK::zero());
                     }
-#pragma unroll
-                    for (int j = 0; j < kHS; ++j)
-                        lzh[j] += ld1<T>(pl + (G::H + hrow[j]) * G::ROWB, G::XH + hcol[j]);
+                    if (xtop || xbot) {
+                        P qa, qb;
+                        quad_pairs<T, PK>(pl + xr * G::ROWB, c0, qa, qb);
+                        lzxA = PK::add3(lzxA, qa, PK::zero());
+                        lzxB = PK::add3(lzxB, qb, PK::zero());
+                    }
+                    lzh += ld1<T>(pl + hpr * G::ROWB, hpc);
                 }
             } else {
 #pragma unroll
@@ -395,53 +439,80 @@ __device__ void ours_items(const FastArgs &a, const CUtensorMap *tmap, unsigned 
                     lzA[i] = PK::addsub(lzA[i], na, oa);
                     lzB[i] = PK::addsub(lzB[i], nb, ob);
                 }
-#pragma unroll
-                for (int j = 0; j < kHS; ++j) {
-                    const int rr = (G::H + hrow[j]) * G::ROWB, cc = G::XH + hcol[j];
-                    lzh[j] += ld1<T>(pn + rr, cc) - ld1<T>(po + rr, cc);
+                if (xtop || xbot) {
+                    P na, nb, oa, ob;
+                    quad_pairs<T, PK>(pn + xr * G::ROWB, c0, na, nb);
+                    quad_pairs<T, PK>(po + xr * G::ROWB, c0, oa, ob);
+                    lzxA = PK::addsub(lzxA, na, oa);
+                    lzxB = PK::addsub(lzxB, nb, ob);
                 }
+                lzh += ld1<T>(pn + hpr * G::ROWB, hpc) - ld1<T>(po + hpr * G::ROWB, hpc);
             }
 
-            // ---- G of the own voxels (packed pairs) -> registers and the G plane
+            // ---- the lane's window of plane g: rows r0-R .. r0+3+R, read once
+            u32 rw[NW][2];
+#pragma unroll
+            for (int j = 0; j < NW; ++j)
+                Ld<T>::quad(pg + (r0 - R + j) * G::ROWB, c0, rw[j][0], rw[j][1]);
+
+            // ---- G of the own voxels (packed pairs): Ly running down the window
             u32 g[kRows][4];
             P lyA = PK::zero(), lyB = PK::zero();
 #pragma unroll
-            for (int d = -R; d <= R; ++d) {
-                P qa, qb;
-                quad_pairs<T, PK>(pg + (r0 + d) * G::ROWB, c0, qa, qb);
-                lyA = PK::add3(lyA, qa, PK::zero());
-                lyB = PK::add3(lyB, qb, PK::zero());
+            for (int j = 0; j <= 2 * R; ++j) {
+                lyA = PK::add3(lyA, PK::word(rw[j][0]), PK::zero());
+                lyB = PK::add3(lyB, PK::word(rw[j][1]), PK::zero());
             }
+            const P ly0A = lyA, ly0B = lyB;
 #pragma unroll
             for (int i = 0; i < kRows; ++i) {
                 if (i > 0) {
-                    P na, nb, oa, ob;
-                    quad_pairs<T, PK>(pg + (r0 + i + R) * G::ROWB, c0, na, nb);
-                    quad_pairs<T, PK>(pg + (r0 + i - R - 1) * G::ROWB, c0, oa, ob);
-                    lyA = PK::addsub(lyA, na, oa);
-                    lyB = PK::addsub(lyB, nb, ob);
+                    lyA = PK::addsub(lyA, PK::word(rw[i + 2 * R][0]), PK::word(rw[i - 1][0]));
+                    lyB = PK::addsub(lyB, PK::word(rw[i + 2 * R][1]), PK::word(rw[i - 1][1]));
                 }
                 P lxA, lxB;
-                lx_pairs<T, R, PK>(pg + (r0 + i) * G::ROWB, c0, lxA, lxB);
+                lx_lanes<T, R, PK>(pg + (r0 + i) * G::ROWB, ec, lane, rw[R + i][0], rw[R + i][1], lxA, lxB);
                 const P gA = PK::add3(lxA, lyA, lzA[i]);
                 const P gB = PK::add3(lxB, lyB, lzB[i]);
                 g[i][0] = PK::lo(gA);
                 g[i][1] = PK::hi(gA);
                 g[i][2] = PK::lo(gB);
                 g[i][3] = PK::hi(gB);
-                *reinterpret_cast<uint4 *>(gp + (gr0 + i) * kGW + gc0) = make_uint4(g[i][0], g[i][1], g[i][2], g[i][3]);
             }
-            // ---- G of the ring voxels, one voxel at a time
-#pragma unroll
-            for (int j = 0; j < kHS; ++j) {
-                if (!hval[j])
-                    continue;
-                const int pr = G::H + hrow[j], pc = G::XH + hcol[j];
-                u32 gx = lzh[j];
+            // rows other warps need: the first and the last own row
+            if (warp > 0)
+                *reinterpret_cast<uint4 *>(gp + gr0 * kGW + gc0) = make_uint4(g[0][0], g[0][1], g[0][2], g[0][3]);
+            if (warp < kWarps - 1)
+                *reinterpret_cast<uint4 *>(gp + (gr0 + kRows - 1) * kGW + gc0) =
+                    make_uint4(g[kRows - 1][0], g[kRows - 1][1], g[kRows - 1][2], g[kRows - 1][3]);
+            // ---- the ring row (first / last warp)
+            if (xtop || xbot) {
+                u32 ea, eb;
+                Ld<T>::quad(pg + xly * G::ROWB, c0, ea, eb);
+                P xlyA, xlyB, lxA, lxB;
+                if (xtop) {
+                    xlyA = PK::addsub(ly0A, PK::word(ea), PK::word(rw[2 * R][0]));
+                    xlyB = PK::addsub(ly0B, PK::word(eb), PK::word(rw[2 * R][1]));
+                    lx_lanes<T, R, PK>(pg + xr * G::ROWB, ec, lane, rw[R - 1][0], rw[R - 1][1], lxA, lxB);
+                } else {
+                    xlyA = PK::addsub(lyA, PK::word(ea), PK::word(rw[kRows - 1][0]));
+                    xlyB = PK::addsub(lyB, PK::word(eb), PK::word(rw[kRows - 1][1]));
+                    lx_lanes<T, R, PK>(pg + xr * G::ROWB, ec, lane, rw[R + kRows][0], rw[R + kRows][1], lxA,
+                                       lxB);
+                }
+                const P gA = PK::add3(lxA, xlyA, lzxA);
+                const P gB = PK::add3(lxB, xlyB, lzxB);
+                *reinterpret_cast<uint4 *>(gp + xg * kGW + gc0) =
+                    make_uint4(PK::lo(gA), PK::hi(gA), PK::lo(gB), PK::hi(gB));
+            }
+            // ---- the ring-column cell, one voxel
+            {
+                u32 gx = lzh;
 #pragma unroll
                 for (int d = -R; d <= R; ++d)
-                    gx += ld1<T>(pg + pr * G::ROWB, pc + d) + ld1<T>(pg + (pr + d) * G::ROWB, pc);
-                gp[(1 + hrow[j]) * kGW + 4 + hcol[j]] = gx;
+                    gx += ld1<T>(pg + hpr * G::ROWB, hpc + d) + ld1<T>(pg + (hpr + d) * G::ROWB, hpc);
+                if (hv)
+                    gp[(1 + hr) * kGW + 4 + hc] = gx;
             }
             __syncthreads();
             // plane s-1 (the oldest) is no longer read: refill its slot
@@ -450,27 +521,47 @@ __device__ void ours_items(const FastArgs &a, const CUtensorMap *tmap, unsigned 
                 prefetch(s - 1 + G::NP + kL2Ahead);
             }
 
-            // ---- C = T_x T_y G from the G plane; outputs at z = g - 1 once three G planes exist
-            u32 tx_[kRows + 2][4];
+            // ---- C = T_x T_y G: T_y from the own rows and the neighbouring rows,
+            // T_x across lanes (the edge lanes take the ring columns)
+            const uint4 gn = *reinterpret_cast<const uint4 *>(gp + (gr0 - 1) * kGW + gc0);
+            const uint4 gs = *reinterpret_cast<const uint4 *>(gp + (gr0 + kRows) * kGW + gc0);
+            u32 eg[kRows + 2];
 #pragma unroll
-            for (int rr = 0; rr < kRows + 2; ++rr) {   // G rows gr0 - 1 .. gr0 + kRows
-                const u32 *row = gp + (gr0 - 1 + rr) * kGW + gc0;
-                const uint4 m = *reinterpret_cast<const uint4 *>(row);
-                const u32 l = row[-1], r = row[4];
-                tx_[rr][0] = l + m.y;
-                tx_[rr][1] = m.x + m.z;
-                tx_[rr][2] = m.y + m.w;
-                tx_[rr][3] = m.z + r;
-            }
+            for (int d = 0; d < kRows + 2; ++d)
+                eg[d] = gp[(gr0 - 1 + d) * kGW + egc];
             const int zout = z0 - 2 + s;
             const bool emit = s >= 2;
             const unsigned char *pc = ring + ((s + R - 1) % G::NP) * G::PBYTES;   // plane z = g - 1
 #pragma unroll
             for (int i = 0; i < kRows; ++i) {
-                u32 c[4];
+                u32 ty_[4];
+                if (i == 0) {
+                    ty_[0] = gn.x + g[1][0];
+                    ty_[1] = gn.y + g[1][1];
+                    ty_[2] = gn.z + g[1][2];
+                    ty_[3] = gn.w + g[1][3];
+                } else if (i == kRows - 1) {
+                    ty_[0] = g[i - 1][0] + gs.x;
+                    ty_[1] = g[i - 1][1] + gs.y;
+                    ty_[2] = g[i - 1][2] + gs.z;
+                    ty_[3] = g[i - 1][3] + gs.w;
+                } else {
 #pragma unroll
-                for (int k = 0; k < 4; ++k)
-                    c[k] = tx_[i][k] + tx_[i + 2][k];
+                    for (int k = 0; k < 4; ++k)
+                        ty_[k] = g[i - 1][k] + g[i + 1][k];
+                }
+                const u32 tye = eg[i] + eg[i + 2];
+                u32 tl = __shfl_up_sync(0xFFFFFFFFu, ty_[3], 1);
+                u32 tr = __shfl_down_sync(0xFFFFFFFFu, ty_[0], 1);
+                if (lane == 0)
+                    tl = tye;
+                if (lane == 31)
+                    tr = tye;
+                u32 c[4];
+                c[0] = tl + ty_[1];
+                c[1] = ty_[0] + ty_[2];
+                c[2] = ty_[1] + ty_[3];
+                c[3] = ty_[2] + tr;
                 if (emit) {
                     const int y = y0 + kRows * warp + i;
                     const int x = x0 + 4 * lane;
@@ -492,20 +583,25 @@ __device__ void ours_items(const FastArgs &a, const CUtensorMap *tmap, unsigned 
                             *reinterpret_cast<u32 *>(static_cast<uint8_t *>(a.out) + o) =
                                 f[0] | (f[1] << 8) | (f[2] << 16) | (f[3] << 24);
                         }
-                        written += 4;
                         if (hist) {
-                            const bool nz = (f[0] | f[1] | f[2] | f[3]) != 0;
-                            if (__any_sync(__activemask(), nz)) {
+                            // window bins for nonzero outputs (hbase >= 1), the
+                            // lane's zero bin for zeros; values above the window
+                            // (rare) go to the global histogram
+                            if (hcheck && __any_sync(__activemask(), max(max(f[0], f[1]), max(f[2], f[3])) >= hlim)) {
+#pragma unroll
+                                for (int k = 0; k < 4; ++k) {
+                                    if (f[k] >= hlim) {
+                                        if (f[k] < 65536u)   // always true for valid outputs
+                                            atomicAdd(&a.out_hist[f[k]], 1ull);
+                                    } else {
+                                        atomicAdd(&hist[min(f[k] - hbase, hzero)], 1u);
+                                    }
+                                }
+                            } else {
+                                // f - hbase wraps to a large value for a zero
 #pragma unroll
                                 for (int k = 0; k < 4; ++k)
-                                    if (f[k]) {
-                                        ++nonzero;
-                                        const u32 bin = f[k] - hbase;
-                                        if (bin < hbins)
-                                            atomicAdd(&hist[bin], 1u);
-                                        else if (f[k] < 65536u)   // always true for valid outputs
-                                            atomicAdd(&a.out_hist[f[k]], 1ull);
-                                    }
+                                    atomicAdd(&hist[min(f[k] - hbase, hzero)], 1u);
                             }
                         }
                     }
@@ -550,34 +646,36 @@ __global__ void __launch_bounds__(kThreads, 2) k_ours_fast(const __grid_constant
     unsigned char *smem = smem_raw + ((128 - (lnfdev::smem_u32(smem_raw) & 127)) & 127);
     __shared__ int s_item, s_abort;
     u32 *hist = reinterpret_cast<u32 *>(smem + G::RING + G::GPLANE);
-    constexpr int bins = sizeof(T) == 1 ? 256 : kHistWinO;
-    for (int i = threadIdx.x; i < bins; i += blockDim.x)
+    constexpr int bins = G::HWIN;
+    for (int i = threadIdx.x; i < bins + 32; i += blockDim.x)
         hist[i] = 0;
     if (threadIdx.x == 0)
         s_abort = 0;
     __syncthreads();
-    // nonzero outputs are >= T (the gate), so the window starts there
-    const u32 hbase = sizeof(T) == 1 ? 0u : max(a.prm->T, a.prm->minv);
-    u32 nonzero = 0, written = 0;
+    // a nonzero output passed the gate and averages voxels >= minv, so it is
+    // >= max(T, minv); the window starts there (and at 1 at least, keeping the
+    // zeros out of it)
+    const u32 hbase = sizeof(T) == 1 ? 1u : max(1u, max(a.prm->T, a.prm->minv));
     const u32 M = 2 * R + 1;
     const bool narrow = 3u * M * a.prm->maxv <= 65535u;
     if (narrow)
-        ours_items<T, R, Narrow>(a, &tmap, smem, &s_item, &s_abort, nonzero, written, a.out_hist ? hist : nullptr,
+        ours_items<T, R, Narrow>(a, &tmap, smem, &s_item, &s_abort, a.out_hist ? hist : nullptr,
                                  hbase);
     else
-        ours_items<T, R, Wide>(a, &tmap, smem, &s_item, &s_abort, nonzero, written, a.out_hist ? hist : nullptr,
+        ours_items<T, R, Wide>(a, &tmap, smem, &s_item, &s_abort, a.out_hist ? hist : nullptr,
                                hbase);
     if (a.out_hist) {
         __syncthreads();
         for (int i = threadIdx.x; i < bins; i += blockDim.x)
             if (hist[i])
                 atomicAdd(&a.out_hist[hbase + i], (u64)hist[i]);
-        // zero outputs = outputs written - nonzero outputs
-        u32 zeros = written - nonzero;
-        for (int o = 16; o > 0; o >>= 1)
-            zeros += __shfl_xor_sync(0xFFFFFFFFu, zeros, o);
-        if ((threadIdx.x & 31) == 0 && zeros)
-            atomicAdd(&a.out_hist[0], (u64)zeros);
+        if (threadIdx.x < 32) {   // the zero bins
+            u32 z = hist[bins + threadIdx.x];
+            for (int o = 16; o > 0; o >>= 1)
+                z += __shfl_xor_sync(0xFFFFFFFFu, z, o);
+            if (threadIdx.x == 0 && z)
+                atomicAdd(&a.out_hist[0], (u64)z);
+        }
     }
 }
 
