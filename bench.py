@@ -26,6 +26,7 @@ import os
 import subprocess
 import sys
 import threading
+import tempfile
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -101,14 +102,15 @@ class ClockSampler:
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, index):
+    def __init__(self, index, path=None):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+        # the samples go to `path` when given (kept as evidence), else to a temporary file
+        self.path = path or os.path.join(tempfile.gettempdir(), f"lnf_clocks_{os.getpid()}.csv")
 
     def start(self):
         try:
-            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            os.makedirs(os.path.dirname(os.path.abspath(self.path)), exist_ok=True)
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.QUERY}",
                                           "--format=csv,noheader,nounits", "-lms", "200"],
@@ -223,6 +225,7 @@ def main():
     ap.add_argument("--dims", type=int, nargs=3, default=None,
                     help="profiling: a smaller phantom of the same workload (nx ny nz); not a bench line")
     ap.add_argument("--no-e2e", action="store_true", help="profiling: skip the host-buffer leg")
+    ap.add_argument("--clocks-csv", default=None, help="keep the nvidia-smi clock samples in this file")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -276,7 +279,7 @@ def main():
         step()
     torch.cuda.synchronize()
 
-    sampler = ClockSampler(local)
+    sampler = ClockSampler(local, args.clocks_csv)
     sampler.start()
     ctx.profile(True)
     if world > 1:
@@ -471,30 +474,52 @@ def run_served(args):
         t = ctx.submit(ids[0], f, 1)
         ctx.wait(t)
         ctx.release(t)
-    tickets = []
+    def voxels(req):
+        vi, f, r, roi = req
+        return int(np.prod(roi[1])) if roi else sizes[vi] ** 3
+
+    def submit(k, arr):
+        vi, f, r, roi = reqs[k]
+        if roi:
+            return ctx.submit(ids[vi], f, r, roi_origin=roi[0], roi_dims=roi[1], arrival_time=arr)
+        return ctx.submit(ids[vi], f, r, arrival_time=arr)
+
+    def drain(pending, lat, block):
+        """Release finished requests (oldest first), as a client consuming its
+        results would; returns the latest finish time seen."""
+        t_last = 0.0
+        while pending:
+            tk, arr = pending[0]
+            res = ctx.wait(tk, 600.0) if block else ctx.poll(tk)
+            if res is None:
+                break
+            pending.pop(0)
+            lat.append(res.t_finish - arr)
+            t_last = max(t_last, res.t_finish)
+            ctx.release(tk)
+        return t_last
+
+    # (1) latency at the stated load: Poisson arrivals at args.rate per second
+    pending, lat = [], []
     t0 = now()
     t_next = t0
-    for k, (vi, f, r, roi) in enumerate(reqs):
+    t_last = 0.0
+    for k in range(n_req):
         t_next += gaps[k]
         while now() < t_next:
-            pass
+            t_last = max(t_last, drain(pending, lat, False))
         arr = now()
-        if roi:
-            tk = ctx.submit(ids[vi], f, r, roi_origin=roi[0], roi_dims=roi[1], arrival_time=arr)
-        else:
-            tk = ctx.submit(ids[vi], f, r, arrival_time=arr)
-        tickets.append((tk, arr))
-    lat = []
-    t_last = 0.0
-    vox = 0
-    for (tk, arr), (vi, f, r, roi) in zip(tickets, reqs):
-        res = ctx.wait(tk, 600.0)
-        lat.append(res.t_finish - arr)
-        t_last = max(t_last, res.t_finish)
-        vox += (np.prod(roi[1]) if roi else sizes[vi] ** 3)
-        ctx.release(tk)
-    served_s = t_last - t0
+        pending.append((submit(k, arr), arr))
+    t_last = max(t_last, drain(pending, lat, True))
+    vox = sum(voxels(q) for q in reqs)
     lat = np.array(lat) * 1e3
+    load_s = t_last - t0
+    # (2) capacity: every request queued at once, against serial plain calls
+    pending, lat_sat = [], []
+    t1 = now()
+    for k in range(n_req):
+        pending.append((submit(k, t1), t1))
+    served_s = drain(pending, lat_sat, True) - t1
     # serial plain calls on the same requests (device buffers, one sync per request)
     dvols = [torch.from_numpy(v).cuda() for v in vols]
     torch.cuda.synchronize()
@@ -514,8 +539,10 @@ def run_served(args):
                                    "half full-volume half ROI 32..256, random filter, r in {1,2,3}, 40 GiB budget",
                        "rate_per_s": args.rate, "duration_s": args.duration, "requests": n_req, "sizes": sizes},
             "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
-                           "max": float(lat.max())},
-            "served": {"seconds": served_s, "gvox_s": vox / served_s / 1e9},
+                           "max": float(lat.max()), "at_rate_per_s": args.rate,
+                           "seconds_to_last_result": load_s},
+            "served": {"seconds": served_s, "gvox_s": vox / served_s / 1e9,
+                       "note": "all requests queued at once (capacity)"},
             "serial_plain": {"seconds": serial_s, "gvox_s": vox / serial_s / 1e9},
             "offered_gvox_s": vox / args.duration / 1e9}
     print(json.dumps(line))

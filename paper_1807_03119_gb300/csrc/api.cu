@@ -369,7 +369,7 @@ lnf_status lnf_analyze(lnf_ctx *ctx, const void *in, const int64_t dims[3], int 
 // Fill job `idx` of the pack; encodes a TMA map when the volume allows it.
 lnf_status lnf_make_job(lnf_ctx *ctx, FilterPack &pk, int idx, int filter, int radius, const void *in, void *out,
                         const int64_t dims[3], int dtype, const int64_t *roi_o, const int64_t *roi_d,
-                        const VolScratch &vs, u64 *out_hist)
+                        const VolScratch &vs, u64 *out_hist, int64_t pitch)
 {
     FilterJob &j = pk.jobs[idx];
     std::memset(&j, 0, sizeof j);
@@ -378,6 +378,7 @@ lnf_status lnf_make_job(lnf_ctx *ctx, FilterPack &pk, int idx, int filter, int r
     j.nx = (int)dims[0];
     j.ny = (int)dims[1];
     j.nz = (int)dims[2];
+    j.pitch = pitch > 0 ? (int)pitch : j.nx;
     if (roi_d && roi_d[0] > 0) {
         j.ox = (int)roi_o[0];
         j.oy = (int)roi_o[1];
@@ -400,12 +401,12 @@ lnf_status lnf_make_job(lnf_ctx *ctx, FilterPack &pk, int idx, int filter, int r
     j.tmap_idx = -1;
     lnf_filter_decompose(j, ctx->zchunk);
     const size_t es = esize(dtype);
-    if (ctx->encode && !ctx->no_tma && (reinterpret_cast<uintptr_t>(in) & 15) == 0 && (dims[0] * es) % 16 == 0) {
+    if (ctx->encode && !ctx->no_tma && (reinterpret_cast<uintptr_t>(in) & 15) == 0 && ((size_t)j.pitch * es) % 16 == 0) {
         unsigned bw = 0, bh = 0;
         lnf_filter_box(filter, radius, ctx->cfg.cluster_offset, dtype, &bw, &bh);
         if (bw <= 256 && bh <= 256) {
             cuuint64_t gdim[3] = {(cuuint64_t)dims[0], (cuuint64_t)dims[1], (cuuint64_t)dims[2]};
-            cuuint64_t gstr[2] = {(cuuint64_t)(dims[0] * es), (cuuint64_t)(dims[0] * dims[1] * es)};
+            cuuint64_t gstr[2] = {(cuuint64_t)((size_t)j.pitch * es), (cuuint64_t)((size_t)j.pitch * dims[1] * es)};
             cuuint32_t box[3] = {bw, bh, 1};
             cuuint32_t estr[3] = {1, 1, 1};
             CUresult r = ctx->encode(&pk.tmaps[idx], dtype == LNF_U8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8
@@ -422,15 +423,15 @@ lnf_status lnf_make_job(lnf_ctx *ctx, FilterPack &pk, int idx, int filter, int r
 
 // Encode a 3D TMA map of the volume with box {box_w, box_h, 1}; false when the
 // volume does not meet TMA's alignment rules or encoding fails.
-bool lnf_encode_box(lnf_ctx *ctx, const void *in, int nx, int ny, int nz, int dtype, unsigned box_w,
+bool lnf_encode_box(lnf_ctx *ctx, const void *in, int nx, int ny, int nz, int pitch, int dtype, unsigned box_w,
                     unsigned box_h, CUtensorMap *map)
 {
     const size_t es = esize(dtype);
-    if (!ctx->encode || ctx->no_tma || (reinterpret_cast<uintptr_t>(in) & 15) != 0 || ((size_t)nx * es) % 16 != 0 ||
-        box_w > 256 || box_h > 256 || (box_w * es) % 16 != 0)
+    if (!ctx->encode || ctx->no_tma || (reinterpret_cast<uintptr_t>(in) & 15) != 0 ||
+        ((size_t)pitch * es) % 16 != 0 || pitch < nx || box_w > 256 || box_h > 256 || (box_w * es) % 16 != 0)
         return false;
     cuuint64_t gdim[3] = {(cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)nz};
-    cuuint64_t gstr[2] = {(cuuint64_t)((size_t)nx * es), (cuuint64_t)((size_t)nx * ny * es)};
+    cuuint64_t gstr[2] = {(cuuint64_t)((size_t)pitch * es), (cuuint64_t)((size_t)pitch * ny * es)};
     cuuint32_t box[3] = {box_w, box_h, 1};
     cuuint32_t estr[3] = {1, 1, 1};
     return ctx->encode(map, dtype == LNF_U8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_UINT16, 3,

@@ -226,6 +226,10 @@ struct FastArgs {
     const void *in;
     void *out;
     int nx, ny, nz;
+    // output region [o, o + b) (the whole volume unless a region of interest),
+    // tiled from column xs = ox rounded down to TMA's 16-byte rule
+    int ox, oy, oz, bx, by, bz, xs, xend, yend;
+    int roi;                              // 1: masked per-voxel stores (ROI-shaped output or odd width)
     int tiles_x, tiles_y, zchunks, zlen;
     int total_items;
     const DevParams *prm;
@@ -343,8 +347,8 @@ __device__ void ours_items(const FastArgs &a, const CUtensorMap *tmap, unsigned 
         const int rest = item / a.tiles_x;
         const int ty = rest % a.tiles_y;
         const int zc = rest / a.tiles_y;
-        const int x0 = tx * kTX, y0 = ty * kTY;
-        const int z0 = zc * a.zlen, z1 = min(a.nz, z0 + a.zlen);
+        const int x0 = a.xs + tx * kTX, y0 = a.oy + ty * kTY;
+        const int z0 = a.oz + zc * a.zlen, z1 = min(a.oz + a.bz, z0 + a.zlen);
         const int px0 = x0 - G::XH, py0 = y0 - G::H;
         const bool border = px0 < 0 || px0 + G::PW > a.nx || py0 < 0 || py0 + G::PH > a.ny;
         // plane p <-> z = z0 - 1 - R + p; G planes g = z0-1 .. z1 (steps s = 0 .. z1-z0+1)
@@ -574,7 +578,26 @@ __device__ void ours_items(const FastArgs &a, const CUtensorMap *tmap, unsigned 
                         const u32 U = accA[i][k] + c[k];
                         f[k] = (p0[k] >= T_ && U >= KT) ? Div::template div_add<HALF>(U) : 0u;
                     }
-                    if (y < a.ny && x < a.nx) {
+                    if (a.roi) {
+                        // a region of interest: masked stores, one voxel at a time
+                        // (the tile starts at xs <= ox, so some lanes lie left of it)
+                        const long long ob = ((long long)(zout - a.oz) * a.by + (y - a.oy)) * a.bx - a.ox;
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) {
+                            const int xk = x + k;
+                            if (y >= a.yend || xk < a.ox || xk >= a.xend)
+                                continue;
+                            static_cast<T *>(a.out)[ob + xk] = (T)f[k];
+                            if (hist) {
+                                if (f[k] >= hlim) {
+                                    if (f[k] < 65536u)   // always true for valid outputs
+                                        atomicAdd(&a.out_hist[f[k]], 1ull);
+                                } else {
+                                    atomicAdd(&hist[min(f[k] - hbase, hzero)], 1u);
+                                }
+                            }
+                        }
+                    } else if (y < a.ny && x < a.nx) {
                         const size_t o = ((size_t)zout * a.ny + y) * a.nx + x;
                         if (sizeof(T) == 2) {
                             *reinterpret_cast<uint2 *>(static_cast<uint16_t *>(a.out) + o) =
@@ -680,12 +703,12 @@ __global__ void __launch_bounds__(kThreads, 2) k_ours_fast(const __grid_constant
 }
 
 template <typename T, int R>
-lnf_status launch(lnf_ctx *ctx, const FilterJob &j, cudaStream_t st, u64 *out_hist, int *handled)
+lnf_status launch(lnf_ctx *ctx, const FilterJob &j, cudaStream_t st, u64 *out_hist, u32 *counter, int *handled)
 {
     typedef FGeo<T, R> G;
     // this kernel's own descriptor: box = its tile + halo
     CUtensorMap map;
-    if (!lnf_encode_box(ctx, j.in, j.nx, j.ny, j.nz, j.dtype, G::PW, G::PH, &map))
+    if (!lnf_encode_box(ctx, j.in, j.nx, j.ny, j.nz, j.pitch, j.dtype, G::PW, G::PH, &map))
         return LNF_OK;   // not handled: the generic kernel runs instead
     const CUtensorMap *tmap = &map;
     FastArgs a;
@@ -695,14 +718,29 @@ lnf_status launch(lnf_ctx *ctx, const FilterJob &j, cudaStream_t st, u64 *out_hi
     a.nx = j.nx;
     a.ny = j.ny;
     a.nz = j.nz;
-    a.tiles_x = (j.nx + kTX - 1) / kTX;
-    a.tiles_y = (j.ny + kTY - 1) / kTY;
+    a.ox = j.ox;
+    a.oy = j.oy;
+    a.oz = j.oz;
+    a.bx = j.bx;
+    a.by = j.by;
+    a.bz = j.bz;
+    a.xs = j.ox - j.ox % (16 / (int)sizeof(T));
+    a.xend = j.ox + j.bx;
+    a.yend = j.oy + j.by;
+    // dense 4-voxel vector stores need rows that start on 4-voxel boundaries of an
+    // aligned output; anything else (a region of interest, an odd width) takes the
+    // masked per-voxel stores
+    const bool whole = !(j.ox || j.oy || j.oz || j.bx != j.nx || j.by != j.ny || j.bz != j.nz);
+    const bool vec = j.nx % 4 == 0 && reinterpret_cast<uintptr_t>(j.out) % (4 * sizeof(T)) == 0;
+    a.roi = whole && vec ? 0 : 1;
+    a.tiles_x = (a.xend - a.xs + kTX - 1) / kTX;
+    a.tiles_y = (j.by + kTY - 1) / kTY;
     a.zlen = ctx->fast_zlen > 0 ? ctx->fast_zlen : 16;
-    a.zchunks = (j.nz + a.zlen - 1) / a.zlen;
+    a.zchunks = (j.bz + a.zlen - 1) / a.zlen;
     a.total_items = a.tiles_x * a.tiles_y * a.zchunks;
     a.prm = j.prm;
     a.out_hist = out_hist;
-    a.counter = ctx->d_counter + 8;
+    a.counter = counter ? counter : ctx->d_counter + 8;
     a.err = ctx->d_err;
     if (cudaFuncSetAttribute(k_ours_fast<T, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, G::SMEM) != cudaSuccess)
         return lnf_fail(ctx, LNF_ECUDA, "fast kernel: shared memory attribute");
@@ -723,30 +761,28 @@ lnf_status launch(lnf_ctx *ctx, const FilterJob &j, cudaStream_t st, u64 *out_hi
 }  // namespace
 
 lnf_status lnf_fast_dispatch(lnf_ctx *ctx, const FilterJob &job, const CUtensorMap *tmap, cudaStream_t stream,
-                             int *handled)
+                             int *handled, u32 *counter)
 {
     *handled = 0;
     if (job.filter != LNF_OURS)
-        return lnf_fast2_dispatch(ctx, job, tmap, stream, handled);
+        return lnf_fast2_dispatch(ctx, job, tmap, stream, handled, counter);
     if (!tmap || job.offset != 1 || job.radius < 1 || job.radius > 4)
-        return LNF_OK;
-    if (job.ox || job.oy || job.oz || job.bx != job.nx || job.by != job.ny || job.bz != job.nz)
         return LNF_OK;
     lnf_status s = LNF_OK;
     u64 *oh = job.out_hist;
     if (job.dtype == LNF_U8) {
         switch (job.radius) {
-        case 1: s = launch<uint8_t, 1>(ctx, job, stream, oh, handled); break;
-        case 2: s = launch<uint8_t, 2>(ctx, job, stream, oh, handled); break;
-        case 3: s = launch<uint8_t, 3>(ctx, job, stream, oh, handled); break;
-        default: s = launch<uint8_t, 4>(ctx, job, stream, oh, handled); break;
+        case 1: s = launch<uint8_t, 1>(ctx, job, stream, oh, counter, handled); break;
+        case 2: s = launch<uint8_t, 2>(ctx, job, stream, oh, counter, handled); break;
+        case 3: s = launch<uint8_t, 3>(ctx, job, stream, oh, counter, handled); break;
+        default: s = launch<uint8_t, 4>(ctx, job, stream, oh, counter, handled); break;
         }
     } else {
         switch (job.radius) {
-        case 1: s = launch<uint16_t, 1>(ctx, job, stream, oh, handled); break;
-        case 2: s = launch<uint16_t, 2>(ctx, job, stream, oh, handled); break;
-        case 3: s = launch<uint16_t, 3>(ctx, job, stream, oh, handled); break;
-        default: s = launch<uint16_t, 4>(ctx, job, stream, oh, handled); break;
+        case 1: s = launch<uint16_t, 1>(ctx, job, stream, oh, counter, handled); break;
+        case 2: s = launch<uint16_t, 2>(ctx, job, stream, oh, counter, handled); break;
+        case 3: s = launch<uint16_t, 3>(ctx, job, stream, oh, counter, handled); break;
+        default: s = launch<uint16_t, 4>(ctx, job, stream, oh, counter, handled); break;
         }
     }
     return s;

@@ -112,6 +112,10 @@ struct Args2 {
     const void *in;
     void *out;
     int nx, ny, nz;
+    // output region [o, o + b) (the whole volume unless a region of interest),
+    // tiled from column xs = ox rounded down to TMA's 16-byte rule
+    int ox, oy, oz, bx, by, bz, xs, xend, yend;
+    int roi;                              // 1: masked per-voxel stores (ROI-shaped output or odd width)
     int tiles_x, tiles_y, zlen;
     int total_items;
     int filter;
@@ -162,6 +166,32 @@ __device__ __forceinline__ void store4(const Args2 &a, int z, int y, int x, cons
             make_uint2(f[0] | (f[1] << 16), f[2] | (f[3] << 16));
     else
         *reinterpret_cast<u32 *>(static_cast<uint8_t *>(a.out) + o) = f[0] | (f[1] << 8) | (f[2] << 16) | (f[3] << 24);
+}
+
+// a region of interest: masked stores of the lane's four voxels, one at a time
+// (the tile starts at xs <= ox, so some lanes lie left of the region)
+template <typename T>
+__device__ __forceinline__ void store_roi(const Args2 &a, Hist2 &h, int z, int y, int x, const u32 f[4])
+{
+    if (y >= a.yend)
+        return;
+    const long long ob = ((long long)(z - a.oz) * a.by + (y - a.oy)) * a.bx - a.ox;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int xk = x + k;
+        if (xk < a.ox || xk >= a.xend)
+            continue;
+        static_cast<T *>(a.out)[ob + xk] = (T)f[k];
+        h.written += 1;
+        if (h.gh && f[k]) {
+            ++h.nonzero;
+            const u32 b = f[k] - h.base;
+            if (b < h.bins)
+                atomicAdd(&h.sh[b], 1u);
+            else if (f[k] < 65536u)   // always true for valid outputs
+                atomicAdd(&h.gh[f[k]], 1ull);
+        }
+    }
 }
 
 // ------------------------------------------------------------------ box kernel body
@@ -263,8 +293,8 @@ __device__ void box_items(const Args2 &a, const CUtensorMap *tmap, unsigned char
         const int rest = item / a.tiles_x;
         const int ty = rest % a.tiles_y;
         const int zc = rest / a.tiles_y;
-        const int x0 = tx * kTX, y0 = ty * kTY;
-        const int z0 = zc * a.zlen, z1 = min(a.nz, z0 + a.zlen);
+        const int x0 = a.xs + tx * kTX, y0 = a.oy + ty * kTY;
+        const int z0 = a.oz + zc * a.zlen, z1 = min(a.oz + a.bz, z0 + a.zlen);
         const int px0 = x0 - G::XH, py0 = y0 - G::H;
         const bool border = px0 < 0 || px0 + G::PW > a.nx || py0 < 0 || py0 + G::PH > a.ny;
         const int nplanes = (z1 - z0) + 2 * R;   // plane p <-> z = z0 - R + p
@@ -287,11 +317,13 @@ __device__ void box_items(const Args2 &a, const CUtensorMap *tmap, unsigned char
         }
         bool ok = true;
         for (int s = 0; s < z1 - z0; ++s) {
+            // one thread waits for the TMA completions; the barrier orders the
+            // data before every thread's reads
             const int pfirst = s == 0 ? 0 : s + 2 * R;
-            for (int p = pfirst; p <= s + 2 * R; ++p) {
-                if (!mbar_wait_bounded(&bars[p % G::NP], (u32)((p / G::NP) & 1), a.err))
-                    *s_abort = 1;
-            }
+            if (threadIdx.x == 0)
+                for (int p = pfirst; p <= s + 2 * R; ++p)
+                    if (!mbar_wait_bounded(&bars[p % G::NP], (u32)((p / G::NP) & 1), a.err))
+                        *s_abort = 1;
             __syncthreads();
             if (*s_abort) {
                 ok = false;
@@ -403,7 +435,9 @@ __device__ void box_items(const Args2 &a, const CUtensorMap *tmap, unsigned char
                                                                      : 0u;
                 }
                 const int y = y0 + kRows * warp + i, x = x0 + 4 * lane;
-                if (y < a.ny && x < a.nx) {
+                if (a.roi) {
+                    store_roi<T>(a, hist, z, y, x, f);
+                } else if (y < a.ny && x < a.nx) {
                     store4<T>(a, z, y, x, f);
                     hist4(hist, f);
                 }
@@ -480,8 +514,8 @@ __device__ void tap_items(const Args2 &a, const CUtensorMap *tmap, unsigned char
         const int rest = item / a.tiles_x;
         const int ty = rest % a.tiles_y;
         const int zc = rest / a.tiles_y;
-        const int x0 = tx * kTX, y0 = ty * kTY;
-        const int z0 = zc * a.zlen, z1 = min(a.nz, z0 + a.zlen);
+        const int x0 = a.xs + tx * kTX, y0 = a.oy + ty * kTY;
+        const int z0 = a.oz + zc * a.zlen, z1 = min(a.oz + a.bz, z0 + a.zlen);
         const int px0 = x0 - G::XH, py0 = y0 - G::H;
         const bool border = px0 < 0 || px0 + G::PW > a.nx || py0 < 0 || py0 + G::PH > a.ny;
         const int nplanes = (z1 - z0) + 2 * R;
@@ -504,11 +538,13 @@ __device__ void tap_items(const Args2 &a, const CUtensorMap *tmap, unsigned char
         }
         bool ok = true;
         for (int s = 0; s < z1 - z0; ++s) {
+            // one thread waits for the TMA completions; the barrier orders the
+            // data before every thread's reads
             const int pfirst = s == 0 ? 0 : s + 2 * R;
-            for (int p = pfirst; p <= s + 2 * R; ++p) {
-                if (!mbar_wait_bounded(&bars[p % G::NP], (u32)((p / G::NP) & 1), a.err))
-                    *s_abort = 1;
-            }
+            if (threadIdx.x == 0)
+                for (int p = pfirst; p <= s + 2 * R; ++p)
+                    if (!mbar_wait_bounded(&bars[p % G::NP], (u32)((p / G::NP) & 1), a.err))
+                        *s_abort = 1;
             __syncthreads();
             if (*s_abort) {
                 ok = false;
@@ -661,7 +697,9 @@ __device__ void tap_items(const Args2 &a, const CUtensorMap *tmap, unsigned char
                     f[k] = (n && p0[i][k] >= T_ && (u64)sm >= (u64)n * T_) ? q : 0u;
                 }
                 const int y = y0 + kRows * warp + i, x = x0 + 4 * lane;
-                if (y < a.ny && x < a.nx) {
+                if (a.roi) {
+                    store_roi<T>(a, hist, z, y, x, f);
+                } else if (y < a.ny && x < a.nx) {
                     store4<T>(a, z, y, x, f);
                     hist4(hist, f);
                 }
@@ -704,7 +742,7 @@ struct K2Smem {
 };
 
 template <typename T, int R, int FILTER>
-__global__ void __launch_bounds__(kThreads, K2Smem<T, R, FILTER>::BOX ? 1 : 2)
+__global__ void __launch_bounds__(kThreads, (K2Smem<T, R, FILTER>::BOX && R > 2) ? 1 : 2)
     k_fast2(const __grid_constant__ CUtensorMap tmap, const Args2 a)
 {
     typedef K2Smem<T, R, FILTER> S;
@@ -757,12 +795,12 @@ __global__ void __launch_bounds__(kThreads, K2Smem<T, R, FILTER>::BOX ? 1 : 2)
 }
 
 template <typename T, int R, int FILTER>
-lnf_status launch2(lnf_ctx *ctx, const FilterJob &j, cudaStream_t st, int *handled)
+lnf_status launch2(lnf_ctx *ctx, const FilterJob &j, cudaStream_t st, u32 *counter, int *handled)
 {
     typedef K2Smem<T, R, FILTER> S;
     typedef typename S::G G;
     CUtensorMap map;   // this kernel's own descriptor: box = its tile + halo
-    if (!lnf_encode_box(ctx, j.in, j.nx, j.ny, j.nz, j.dtype, G::PW, G::PH, &map))
+    if (!lnf_encode_box(ctx, j.in, j.nx, j.ny, j.nz, j.pitch, j.dtype, G::PW, G::PH, &map))
         return LNF_OK;
     const CUtensorMap *tmap = &map;
     Args2 a;
@@ -772,15 +810,30 @@ lnf_status launch2(lnf_ctx *ctx, const FilterJob &j, cudaStream_t st, int *handl
     a.nx = j.nx;
     a.ny = j.ny;
     a.nz = j.nz;
-    a.tiles_x = (j.nx + kTX - 1) / kTX;
-    a.tiles_y = (j.ny + kTY - 1) / kTY;
+    a.ox = j.ox;
+    a.oy = j.oy;
+    a.oz = j.oz;
+    a.bx = j.bx;
+    a.by = j.by;
+    a.bz = j.bz;
+    a.xs = j.ox - j.ox % (16 / (int)sizeof(T));
+    a.xend = j.ox + j.bx;
+    a.yend = j.oy + j.by;
+    // dense 4-voxel vector stores need rows that start on 4-voxel boundaries of an
+    // aligned output; anything else (a region of interest, an odd width) takes the
+    // masked per-voxel stores
+    const bool whole = !(j.ox || j.oy || j.oz || j.bx != j.nx || j.by != j.ny || j.bz != j.nz);
+    const bool vec = j.nx % 4 == 0 && reinterpret_cast<uintptr_t>(j.out) % (4 * sizeof(T)) == 0;
+    a.roi = whole && vec ? 0 : 1;
+    a.tiles_x = (a.xend - a.xs + kTX - 1) / kTX;
+    a.tiles_y = (j.by + kTY - 1) / kTY;
     a.zlen = ctx->fast_zlen > 0 ? ctx->fast_zlen : 16;
-    a.total_items = a.tiles_x * a.tiles_y * ((j.nz + a.zlen - 1) / a.zlen);
+    a.total_items = a.tiles_x * a.tiles_y * ((j.bz + a.zlen - 1) / a.zlen);
     a.filter = FILTER;
     a.prm = j.prm;
     a.lut = j.lut;
     a.out_hist = j.out_hist;
-    a.counter = ctx->d_counter + 9;
+    a.counter = counter ? counter : ctx->d_counter + 9;
     a.err = ctx->d_err;
     a.one = 1u;
     if (cudaFuncSetAttribute(k_fast2<T, R, FILTER>, cudaFuncAttributeMaxDynamicSharedMemorySize, S::TOTAL) !=
@@ -801,40 +854,39 @@ lnf_status launch2(lnf_ctx *ctx, const FilterJob &j, cudaStream_t st, int *handl
 }
 
 template <typename T, int FILTER>
-lnf_status by_radius(lnf_ctx *ctx, const FilterJob &j, cudaStream_t st, int *handled)
+lnf_status by_radius(lnf_ctx *ctx, const FilterJob &j, cudaStream_t st, u32 *counter, int *handled)
 {
     switch (j.radius) {
-    case 1: return launch2<T, 1, FILTER>(ctx, j, st, handled);
-    case 2: return launch2<T, 2, FILTER>(ctx, j, st, handled);
-    case 3: return launch2<T, 3, FILTER>(ctx, j, st, handled);
-    default: return launch2<T, 4, FILTER>(ctx, j, st, handled);
+    case 1: return launch2<T, 1, FILTER>(ctx, j, st, counter, handled);
+    case 2: return launch2<T, 2, FILTER>(ctx, j, st, counter, handled);
+    case 3: return launch2<T, 3, FILTER>(ctx, j, st, counter, handled);
+    default: return launch2<T, 4, FILTER>(ctx, j, st, counter, handled);
     }
 }
 
 }  // namespace
 
-// Route mean / sigma / entropy / Okada jobs on whole TMA-able volumes at
-// radius 1..4 (sigma 1..3) to the specialised kernels.
+// Route mean / sigma / entropy / Okada jobs on TMA-able volumes (whole or a
+// region of interest) at radius 1..4 (sigma 1..2) to the specialised kernels.
 lnf_status lnf_fast2_dispatch(lnf_ctx *ctx, const FilterJob &job, const CUtensorMap *tmap, cudaStream_t stream,
-                              int *handled)
+                              int *handled, u32 *counter)
 {
     *handled = 0;
     if (!tmap || job.radius < 1 || job.radius > 4 || job.filter == LNF_OURS)
         return LNF_OK;
-    if (job.filter == LNF_SIGMA && job.radius > 3)
-        return LNF_OK;
-    if (job.ox || job.oy || job.oz || job.bx != job.nx || job.by != job.ny || job.bz != job.nz)
+    // sigma at r = 3 (343 taps per voxel) runs faster on the generic kernel
+    if (job.filter == LNF_SIGMA && job.radius > 2)
         return LNF_OK;
     const bool u8 = job.dtype == LNF_U8;
     switch (job.filter) {
-    case LNF_MEAN: return u8 ? by_radius<uint8_t, LNF_MEAN>(ctx, job, stream, handled)
-                             : by_radius<uint16_t, LNF_MEAN>(ctx, job, stream, handled);
-    case LNF_ENTROPY: return u8 ? by_radius<uint8_t, LNF_ENTROPY>(ctx, job, stream, handled)
-                                : by_radius<uint16_t, LNF_ENTROPY>(ctx, job, stream, handled);
-    case LNF_SIGMA: return u8 ? by_radius<uint8_t, LNF_SIGMA>(ctx, job, stream, handled)
-                              : by_radius<uint16_t, LNF_SIGMA>(ctx, job, stream, handled);
-    case LNF_OKADA: return u8 ? by_radius<uint8_t, LNF_OKADA>(ctx, job, stream, handled)
-                              : by_radius<uint16_t, LNF_OKADA>(ctx, job, stream, handled);
+    case LNF_MEAN: return u8 ? by_radius<uint8_t, LNF_MEAN>(ctx, job, stream, counter, handled)
+                             : by_radius<uint16_t, LNF_MEAN>(ctx, job, stream, counter, handled);
+    case LNF_ENTROPY: return u8 ? by_radius<uint8_t, LNF_ENTROPY>(ctx, job, stream, counter, handled)
+                                : by_radius<uint16_t, LNF_ENTROPY>(ctx, job, stream, counter, handled);
+    case LNF_SIGMA: return u8 ? by_radius<uint8_t, LNF_SIGMA>(ctx, job, stream, counter, handled)
+                              : by_radius<uint16_t, LNF_SIGMA>(ctx, job, stream, counter, handled);
+    case LNF_OKADA: return u8 ? by_radius<uint8_t, LNF_OKADA>(ctx, job, stream, counter, handled)
+                              : by_radius<uint16_t, LNF_OKADA>(ctx, job, stream, counter, handled);
     default: return LNF_OK;
     }
 }

@@ -310,13 +310,13 @@ __device__ void process_item(const FilterJob &J, const CUtensorMap *tmap, int it
     // stage loader for plain loads
     auto load_plane_plain = [&](int p, T *dst) {
         const int z = clampi(z0 - h + p, 0, J.nz - 1);
-        const size_t zoff = (size_t)z * J.ny * J.nx;
+        const size_t zoff = (size_t)z * J.ny * J.pitch;
         for (int e = threadIdx.x; e < g.PW * g.PH; e += blockDim.x) {
             const int row = e / g.PW;
             const int col = e - row * g.PW;
             const int yy = clampi(py0 + row, 0, J.ny - 1);
             const int xx = clampi(px0 + col, 0, J.nx - 1);
-            dst[row * g.PW + col] = vin[zoff + (size_t)yy * J.nx + xx];
+            dst[row * g.PW + col] = vin[zoff + (size_t)yy * J.pitch + xx];
         }
     };
 
@@ -358,12 +358,13 @@ __device__ void process_item(const FilterJob &J, const CUtensorMap *tmap, int it
     for (int s = 0; s < lz1 - lz0; ++s) {
         // make planes up to s + 2h resident
         if (use_tma) {
+            // one thread waits for the TMA completions; the barrier orders the
+            // data before every thread's reads
             const int pfirst = s == 0 ? 0 : s + 2 * h;
-            for (int p = pfirst; p <= s + 2 * h; ++p) {
-                const int slot = p % g.NP;
-                if (!mbar_wait_bounded(&bars[slot], (u32)((p / g.NP) & 1), err))
-                    *s_abort = 1;
-            }
+            if (threadIdx.x == 0)
+                for (int p = pfirst; p <= s + 2 * h; ++p)
+                    if (!mbar_wait_bounded(&bars[p % g.NP], (u32)((p / g.NP) & 1), err))
+                        *s_abort = 1;
             __syncthreads();
             if (*s_abort) {
                 ok = false;

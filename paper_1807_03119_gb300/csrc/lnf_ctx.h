@@ -27,8 +27,7 @@ struct VolScratch {
     void *pscr = nullptr;       // parameter-derivation scratch (zeroed once)
 };
 
-struct BatchEntry;      lnf_status lnf_fast2_dispatch(lnf_ctx *ctx, const FilterJob &job, const CUtensorMap *tmap, cudaStream_t stream,
-                              int *handled);
+struct BatchEntry;
 // batch.cu
 struct Server;          // serve.cu
 
@@ -81,10 +80,13 @@ ParamCfg lnf_param_cfg(const lnf_config &c);
 lnf_status lnf_scratch_pool(lnf_ctx *ctx, size_t n);
 lnf_status lnf_analyze(lnf_ctx *ctx, const void *in, const int64_t dims[3], int dtype, VolScratch &vs,
                        cudaStream_t stream);
+// `pitch`: the input's row stride in elements (0: dense rows, = dims[0])
 lnf_status lnf_make_job(lnf_ctx *ctx, FilterPack &pk, int idx, int filter, int radius, const void *in, void *out,
                         const int64_t dims[3], int dtype, const int64_t *roi_o, const int64_t *roi_d,
-                        const VolScratch &vs, u64 *out_hist);
-bool lnf_encode_box(lnf_ctx *ctx, const void *in, int nx, int ny, int nz, int dtype, unsigned box_w,
+                        const VolScratch &vs, u64 *out_hist, int64_t pitch = 0);
+// 3D TMA map of a volume with row stride `pitch` elements, box {box_w, box_h, 1};
+// false when the volume does not meet TMA's alignment rules or encoding fails
+bool lnf_encode_box(lnf_ctx *ctx, const void *in, int nx, int ny, int nz, int pitch, int dtype, unsigned box_w,
                     unsigned box_h, CUtensorMap *map);
 lnf_status lnf_run_pack(lnf_ctx *ctx, FilterPack &pk, int persistent, cudaStream_t stream);
 lnf_status lnf_run_pack_counter(lnf_ctx *ctx, FilterPack &pk, int persistent, cudaStream_t stream, u32 *counter);
@@ -94,11 +96,12 @@ lnf_status lnf_run_one(lnf_ctx *ctx, int filter, int radius, const void *in, voi
 // profiling helpers (api.cu): bracket one launch (or a group of `count` launches)
 int lnf_prof_begin(lnf_ctx *ctx, cudaStream_t st);
 void lnf_prof_end(lnf_ctx *ctx, int rec, const char *name, cudaStream_t st, int count);
-// fast.cu: run the job through a specialised kernel if one covers it (*handled = 1)
+// fast.cu: run the job through a specialised kernel if one covers it (*handled = 1);
+// `counter` is the launch's work counter (null: the context's own, for its stream)
 lnf_status lnf_fast_dispatch(lnf_ctx *ctx, const FilterJob &job, const CUtensorMap *tmap, cudaStream_t stream,
-                             int *handled);
+                             int *handled, u32 *counter = nullptr);
 lnf_status lnf_fast2_dispatch(lnf_ctx *ctx, const FilterJob &job, const CUtensorMap *tmap, cudaStream_t stream,
-                              int *handled);
+                              int *handled, u32 *counter = nullptr);
 // batch.cu
 void lnf_batch_cache_clear(lnf_ctx *ctx);
 // serve.cu

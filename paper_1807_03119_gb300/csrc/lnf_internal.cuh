@@ -52,6 +52,7 @@ struct FilterJob {
     const void *in;
     void *out;
     int nx, ny, nz;             // whole volume
+    int pitch;                  // input row stride in elements (>= nx)
     int ox, oy, oz;             // ROI origin
     int bx, by, bz;             // ROI dims (= output dims)
     int dtype;                  // 0 u8, 1 u16

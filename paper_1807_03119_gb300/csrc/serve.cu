@@ -29,6 +29,7 @@ double now_s()
 struct Resident {
     void *d_vol = nullptr;
     int64_t dims[3] = {0, 0, 0};
+    int64_t pitch = 0;              // row stride in elements: rows padded to 16 bytes (TMA's rule)
     int dtype = 0;
     size_t bytes = 0;
     VolScratch vs;
@@ -181,13 +182,18 @@ lnf_status launch_wave(Server *s, Wave *w)
     cudaStream_t st = s->streams[w->stream_idx];
     FilterPack &pk = s->pack;
     std::memset(&pk, 0, sizeof(int) * 16);
-    pk.n_jobs = (int)w->reqs.size();
+    // every request is its own launch on the wave's stream, sized for its own
+    // filter and radius (a shared launch would run every job at the largest
+    // job's shared memory and occupancy); a specialised kernel takes the
+    // request when it covers it (with this stream's own work counter), else
+    // the generic kernel
+    u32 *fast_counter = ctx->d_counter + 10 + w->stream_idx;
     EntropyPack ep;
     std::memset(&ep, 0, sizeof ep);
     cudaEventCreateWithFlags(&w->ev_start, cudaEventDefault);
     cudaEventCreateWithFlags(&w->ev_done, cudaEventDefault);
     cudaEventRecord(w->ev_start, st);
-    for (int i = 0; i < pk.n_jobs; ++i) {
+    for (int i = 0; i < (int)w->reqs.size(); ++i) {
         Req *q = w->reqs[i];
         Resident *v;
         {
@@ -209,14 +215,23 @@ lnf_status launch_wave(Server *s, Wave *w)
             ep.H[k] = s->d_H + q->slot;
         }
         const bool roi = q->r.roi_dims[0] > 0;
-        lnf_status r = lnf_make_job(ctx, pk, i, q->r.filter_id, q->r.radius, v->d_vol, q->d_out, v->dims, v->dtype,
-                                    roi ? q->r.roi_origin : nullptr, roi ? q->r.roi_dims : nullptr, v->vs, oh);
+        pk.n_jobs = 1;
+        lnf_status r = lnf_make_job(ctx, pk, 0, q->r.filter_id, q->r.radius, v->d_vol, q->d_out, v->dims,
+                                    v->dtype, roi ? q->r.roi_origin : nullptr, roi ? q->r.roi_dims : nullptr, v->vs,
+                                    oh, v->pitch);
         if (r != LNF_OK)
             return r;
+        int handled = 0;
+        if (!ctx->no_fast) {
+            const FilterJob &j = pk.jobs[0];
+            r = lnf_fast_dispatch(ctx, j, j.tmap_idx >= 0 ? &pk.tmaps[j.tmap_idx] : nullptr, st, &handled,
+                                  fast_counter);
+            if (r != LNF_OK)
+                return r;
+        }
+        if (!handled && (r = lnf_run_pack_counter(ctx, pk, 0, st, nullptr)) != LNF_OK)
+            return r;
     }
-    lnf_status r = lnf_run_pack_counter(ctx, pk, 1, st, ctx->d_counter + 1 + w->stream_idx);
-    if (r != LNF_OK)
-        return r;
     if (lnf_launch_entropy_pack(ep, s->ent_part + (size_t)w->stream_idx * LNF_ENT_SPLIT * LNF_MAX_ENT,
                                 s->ent_done + (size_t)w->stream_idx * LNF_MAX_ENT, st) != cudaSuccess)
         return lnf_fail(ctx, LNF_ECUDA, "serving: entropy launch failed");
@@ -403,7 +418,11 @@ extern "C" lnf_status lnf_volume_register(lnf_ctx *ctx, const void *src, int src
     v.dims[1] = dims[1];
     v.dims[2] = dims[2];
     v.dtype = dtype;
-    v.bytes = (size_t)dims[0] * dims[1] * dims[2] * (dtype == LNF_U8 ? 1 : 2);
+    const size_t es = dtype == LNF_U8 ? 1 : 2;
+    // rows padded to a multiple of 16 bytes, so that every resident volume can be
+    // read by TMA (the specialised kernels) whatever its width
+    v.pitch = (int64_t)(((size_t)dims[0] * es + 15) / 16 * 16 / es);
+    v.bytes = (size_t)v.pitch * dims[1] * dims[2] * es;
     {
         std::lock_guard<std::mutex> g(s->mu);
         if (s->used + v.bytes > ctx->cfg.hbm_budget_bytes)
@@ -416,13 +435,10 @@ extern "C" lnf_status lnf_volume_register(lnf_ctx *ctx, const void *src, int src
         s->used -= v.bytes;
         return e;
     };
-    // round the allocation up so that a 16-byte row pitch stays TMA-aligned
-    if (cudaMalloc(&v.d_vol, v.bytes + 16) != cudaSuccess)
-        return undo(lnf_fail(ctx, LNF_ENOMEM, "resident volume allocation failed"));
     cudaStream_t st0 = s->streams[0];
-    if (cudaMemcpyAsync(v.d_vol, src, v.bytes, src_is_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice,
-                        st0) != cudaSuccess ||
-        cudaMalloc(&v.vs.hist, sizeof(u64) * LNF_LEVELS_U16) != cudaSuccess ||
+    if (cudaMalloc(&v.d_vol, v.bytes) != cudaSuccess)
+        return undo(lnf_fail(ctx, LNF_ENOMEM, "resident volume allocation failed"));
+    if (cudaMalloc(&v.vs.hist, sizeof(u64) * LNF_LEVELS_U16) != cudaSuccess ||
         cudaMalloc(&v.vs.st, sizeof(DevStats)) != cudaSuccess ||
         cudaMalloc(&v.vs.prm, sizeof(DevParams)) != cudaSuccess ||
         cudaMalloc(&v.vs.lut, sizeof(u32) * LNF_LEVELS_U16) != cudaSuccess ||
@@ -431,10 +447,46 @@ extern "C" lnf_status lnf_volume_register(lnf_ctx *ctx, const void *src, int src
         cudaFree(v.d_vol);
         return undo(lnf_fail(ctx, LNF_ENOMEM, "resident volume scratch allocation failed"));
     }
-    if ((st = lnf_analyze(ctx, v.d_vol, v.dims, dtype, v.vs, st0)) != LNF_OK)
+    // the statistics read dense rows: the caller's device buffer itself, or a
+    // dense staging copy of a host buffer; then the rows go to their padded places
+    const size_t row = (size_t)dims[0] * es;
+    const void *dense = src;
+    void *tmp = nullptr;
+    if (src_is_host) {
+        if (v.pitch == dims[0]) {
+            dense = v.d_vol;   // already dense: stage in place
+        } else if (cudaMalloc(&tmp, row * dims[1] * dims[2]) != cudaSuccess) {
+            cudaFree(v.d_vol);
+            return undo(lnf_fail(ctx, LNF_ENOMEM, "resident volume staging allocation failed"));
+        } else {
+            dense = tmp;
+        }
+        if (cudaMemcpyAsync(const_cast<void *>(dense), src, row * dims[1] * dims[2], cudaMemcpyHostToDevice, st0) !=
+            cudaSuccess) {
+            cudaFree(tmp);
+            cudaFree(v.d_vol);
+            return undo(lnf_fail(ctx, LNF_ECUDA, "resident volume upload failed"));
+        }
+    }
+    if ((st = lnf_analyze(ctx, dense, v.dims, dtype, v.vs, st0)) != LNF_OK) {
+        cudaStreamSynchronize(st0);
+        cudaFree(tmp);
+        cudaFree(v.d_vol);
         return undo(st);
-    if (cudaStreamSynchronize(st0) != cudaSuccess)
+    }
+    if (dense != v.d_vol &&
+        cudaMemcpy2DAsync(v.d_vol, (size_t)v.pitch * es, dense, row, row, (size_t)dims[1] * dims[2],
+                          cudaMemcpyDeviceToDevice, st0) != cudaSuccess) {
+        cudaStreamSynchronize(st0);
+        cudaFree(tmp);
+        cudaFree(v.d_vol);
+        return undo(lnf_fail(ctx, LNF_ECUDA, "resident volume copy failed"));
+    }
+    const cudaError_t done = cudaStreamSynchronize(st0);
+    cudaFree(tmp);
+    if (done != cudaSuccess)
         return undo(lnf_fail(ctx, LNF_ECUDA, "statistics of the resident volume failed"));
+
     std::lock_guard<std::mutex> g(s->mu);
     *vol_id = s->next_vol++;
     s->vols[*vol_id] = v;
