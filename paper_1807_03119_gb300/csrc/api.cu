@@ -227,6 +227,7 @@ extern "C" void lnf_destroy(lnf_ctx *ctx)
     cudaFree(ctx->d_H);
     cudaFree(ctx->d_err);
     cudaFree(ctx->d_counter);
+    cudaFree(ctx->pitched);
     cudaFree(ctx->d_ent_part);
     cudaFree(ctx->d_ent_done);
     cudaFree(ctx->st_in);
@@ -467,14 +468,60 @@ lnf_status lnf_run_pack_counter(lnf_ctx *ctx, FilterPack &pk, int persistent, cu
     return LNF_OK;
 }
 
+size_t lnf_pitched_row(const void *in, const int64_t dims[3], int dtype)
+{
+    const size_t row = (size_t)dims[0] * esize(dtype);
+    if ((reinterpret_cast<uintptr_t>(in) & 15) == 0 && row % 16 == 0)
+        return 0;
+    return (row + 15) / 16 * 16;
+}
+
+lnf_status lnf_copy_pitched(lnf_ctx *ctx, void *dst, size_t prow, const void *in, const int64_t dims[3], int dtype,
+                            cudaStream_t st)
+{
+    const size_t row = (size_t)dims[0] * esize(dtype);
+    CK(cudaMemcpy2DAsync(dst, prow, in, row, row, (size_t)dims[1] * dims[2], cudaMemcpyDeviceToDevice, st));
+    return LNF_OK;
+}
+
+// A whole-volume input that TMA cannot address (an unaligned base or a row
+// length that is not a multiple of 16 bytes) is copied once into the
+// context's staging buffer with padded rows, so that the specialised kernels
+// can read it; *src / *pitch name what the filter launches read.
+static lnf_status stage_input(lnf_ctx *ctx, const void *in, const int64_t dims[3], int dtype, cudaStream_t st,
+                              const void **src, int64_t *pitch)
+{
+    *src = in;
+    *pitch = 0;
+    const size_t prow = lnf_pitched_row(in, dims, dtype);
+    if (prow == 0 || !ctx->encode || ctx->no_tma || ctx->no_fast)
+        return LNF_OK;
+    const size_t need = prow * dims[1] * dims[2];
+    if (ctx->pitched_cap < need) {
+        cudaFree(ctx->pitched);   // waits for the work that still reads it
+        ctx->pitched = nullptr;
+        ctx->pitched_cap = 0;
+        if (cudaMalloc(&ctx->pitched, need) != cudaSuccess)
+            return LNF_OK;   // no room for the copy: the generic kernel reads the input itself
+        ctx->pitched_cap = need;
+    }
+    lnf_status s = lnf_copy_pitched(ctx, ctx->pitched, prow, in, dims, dtype, st);
+    if (s != LNF_OK)
+        return s;
+    *src = ctx->pitched;
+    *pitch = (int64_t)(prow / esize(dtype));
+    return LNF_OK;
+}
+
 // Run one filter job on an analysed volume, through the fastest kernel that covers it.
 lnf_status lnf_run_one(lnf_ctx *ctx, int filter, int radius, const void *in, void *out, const int64_t dims[3],
                        int dtype, const int64_t *roi_o, const int64_t *roi_d, const VolScratch &vs,
-                       u64 *out_hist, cudaStream_t stream)
+                       u64 *out_hist, cudaStream_t stream, int64_t pitch)
 {
     FilterPack &pk = ctx->pack;
     pk.n_jobs = 1;
-    lnf_status s = lnf_make_job(ctx, pk, 0, filter, radius, in, out, dims, dtype, roi_o, roi_d, vs, out_hist);
+    lnf_status s =
+        lnf_make_job(ctx, pk, 0, filter, radius, in, out, dims, dtype, roi_o, roi_d, vs, out_hist, pitch);
     if (s != LNF_OK)
         return s;
     const int rec = lnf_prof_begin(ctx, stream);
@@ -510,8 +557,13 @@ extern "C" lnf_status lnf_filter_volume(lnf_ctx *ctx, int filter_id, int radius,
         return lnf_fail(ctx, LNF_EINVAL, "input and output overlap");
     if ((s = lnf_analyze(ctx, in, dims, dtype, ctx->vs, ctx->stream)) != LNF_OK)
         return s;
-    return lnf_run_one(ctx, filter_id, radius, in, out, dims, dtype, nullptr, nullptr, ctx->vs, nullptr,
-                       ctx->stream);
+    const void *src = in;
+    int64_t pitch = 0;
+    if (lnf_fast_covers(filter_id, radius, ctx->cfg.cluster_offset) &&
+        (s = stage_input(ctx, in, dims, dtype, ctx->stream, &src, &pitch)) != LNF_OK)
+        return s;
+    return lnf_run_one(ctx, filter_id, radius, src, out, dims, dtype, nullptr, nullptr, ctx->vs, nullptr,
+                       ctx->stream, pitch);
 }
 
 extern "C" lnf_status lnf_filter_roi(lnf_ctx *ctx, int filter_id, int radius, const void *in,
@@ -566,10 +618,19 @@ extern "C" lnf_status lnf_filter_multi(lnf_ctx *ctx, int radius, const void *in,
         CK(lnf_launch_zero(ctx->out_hist, (u64)LNF_LEVELS_U16 * n, st));
         lnf_prof_end(ctx, rec, "zero_hist", st, 1);
     }
+    // one padded copy serves every filter a specialised kernel covers
+    bool any_fast = false;
+    for (int i = 0; i < n; ++i)
+        any_fast = any_fast || lnf_fast_covers(filter_ids[i], radius, ctx->cfg.cluster_offset);
+    const void *src = in;
+    int64_t pitch = 0;
+    if (any_fast && (s = stage_input(ctx, in, dims, dtype, st, &src, &pitch)) != LNF_OK)
+        return s;
     for (int i = 0; i < n; ++i) {
         u64 *oh = d_entropy ? ctx->out_hist + (size_t)i * LNF_LEVELS_U16 : nullptr;
-        if ((s = lnf_run_one(ctx, filter_ids[i], radius, in, outs[i], dims, dtype, nullptr, nullptr, ctx->vs, oh,
-                             st)) != LNF_OK)
+        const bool f = lnf_fast_covers(filter_ids[i], radius, ctx->cfg.cluster_offset);
+        if ((s = lnf_run_one(ctx, filter_ids[i], radius, f ? src : in, outs[i], dims, dtype, nullptr, nullptr,
+                             ctx->vs, oh, st, f ? pitch : 0)) != LNF_OK)
             return s;
     }
     if (d_entropy) {

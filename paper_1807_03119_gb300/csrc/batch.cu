@@ -1,9 +1,11 @@
-// Batched delivery: many volumes / ROIs / filters / radii in ONE persistent
-// launch over the flattened tile list of all jobs, preceded by one batched
-// statistics launch and one batched parameter launch, captured once into a
-// CUDA graph and replayed for the same batch.  An autotuner picks the z chunk
-// of a work item (the tile's depth, which sets the halo re-read share and the
-// load balance) by timing the candidates on the first batch it sees.
+// Batched delivery: many volumes / ROIs / filters / radii behind one batched
+// statistics launch and one batched parameter launch; jobs a specialised kernel
+// covers run as its launches (inputs TMA cannot address first get one padded
+// copy per volume), all other jobs share ONE persistent launch of the generic
+// kernel over their flattened tile list.  The whole sequence is captured once
+// into a CUDA graph and replayed for the same batch.  An autotuner picks the z
+// chunk of a generic work item (the tile's depth, which sets the halo re-read
+// share and the load balance) by timing the candidates on the first batch it sees.
 #include "lnf_ctx.h"
 
 #include <algorithm>
@@ -18,23 +20,84 @@
             return lnf_fail(ctx, LNF_ECUDA, "%s: %s", #call, cudaGetErrorString(e_));             \
     } while (0)
 
+static void free_stage(std::vector<void *> &stage)
+{
+    for (void *p : stage)
+        if (p)
+            cudaFree(p);   // waits for the work that still reads it
+    stage.clear();
+}
+
 struct BatchEntry {
     std::vector<lnf_job> key;
     cudaStream_t stream = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
+    std::vector<void *> stage;   // padded copies of the distinct inputs (owned; null: none needed)
+    ~BatchEntry()
+    {
+        if (exec)
+            cudaGraphExecDestroy(exec);
+        if (graph)
+            cudaGraphDestroy(graph);
+        free_stage(stage);
+    }
 };
+
+static void destroy_entry(BatchEntry *b) { delete b; }
 
 void lnf_batch_cache_clear(lnf_ctx *ctx)
 {
-    for (BatchEntry *b : ctx->batches) {
-        if (b->exec)
-            cudaGraphExecDestroy(b->exec);
-        if (b->graph)
-            cudaGraphDestroy(b->graph);
-        delete b;
-    }
+    for (BatchEntry *b : ctx->batches)
+        destroy_entry(b);
     ctx->batches.clear();
+}
+
+// the distinct input volumes of a batch, in order of first use
+static std::vector<const void *> distinct_inputs(const lnf_job *jobs, int n, std::vector<int> &vol_of)
+{
+    std::vector<const void *> vols;
+    vol_of.assign(n, 0);
+    for (int i = 0; i < n; ++i) {
+        auto it = std::find(vols.begin(), vols.end(), jobs[i].in);
+        if (it == vols.end()) {
+            vol_of[i] = (int)vols.size();
+            vols.push_back(jobs[i].in);
+        } else {
+            vol_of[i] = (int)(it - vols.begin());
+        }
+    }
+    return vols;
+}
+
+static bool whole_volume(const lnf_job &j)
+{
+    return j.roi_dims[0] <= 0;
+}
+
+// Allocate (outside any capture) a padded copy for each distinct input that
+// TMA cannot address and that a whole-volume job of a specialised kernel reads.
+static lnf_status alloc_stage(lnf_ctx *ctx, const lnf_job *jobs, int n, std::vector<void *> &stage)
+{
+    std::vector<int> vol_of;
+    const std::vector<const void *> vols = distinct_inputs(jobs, n, vol_of);
+    stage.assign(vols.size(), nullptr);
+    if (!ctx->encode || ctx->no_tma || ctx->no_fast)
+        return LNF_OK;
+    for (int i = 0; i < n; ++i) {
+        const lnf_job &j = jobs[i];
+        const int v = vol_of[i];
+        if (stage[v] || !whole_volume(j) || !lnf_fast_covers(j.filter_id, j.radius, ctx->cfg.cluster_offset))
+            continue;
+        const size_t prow = lnf_pitched_row(j.in, j.dims, j.dtype);
+        if (prow == 0)
+            continue;
+        if (cudaMalloc(&stage[v], prow * j.dims[1] * j.dims[2]) != cudaSuccess) {
+            stage[v] = nullptr;   // no room: the generic kernel reads the input itself
+            cudaGetLastError();
+        }
+    }
+    return LNF_OK;
 }
 
 static bool same_jobs(const std::vector<lnf_job> &a, const lnf_job *b, int n)
@@ -65,22 +128,15 @@ static lnf_status check_job(lnf_ctx *ctx, const lnf_job &j, int i)
 }
 
 // Enqueue the whole batch (<= LNF_MAX_PACK jobs) on `st`: stats, params,
-// histogram zeroing, the persistent filter launch and the entropies.
+// histogram zeroing, the padded copies named by `stage` (one per distinct
+// input, null: none), the specialised launches, the persistent generic launch
+// over the remaining jobs and the entropies.
 lnf_status lnf_enqueue_batch(lnf_ctx *ctx, const lnf_job *jobs, int n, int zchunk, cudaStream_t st,
-                             std::vector<VolScratch> *scratch_out)
+                             std::vector<VolScratch> *scratch_out, const std::vector<void *> *stage)
 {
     // distinct input volumes share one statistics pass
-    std::vector<const void *> vols;
-    std::vector<int> vol_of(n);
-    for (int i = 0; i < n; ++i) {
-        auto it = std::find(vols.begin(), vols.end(), jobs[i].in);
-        if (it == vols.end()) {
-            vol_of[i] = (int)vols.size();
-            vols.push_back(jobs[i].in);
-        } else {
-            vol_of[i] = (int)(it - vols.begin());
-        }
-    }
+    std::vector<int> vol_of;
+    const std::vector<const void *> vols = distinct_inputs(jobs, n, vol_of);
     lnf_status s = lnf_scratch_pool(ctx, vols.size());
     if (s != LNF_OK)
         return s;
@@ -105,9 +161,22 @@ lnf_status lnf_enqueue_batch(lnf_ctx *ctx, const lnf_job *jobs, int n, int zchun
     CK(lnf_launch_stats_batched(sp, per, st));
     CK(lnf_launch_params_batched(sp, lnf_param_cfg(ctx->cfg), st));
 
+    // padded copies of the inputs TMA cannot address
+    std::vector<int64_t> pitch(vols.size(), 0);
+    for (size_t v = 0; stage && v < vols.size(); ++v) {
+        if (!(*stage)[v])
+            continue;
+        int first = (int)(std::find(vol_of.begin(), vol_of.end(), (int)v) - vol_of.begin());
+        const lnf_job &j = jobs[first];
+        const size_t prow = lnf_pitched_row(j.in, j.dims, j.dtype);
+        if ((s = lnf_copy_pitched(ctx, (*stage)[v], prow, j.in, j.dims, j.dtype, st)) != LNF_OK)
+            return s;
+        pitch[v] = (int64_t)(prow / (j.dtype == LNF_U8 ? 1 : 2));
+    }
+
     FilterPack &pk = ctx->pack;
     std::memset(&pk, 0, sizeof(int) * 16);
-    pk.n_jobs = n;
+    int g = 0;   // jobs left to the generic kernel
     EntropyPack ep;
     std::memset(&ep, 0, sizeof ep);
     const int zsave = ctx->zchunk;
@@ -126,15 +195,26 @@ lnf_status lnf_enqueue_batch(lnf_ctx *ctx, const lnf_job *jobs, int n, int zchun
                                         : (u64)j.dims[0] * j.dims[1] * j.dims[2];
             ep.H[k] = j.d_entropy;
         }
-        s = lnf_make_job(ctx, pk, i, j.filter_id, j.radius, j.in, j.out, j.dims, j.dtype, j.roi_origin,
-                         j.roi_dims, ctx->pool[vol_of[i]], oh);
+        const int v = vol_of[i];
+        const bool fast = !ctx->no_fast && lnf_fast_covers(j.filter_id, j.radius, ctx->cfg.cluster_offset);
+        const bool staged = fast && stage && (*stage)[v];
+        s = lnf_make_job(ctx, pk, g, j.filter_id, j.radius, staged ? (*stage)[v] : j.in, j.out, j.dims, j.dtype,
+                         j.roi_origin, j.roi_dims, ctx->pool[v], oh, staged ? pitch[v] : 0);
+        int handled = 0;
+        if (s == LNF_OK && fast) {
+            const FilterJob &fj = pk.jobs[g];
+            s = lnf_fast_dispatch(ctx, fj, fj.tmap_idx >= 0 ? &pk.tmaps[fj.tmap_idx] : nullptr, st, &handled);
+        }
         if (s != LNF_OK) {
             ctx->zchunk = zsave;
             return s;
         }
+        if (!handled)
+            ++g;
     }
     ctx->zchunk = zsave;
-    if ((s = lnf_run_pack(ctx, pk, 1, st)) != LNF_OK)
+    pk.n_jobs = g;
+    if (g > 0 && (s = lnf_run_pack(ctx, pk, 1, st)) != LNF_OK)
         return s;
     CK(lnf_launch_entropy_pack(ep, ctx->d_ent_part, ctx->d_ent_done, st));
     if (scratch_out) {
@@ -146,7 +226,7 @@ lnf_status lnf_enqueue_batch(lnf_ctx *ctx, const lnf_job *jobs, int n, int zchun
 }
 
 // time one enqueue of the batch with zchunk `zc` (events on the context stream)
-static float time_batch(lnf_ctx *ctx, const lnf_job *jobs, int n, int zc)
+static float time_batch(lnf_ctx *ctx, const lnf_job *jobs, int n, int zc, const std::vector<void *> *stage)
 {
     cudaEvent_t a, b;
     cudaEventCreate(&a);
@@ -154,7 +234,7 @@ static float time_batch(lnf_ctx *ctx, const lnf_job *jobs, int n, int zc)
     float best = 1e30f;
     for (int rep = 0; rep < 3; ++rep) {
         cudaEventRecord(a, ctx->stream);
-        if (lnf_enqueue_batch(ctx, jobs, n, zc, ctx->stream, nullptr) != LNF_OK) {
+        if (lnf_enqueue_batch(ctx, jobs, n, zc, ctx->stream, nullptr, stage) != LNF_OK) {
             best = 1e30f;
             break;
         }
@@ -195,12 +275,16 @@ extern "C" lnf_status lnf_filter_batch(lnf_ctx *ctx, const lnf_job *jobs, int n_
             CK(cudaGraphLaunch(b->exec, ctx->stream));
             return LNF_OK;
         }
+    std::unique_ptr<BatchEntry> e(new BatchEntry());
+    lnf_status ss = alloc_stage(ctx, jobs, n_jobs, e->stage);
+    if (ss != LNF_OK)
+        return ss;
     // autotune the z chunk once per context
     if (ctx->cfg.autotune && ctx->tuned_zchunk == 0) {
         int best_zc = 64;
         float best_ms = 1e30f;
         for (int zc : {16, 32, 64, 128}) {
-            float ms = time_batch(ctx, jobs, n_jobs, zc);
+            float ms = time_batch(ctx, jobs, n_jobs, zc, &e->stage);
             if (ms < best_ms) {
                 best_ms = ms;
                 best_zc = zc;
@@ -209,7 +293,6 @@ extern "C" lnf_status lnf_filter_batch(lnf_ctx *ctx, const lnf_job *jobs, int n_
         ctx->tuned_zchunk = best_zc;
     }
     const int zc = ctx->tuned_zchunk ? ctx->tuned_zchunk : 64;
-    std::unique_ptr<BatchEntry> e(new BatchEntry());
     e->key.assign(jobs, jobs + n_jobs);
     e->stream = ctx->stream;
     // capture needs a non-default stream
@@ -220,7 +303,7 @@ extern "C" lnf_status lnf_filter_batch(lnf_ctx *ctx, const lnf_job *jobs, int n_
         own = true;
     }
     CK(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
-    lnf_status s = lnf_enqueue_batch(ctx, jobs, n_jobs, zc, cap, nullptr);
+    lnf_status s = lnf_enqueue_batch(ctx, jobs, n_jobs, zc, cap, nullptr, &e->stage);
     cudaGraph_t g = nullptr;
     cudaError_t ce = cudaStreamEndCapture(cap, &g);
     if (s != LNF_OK || ce != cudaSuccess) {
@@ -238,10 +321,7 @@ extern "C" lnf_status lnf_filter_batch(lnf_ctx *ctx, const lnf_job *jobs, int n_
         return lnf_fail(ctx, LNF_ECUDA, "graph instantiate: %s", cudaGetErrorString(ie));
     CK(cudaGraphLaunch(e->exec, ctx->stream));
     if (ctx->batches.size() >= 16) {
-        BatchEntry *old = ctx->batches.front();
-        cudaGraphExecDestroy(old->exec);
-        cudaGraphDestroy(old->graph);
-        delete old;
+        destroy_entry(ctx->batches.front());
         ctx->batches.erase(ctx->batches.begin());
     }
     ctx->batches.push_back(e.release());

@@ -284,7 +284,7 @@ __device__ __forceinline__ void lx_lanes(const unsigned char *row, int ec, int l
     lxB = window_sum<R, PK>(&w[A + 1]);
 }
 
-template <typename T, int R, class PK>
+template <typename T, int R, class PK, bool MASK>
 __device__ void ours_items(const FastArgs &a, const CUtensorMap *tmap, unsigned char *smem, int *s_item,
                            int *s_abort, u32 *hist, u32 hbase)
 {
@@ -578,8 +578,8 @@ __device__ void ours_items(const FastArgs &a, const CUtensorMap *tmap, unsigned 
                         const u32 U = accA[i][k] + c[k];
                         f[k] = (p0[k] >= T_ && U >= KT) ? Div::template div_add<HALF>(U) : 0u;
                     }
-                    if (a.roi) {
-                        // a region of interest: masked stores, one voxel at a time
+                    if (MASK) {
+                        // a region of interest or an odd width: masked stores, one voxel at a time
                         // (the tile starts at xs <= ox, so some lanes lie left of it)
                         const long long ob = ((long long)(zout - a.oz) * a.by + (y - a.oy)) * a.bx - a.ox;
 #pragma unroll
@@ -661,7 +661,9 @@ __device__ void ours_items(const FastArgs &a, const CUtensorMap *tmap, unsigned 
     }
 }
 
-template <typename T, int R>
+// MASK: masked per-voxel stores (a region of interest, an odd width), else dense
+// 4-voxel vector stores
+template <typename T, int R, bool MASK>
 __global__ void __launch_bounds__(kThreads, 2) k_ours_fast(const __grid_constant__ CUtensorMap tmap, const FastArgs a)
 {
     typedef FGeo<T, R> G;
@@ -682,10 +684,10 @@ __global__ void __launch_bounds__(kThreads, 2) k_ours_fast(const __grid_constant
     const u32 M = 2 * R + 1;
     const bool narrow = 3u * M * a.prm->maxv <= 65535u;
     if (narrow)
-        ours_items<T, R, Narrow>(a, &tmap, smem, &s_item, &s_abort, a.out_hist ? hist : nullptr,
+        ours_items<T, R, Narrow, MASK>(a, &tmap, smem, &s_item, &s_abort, a.out_hist ? hist : nullptr,
                                  hbase);
     else
-        ours_items<T, R, Wide>(a, &tmap, smem, &s_item, &s_abort, a.out_hist ? hist : nullptr,
+        ours_items<T, R, Wide, MASK>(a, &tmap, smem, &s_item, &s_abort, a.out_hist ? hist : nullptr,
                                hbase);
     if (a.out_hist) {
         __syncthreads();
@@ -742,16 +744,17 @@ lnf_status launch(lnf_ctx *ctx, const FilterJob &j, cudaStream_t st, u64 *out_hi
     a.out_hist = out_hist;
     a.counter = counter ? counter : ctx->d_counter + 8;
     a.err = ctx->d_err;
-    if (cudaFuncSetAttribute(k_ours_fast<T, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, G::SMEM) != cudaSuccess)
+    void (*kern)(const CUtensorMap, const FastArgs) = a.roi ? k_ours_fast<T, R, true> : k_ours_fast<T, R, false>;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, G::SMEM) != cudaSuccess)
         return lnf_fail(ctx, LNF_ECUDA, "fast kernel: shared memory attribute");
     int occ = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_ours_fast<T, R>, kThreads, G::SMEM);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kThreads, G::SMEM);
     if (occ < 1)
         occ = 1;
     const int grid = std::min(a.total_items, ctx->num_sms * occ);
     if (cudaMemsetAsync(a.counter, 0, sizeof(u32), st) != cudaSuccess)
         return lnf_fail(ctx, LNF_ECUDA, "fast kernel: counter reset");
-    k_ours_fast<T, R><<<grid, kThreads, G::SMEM, st>>>(*tmap, a);
+    kern<<<grid, kThreads, G::SMEM, st>>>(*tmap, a);
     if (cudaGetLastError() != cudaSuccess)
         return lnf_fail(ctx, LNF_ECUDA, "fast kernel launch failed");
     *handled = 1;
@@ -760,14 +763,28 @@ lnf_status launch(lnf_ctx *ctx, const FilterJob &j, cudaStream_t st, u64 *out_hi
 
 }  // namespace
 
+bool lnf_fast_covers(int filter, int radius, int offset)
+{
+    if (radius < 1 || radius > 4)
+        return false;
+    switch (filter) {
+    case LNF_OURS: return offset == 1;
+    case LNF_SIGMA: return radius <= 2;   // r = 3 (343 taps per voxel) runs faster on the generic kernel
+    case LNF_MEAN:
+    case LNF_ENTROPY:
+    case LNF_OKADA: return true;
+    default: return false;
+    }
+}
+
 lnf_status lnf_fast_dispatch(lnf_ctx *ctx, const FilterJob &job, const CUtensorMap *tmap, cudaStream_t stream,
                              int *handled, u32 *counter)
 {
     *handled = 0;
+    if (!tmap || !lnf_fast_covers(job.filter, job.radius, job.offset))
+        return LNF_OK;
     if (job.filter != LNF_OURS)
         return lnf_fast2_dispatch(ctx, job, tmap, stream, handled, counter);
-    if (!tmap || job.offset != 1 || job.radius < 1 || job.radius > 4)
-        return LNF_OK;
     lnf_status s = LNF_OK;
     u64 *oh = job.out_hist;
     if (job.dtype == LNF_U8) {

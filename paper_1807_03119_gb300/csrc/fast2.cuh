@@ -1,6 +1,8 @@
-// Specialised kernels for the four comparison filters on whole volumes whose
-// row pitch allows TMA (lnf_fast2_dispatch); every other job runs on the
-// generic kernel (filter.cu).
+// Specialised kernels for the four comparison filters on volumes whose row
+// pitch allows TMA (whole volumes or regions of interest); every other job
+// runs on the generic kernel (filter.cu).  Included by fast2_box.cu (mean,
+// entropy filter) and fast2_tap.cu (sigma, Okada, and the dispatch), two
+// translation units that compile in parallel.
 //
 //   box kernel  -- mean (Eq. 4) and entropy filter (Eq. 7): B = sum over the
 //                  M^3 cube of q(P), q = identity or the fixed-point weight
@@ -18,6 +20,7 @@
 // planes (tile + halo, x halo widened to 16 bytes) stream into a ring of
 // shared-memory slots by TMA with one mbarrier per slot and bounded waits;
 // border tiles replicate the volume's edge into out-of-range cells.
+#pragma once
 #include "lnf_ctx.h"
 
 #include <algorithm>
@@ -220,7 +223,7 @@ struct BoxBody {
     }
 };
 
-template <typename T, int R, bool ENT>
+template <typename T, int R, bool ENT, bool MASK>
 __device__ void box_items(const Args2 &a, const CUtensorMap *tmap, unsigned char *smem, int *s_item, int *s_abort,
                           Hist2 &hist, const u32 *lut_sh, u32 lut_base)
 {
@@ -435,7 +438,7 @@ __device__ void box_items(const Args2 &a, const CUtensorMap *tmap, unsigned char
                                                                      : 0u;
                 }
                 const int y = y0 + kRows * warp + i, x = x0 + 4 * lane;
-                if (a.roi) {
+                if (MASK) {
                     store_roi<T>(a, hist, z, y, x, f);
                 } else if (y < a.ny && x < a.nx) {
                     store4<T>(a, z, y, x, f);
@@ -478,7 +481,7 @@ struct TapPack {
     static constexpr bool PACK = MAXV * M3 * (1ull << CS) < (1ull << 32);
 };
 
-template <typename T, int R, int FILTER>
+template <typename T, int R, int FILTER, bool MASK>
 __device__ void tap_items(const Args2 &a, const CUtensorMap *tmap, unsigned char *smem, int *s_item, int *s_abort,
                           Hist2 &hist, const u32 *recip)
 {
@@ -697,7 +700,7 @@ __device__ void tap_items(const Args2 &a, const CUtensorMap *tmap, unsigned char
                     f[k] = (n && p0[i][k] >= T_ && (u64)sm >= (u64)n * T_) ? q : 0u;
                 }
                 const int y = y0 + kRows * warp + i, x = x0 + 4 * lane;
-                if (a.roi) {
+                if (MASK) {
                     store_roi<T>(a, hist, z, y, x, f);
                 } else if (y < a.ny && x < a.nx) {
                     store4<T>(a, z, y, x, f);
@@ -741,7 +744,9 @@ struct K2Smem {
     static constexpr int TOTAL = 128 + MAIN + 64 + HISTB + LUTB;
 };
 
-template <typename T, int R, int FILTER>
+// MASK: masked per-voxel stores (a region of interest, an odd width), else dense
+// 4-voxel vector stores
+template <typename T, int R, int FILTER, bool MASK>
 __global__ void __launch_bounds__(kThreads, (K2Smem<T, R, FILTER>::BOX && R > 2) ? 1 : 2)
     k_fast2(const __grid_constant__ CUtensorMap tmap, const Args2 a)
 {
@@ -776,11 +781,11 @@ __global__ void __launch_bounds__(kThreads, (K2Smem<T, R, FILTER>::BOX && R > 2)
         s_abort = 0;
     __syncthreads();
     if (FILTER == LNF_MEAN)
-        box_items<T, R, false>(a, &tmap, smem, &s_item, &s_abort, h, lut_sh, lut_base);
+        box_items<T, R, false, MASK>(a, &tmap, smem, &s_item, &s_abort, h, lut_sh, lut_base);
     else if (FILTER == LNF_ENTROPY)
-        box_items<T, R, true>(a, &tmap, smem, &s_item, &s_abort, h, lut_sh, lut_base);
+        box_items<T, R, true, MASK>(a, &tmap, smem, &s_item, &s_abort, h, lut_sh, lut_base);
     else
-        tap_items<T, R, FILTER>(a, &tmap, smem, &s_item, &s_abort, h, lut_sh);
+        tap_items<T, R, FILTER, MASK>(a, &tmap, smem, &s_item, &s_abort, h, lut_sh);
     if (a.out_hist) {
         __syncthreads();
         for (int i = threadIdx.x; i < (int)bins; i += blockDim.x)
@@ -836,17 +841,18 @@ lnf_status launch2(lnf_ctx *ctx, const FilterJob &j, cudaStream_t st, u32 *count
     a.counter = counter ? counter : ctx->d_counter + 9;
     a.err = ctx->d_err;
     a.one = 1u;
-    if (cudaFuncSetAttribute(k_fast2<T, R, FILTER>, cudaFuncAttributeMaxDynamicSharedMemorySize, S::TOTAL) !=
+    void (*kern)(const CUtensorMap, const Args2) = a.roi ? k_fast2<T, R, FILTER, true> : k_fast2<T, R, FILTER, false>;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, S::TOTAL) !=
         cudaSuccess)
         return lnf_fail(ctx, LNF_ECUDA, "fast2 kernel: shared memory attribute (%d bytes)", S::TOTAL);
     int occ = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_fast2<T, R, FILTER>, kThreads, S::TOTAL);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kThreads, S::TOTAL);
     if (occ < 1)
         occ = 1;
     const int grid = std::min(a.total_items, ctx->num_sms * occ);
     if (cudaMemsetAsync(a.counter, 0, sizeof(u32), st) != cudaSuccess)
         return lnf_fail(ctx, LNF_ECUDA, "fast2 kernel: counter reset");
-    k_fast2<T, R, FILTER><<<grid, kThreads, S::TOTAL, st>>>(*tmap, a);
+    kern<<<grid, kThreads, S::TOTAL, st>>>(*tmap, a);
     if (cudaGetLastError() != cudaSuccess)
         return lnf_fail(ctx, LNF_ECUDA, "fast2 kernel launch failed");
     *handled = 1;
@@ -865,28 +871,3 @@ lnf_status by_radius(lnf_ctx *ctx, const FilterJob &j, cudaStream_t st, u32 *cou
 }
 
 }  // namespace
-
-// Route mean / sigma / entropy / Okada jobs on TMA-able volumes (whole or a
-// region of interest) at radius 1..4 (sigma 1..2) to the specialised kernels.
-lnf_status lnf_fast2_dispatch(lnf_ctx *ctx, const FilterJob &job, const CUtensorMap *tmap, cudaStream_t stream,
-                              int *handled, u32 *counter)
-{
-    *handled = 0;
-    if (!tmap || job.radius < 1 || job.radius > 4 || job.filter == LNF_OURS)
-        return LNF_OK;
-    // sigma at r = 3 (343 taps per voxel) runs faster on the generic kernel
-    if (job.filter == LNF_SIGMA && job.radius > 2)
-        return LNF_OK;
-    const bool u8 = job.dtype == LNF_U8;
-    switch (job.filter) {
-    case LNF_MEAN: return u8 ? by_radius<uint8_t, LNF_MEAN>(ctx, job, stream, counter, handled)
-                             : by_radius<uint16_t, LNF_MEAN>(ctx, job, stream, counter, handled);
-    case LNF_ENTROPY: return u8 ? by_radius<uint8_t, LNF_ENTROPY>(ctx, job, stream, counter, handled)
-                                : by_radius<uint16_t, LNF_ENTROPY>(ctx, job, stream, counter, handled);
-    case LNF_SIGMA: return u8 ? by_radius<uint8_t, LNF_SIGMA>(ctx, job, stream, counter, handled)
-                              : by_radius<uint16_t, LNF_SIGMA>(ctx, job, stream, counter, handled);
-    case LNF_OKADA: return u8 ? by_radius<uint8_t, LNF_OKADA>(ctx, job, stream, counter, handled)
-                              : by_radius<uint16_t, LNF_OKADA>(ctx, job, stream, counter, handled);
-    default: return LNF_OK;
-    }
-}

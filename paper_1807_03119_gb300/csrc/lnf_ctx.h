@@ -55,6 +55,9 @@ struct lnf_ctx {
     size_t st_in_cap = 0;
     std::vector<void *> st_out;
     std::vector<size_t> st_out_cap;
+    // plain calls: a copy of an input TMA cannot address, rows padded to 16 bytes
+    void *pitched = nullptr;
+    size_t pitched_cap = 0;
     // batched graph cache
     std::vector<BatchEntry *> batches;   // owned; freed by lnf_batch_cache_clear
     // autotuner choice for batched launches (0 = not tuned yet)
@@ -92,16 +95,27 @@ lnf_status lnf_run_pack(lnf_ctx *ctx, FilterPack &pk, int persistent, cudaStream
 lnf_status lnf_run_pack_counter(lnf_ctx *ctx, FilterPack &pk, int persistent, cudaStream_t stream, u32 *counter);
 lnf_status lnf_run_one(lnf_ctx *ctx, int filter, int radius, const void *in, void *out, const int64_t dims[3],
                        int dtype, const int64_t *roi_o, const int64_t *roi_d, const VolScratch &vs,
-                       u64 *out_hist, cudaStream_t stream);
+                       u64 *out_hist, cudaStream_t stream, int64_t pitch = 0);
+// Row length in bytes of the padded copy of an input TMA cannot address (0: the
+// input itself is addressable: 16-byte-aligned base and row length)
+size_t lnf_pitched_row(const void *in, const int64_t dims[3], int dtype);
+// Copy `in` into `dst` with rows padded to `prow` bytes (on `st`)
+lnf_status lnf_copy_pitched(lnf_ctx *ctx, void *dst, size_t prow, const void *in, const int64_t dims[3], int dtype,
+                            cudaStream_t st);
 // profiling helpers (api.cu): bracket one launch (or a group of `count` launches)
 int lnf_prof_begin(lnf_ctx *ctx, cudaStream_t st);
 void lnf_prof_end(lnf_ctx *ctx, int rec, const char *name, cudaStream_t st, int count);
+// fast.cu: whether a specialised kernel covers this filter, radius and cluster
+// offset (on an input TMA can address)
+bool lnf_fast_covers(int filter, int radius, int offset);
 // fast.cu: run the job through a specialised kernel if one covers it (*handled = 1);
 // `counter` is the launch's work counter (null: the context's own, for its stream)
 lnf_status lnf_fast_dispatch(lnf_ctx *ctx, const FilterJob &job, const CUtensorMap *tmap, cudaStream_t stream,
                              int *handled, u32 *counter = nullptr);
 lnf_status lnf_fast2_dispatch(lnf_ctx *ctx, const FilterJob &job, const CUtensorMap *tmap, cudaStream_t stream,
                               int *handled, u32 *counter = nullptr);
+// fast2_box.cu: the mean / entropy-filter job through its box kernel
+lnf_status lnf_fast2_box(lnf_ctx *ctx, const FilterJob &job, cudaStream_t stream, u32 *counter, int *handled);
 // batch.cu
 void lnf_batch_cache_clear(lnf_ctx *ctx);
 // serve.cu
