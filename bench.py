@@ -72,29 +72,84 @@ def algorithmic(kind):
     return None, None
 
 
-def source_digest():
+# the kernel sources behind each kind of launch (a recorded traffic figure is
+# void once any of them changes)
+KIND_SOURCES = {
+    "stats": ["stats.cu"],
+    "params": ["stats.cu"],
+    "entropy": ["stats.cu"],
+    "filter:ours": ["fast.cu"],
+    "filter:mean": ["fast2.cuh", "fast2_box.cu"],
+    "filter:entropy": ["fast2.cuh", "fast2_box.cu"],
+    "filter:sigma": ["fast2.cuh", "fast2_tap.cu"],
+    "filter:okada": ["fast2.cuh", "fast2_tap.cu"],
+}
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "dram_traffic_512cubed_u16_r2.txt")
+
+
+def source_digest(kind):
     h = hashlib.sha256()
     cdir = os.path.join(ROOT, "paper_1807_03119_gb300", "csrc")
-    for fn in sorted(os.listdir(cdir)):
-        if fn.endswith((".cu", ".cuh", ".h")):
-            with open(os.path.join(cdir, fn), "rb") as f:
-                h.update(f.read())
+    for fn in KIND_SOURCES.get(kind, []) + ["lnf_internal.cuh", "lnf_ctx.h"]:
+        with open(os.path.join(cdir, fn), "rb") as f:
+            h.update(f.read())
     return h.hexdigest()[:16]
 
 
 def recorded_traffic(kind):
     """DRAM bytes per launch from the committed ncu summary, if it was taken on
-    the current kernel sources (else None)."""
-    p = os.path.join(ROOT, "profiles", "dram_traffic_512cubed_u16_r2.txt")
-    if not os.path.exists(p):
+    the current sources of that kernel (else None)."""
+    if not os.path.exists(TRAFFIC_FILE):
         return None
-    dig = source_digest()
-    with open(p) as f:
+    dig = source_digest(kind)
+    with open(TRAFFIC_FILE) as f:
         for line in f:
             parts = line.split()
             if len(parts) >= 3 and parts[0] == kind and parts[2] == dig:
                 return int(parts[1])
     return None
+
+
+def kind_of_kernel(name):
+    """Bench kind of an ncu kernel name (None for launches that are not ours)."""
+    import re
+    m = re.search(r"k_fast2<[^,]+, \d+, (\d+)", name)
+    if m:
+        return "filter:" + {0: "mean", 1: "sigma", 2: "entropy", 3: "okada"}[int(m.group(1))]
+    if "k_ours_fast" in name:
+        return "filter:ours"
+    for k, kind in (("k_stats_batched", None), ("k_stats<", "stats"), ("k_params", "params"),
+                    ("k_entropy_pack", "entropy")):
+        if k in name:
+            return kind
+    return None
+
+
+def record_traffic(csv_path, scale):
+    """Write the traffic file from an ncu CSV log (metrics dram__bytes_read.sum and
+    dram__bytes_write.sum per launch, e.g. of `bench.py --dims 384 384 512`):
+    mean bytes per launch of each kind, times `scale` (the voxel ratio to the
+    512^3 workload), tagged with the digest of that kind's sources."""
+    import csv
+    rows = {}
+    with open(csv_path) as f:
+        lines = [l for l in f if l.startswith('"')]
+    for r in csv.DictReader(lines):
+        key = (r["ID"], r["Kernel Name"])
+        rows.setdefault(key, {})[r["Metric Name"]] = float(r["Metric Value"].replace(",", ""))
+    acc = {}
+    for (_, name), m in rows.items():
+        kind = kind_of_kernel(name)
+        if kind is None or "dram__bytes_read.sum" not in m:
+            continue
+        a = acc.setdefault(kind, [0, 0.0])
+        a[0] += 1
+        a[1] += m["dram__bytes_read.sum"] + m.get("dram__bytes_write.sum", 0.0)
+    with open(TRAFFIC_FILE, "w") as f:
+        for kind in sorted(acc):
+            n, b = acc[kind]
+            f.write(f"{kind} {int(round(b / n * scale))} {source_digest(kind)}\n")
+    print(f"wrote {TRAFFIC_FILE}: {sorted(acc)}")
 
 
 class ClockSampler:
@@ -226,7 +281,13 @@ def main():
                     help="profiling: a smaller phantom of the same workload (nx ny nz); not a bench line")
     ap.add_argument("--no-e2e", action="store_true", help="profiling: skip the host-buffer leg")
     ap.add_argument("--clocks-csv", default=None, help="keep the nvidia-smi clock samples in this file")
+    ap.add_argument("--record-traffic", default=None, metavar="NCU_CSV",
+                    help="write the per-kind DRAM traffic file from an ncu CSV log and exit")
+    ap.add_argument("--traffic-scale", type=float, default=1.0,
+                    help="with --record-traffic: voxels of the 512^3 workload / voxels of the captured case")
     args = ap.parse_args()
+    if args.record_traffic:
+        return record_traffic(args.record_traffic, args.traffic_scale)
     if args.warmup < 3:
         args.warmup = 3
 
