@@ -2,6 +2,270 @@
 // dispatch of the four comparison filters to the specialised kernels.
 #include "fast2.cuh"
 
+namespace {
+
+// ------------------------------------------------------------------ tap kernel body
+
+// SIGMA: |P_i - P0| <= delta over the cube; OKADA: centre + axis cross, |P0 - P_i| < td.
+// Value and count are accumulated in one word: acc += (v << CS) | 1.
+template <typename T, int R>
+struct TapPack {
+    static constexpr int M3 = (2 * R + 1) * (2 * R + 1) * (2 * R + 1);
+    static constexpr int CS = M3 < 256 ? 8 : (M3 < 1024 ? 10 : 13);
+    static constexpr unsigned long long MAXV = sizeof(T) == 1 ? 255ull : 65535ull;
+    static constexpr bool PACK = MAXV * M3 * (1ull << CS) < (1ull << 32);
+};
+
+template <typename T, int R, int FILTER, bool MASK>
+__device__ void tap_items(const Args2 &a, const CUtensorMap *tmap, unsigned char *smem, int *s_item, int *s_abort,
+                          Hist2 &hist, const u32 *recip)
+{
+    using namespace lnfdev;
+    typedef Geo2<T, R> G;
+    typedef TapPack<T, R> TP;
+    unsigned char *ring = smem;
+    u64 *bars = reinterpret_cast<u64 *>(smem + G::RING);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int c0 = G::XH + 4 * lane;
+    const int r0 = G::H + kRows * warp;
+    const DevParams &P = *a.prm;
+    const u32 T_ = P.T;
+    const u32 dl = min(P.delta, 65535u);
+    const long long td = P.td;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < G::NP; ++s)
+            mbar_init(&bars[s], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+
+    for (;;) {
+        if (threadIdx.x == 0)
+            *s_item = (int)atomicAdd(a.counter, 1u);
+        __syncthreads();
+        const int item = *s_item;
+        __syncthreads();
+        if (item >= a.total_items || *s_abort)
+            break;
+        const int tx = item % a.tiles_x;
+        const int rest = item / a.tiles_x;
+        const int ty = rest % a.tiles_y;
+        const int zc = rest / a.tiles_y;
+        const int x0 = a.xs + tx * kTX, y0 = a.oy + ty * kTY;
+        const int z0 = a.oz + zc * a.zlen, z1 = min(a.oz + a.bz, z0 + a.zlen);
+        const int px0 = x0 - G::XH, py0 = y0 - G::H;
+        const bool border = px0 < 0 || px0 + G::PW > a.nx || py0 < 0 || py0 + G::PH > a.ny;
+        const int nplanes = (z1 - z0) + 2 * R;
+        const u32 pbytes = G::PW * G::PH * sizeof(T);
+        auto issue = [&](int p) {
+            const int slot = p % G::NP;
+            fence_proxy_async_smem();
+            mbar_arrive_expect_tx(&bars[slot], pbytes);
+            tma_load_3d(ring + slot * G::PBYTES, tmap, &bars[slot], px0, py0, clampi(z0 - R + p, 0, a.nz - 1));
+        };
+        auto prefetch = [&](int p) {   // thread 0 only: plane p into L2
+            if (p < nplanes)
+                tma_prefetch_3d(tmap, max(px0, 0), max(py0, 0), clampi(z0 - R + p, 0, a.nz - 1));
+        };
+        if (threadIdx.x == 0) {
+            for (int p = 0; p < min(G::NP, nplanes); ++p)
+                issue(p);
+            for (int p = G::NP; p < G::NP + kL2Ahead; ++p)
+                prefetch(p);
+        }
+        bool ok = true;
+        for (int s = 0; s < z1 - z0; ++s) {
+            // one thread waits for the TMA completions; the barrier orders the
+            // data before every thread's reads
+            const int pfirst = s == 0 ? 0 : s + 2 * R;
+            if (threadIdx.x == 0)
+                for (int p = pfirst; p <= s + 2 * R; ++p)
+                    if (!mbar_wait_bounded(&bars[p % G::NP], (u32)((p / G::NP) & 1), a.err))
+                        *s_abort = 1;
+            __syncthreads();
+            if (*s_abort) {
+                ok = false;
+                break;
+            }
+            // plane s-1 was last read at step s-1, which every thread has finished
+            if (threadIdx.x == 0 && s >= 1 && s - 1 + G::NP < nplanes) {
+                issue(s - 1 + G::NP);
+                prefetch(s - 1 + G::NP + kL2Ahead);
+            }
+            if (border)
+                for (int p = pfirst; p <= s + 2 * R; ++p)
+                    fixup2<T, R>(ring + (p % G::NP) * G::PBYTES, px0, py0, a.nx, a.ny);
+            const unsigned char *pc = ring + ((s + R) % G::NP) * G::PBYTES;   // plane z
+            u32 p0[kRows][4], lo[kRows][4], wd[kRows][4];
+#pragma unroll
+            for (int i = 0; i < kRows; ++i) {
+                ld4<T>(pc + (r0 + i) * G::ROWB, c0, p0[i]);
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    if (FILTER == LNF_SIGMA) {   // band [P0 - delta, P0 + delta] as (v - lo) <= width
+                        lo[i][k] = p0[i][k] > dl ? p0[i][k] - dl : 0u;
+                        wd[i][k] = p0[i][k] - lo[i][k] + dl;
+                    } else {                     // |P0 - v| < td  as (v - lo) <= width, td >= 1
+                        const u32 t1 = td > 65536 ? 65535u : (u32)(td - 1);
+                        lo[i][k] = p0[i][k] > t1 ? p0[i][k] - t1 : 0u;
+                        wd[i][k] = p0[i][k] - lo[i][k] + t1;
+                    }
+                }
+            }
+            u32 acc[kRows][4], cnt[kRows][4];
+#pragma unroll
+            for (int i = 0; i < kRows; ++i)
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    acc[i][k] = 0;
+                    cnt[i][k] = 0;
+                }
+            // per tap and voxel: d = v - lo (multiply-add: FMA pipe), in-band test
+            // (compare: ALU pipe), accumulate (alternately FMA and ALU pipe), so
+            // that the integer work is split between the two half-rate pipes
+            const u32 one = a.one;
+            u32 nlo[kRows][4];
+#pragma unroll
+            for (int i = 0; i < kRows; ++i)
+#pragma unroll
+                for (int k = 0; k < 4; ++k)
+                    nlo[i][k] = 0u - lo[i][k];
+            auto take = [&](int i, int k, u32 v, u32 pv) {
+                if (TP::PACK) {
+                    // d = v - lo: a plain add (ALU) for even voxels, a multiply-add by
+                    // the runtime 1 (FMA pipe) for odd ones; the in-band test is a
+                    // compare (ALU) and the accumulate a predicated multiply-add (FMA)
+                    u32 d;
+                    if (k & 1)
+                        asm("mad.lo.u32 %0, %1, %2, %3;" : "=r"(d) : "r"(v), "r"(one), "r"(nlo[i][k]));
+                    else
+                        d = v + nlo[i][k];
+                    asm(
+                        "{\n\t.reg .pred p;\n\tsetp.le.u32 p, %1, %2;\n\t@p mad.lo.u32 %0, %3, %4, %0;\n\t}"
+                        : "+r"(acc[i][k])
+                        : "r"(d), "r"(wd[i][k]), "r"(pv), "r"(one));
+                } else {
+                    if (v - lo[i][k] <= wd[i][k]) {
+                        acc[i][k] += v;
+                        cnt[i][k] += 1;
+                    }
+                }
+            };
+            if (FILTER == LNF_SIGMA) {
+#pragma unroll 1
+                for (int dz = -R; dz <= R; ++dz) {
+                    const unsigned char *pl = ring + ((s + R + dz) % G::NP) * G::PBYTES;
+#pragma unroll
+                    for (int rr = 0; rr < kRows + 2 * R; ++rr) {   // rows r0 - R .. r0 + 3 + R
+                        u32 v[12], pv[12];
+                        const unsigned char *row = pl + (r0 - R + rr) * G::ROWB;
+                        ld4<T>(row, c0 - 4, v);
+                        ld4<T>(row, c0, v + 4);
+                        ld4<T>(row, c0 + 4, v + 8);
+#pragma unroll
+                        for (int e = 0; e < 12; ++e)
+                            pv[e] = TP::PACK ? ((v[e] << TP::CS) | 1u) : v[e];
+#pragma unroll
+                        for (int i = 0; i < kRows; ++i) {
+                            const int dy = rr - R - i;
+                            if (dy < -R || dy > R)
+                                continue;
+#pragma unroll
+                            for (int k = 0; k < 4; ++k)
+#pragma unroll
+                                for (int dx = -R; dx <= R; ++dx)
+                                    take(i, k, v[4 + k + dx], pv[4 + k + dx]);
+                        }
+                    }
+                }
+            } else if (td > 0) {   // Okada: centre + cross of arm R (td == 0 selects nothing)
+#pragma unroll
+                for (int i = 0; i < kRows; ++i) {
+                    const unsigned char *row = pc + (r0 + i) * G::ROWB;
+                    u32 v[12];
+                    ld4<T>(row, c0 - 4, v);
+                    ld4<T>(row, c0, v + 4);
+                    ld4<T>(row, c0 + 4, v + 8);
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        auto pk = [&](u32 x) { return TP::PACK ? ((x << TP::CS) | 1u) : x; };
+                        take(i, k, v[4 + k], pk(v[4 + k]));   // the centre itself
+#pragma unroll
+                        for (int t = 1; t <= R; ++t) {
+                            take(i, k, v[4 + k - t], pk(v[4 + k - t]));
+                            take(i, k, v[4 + k + t], pk(v[4 + k + t]));
+                        }
+                    }
+                }
+#pragma unroll
+                for (int t = 1; t <= R; ++t) {
+#pragma unroll
+                    for (int sg = -1; sg <= 1; sg += 2) {
+                        const unsigned char *plz = ring + ((s + R + sg * t) % G::NP) * G::PBYTES;
+#pragma unroll
+                        for (int i = 0; i < kRows; ++i) {
+                            u32 vy[4], vz[4];
+                            ld4<T>(pc + (r0 + i + sg * t) * G::ROWB, c0, vy);
+                            ld4<T>(plz + (r0 + i) * G::ROWB, c0, vz);
+#pragma unroll
+                            for (int k = 0; k < 4; ++k) {
+                                take(i, k, vy[k], TP::PACK ? ((vy[k] << TP::CS) | 1u) : vy[k]);
+                                take(i, k, vz[k], TP::PACK ? ((vz[k] << TP::CS) | 1u) : vz[k]);
+                            }
+                        }
+                    }
+                }
+            }
+            // ---- gate, round, store, histogram
+            // round(sm / n) half up = floor((sm + floor(n/2)) / n) = (x * recip[n]) >> 32
+            // with recip[n] = ceil(2^32 / n): exact when x e < 2^32 (e = recip n - 2^32 < n);
+            // x < n 2^16 gives x e < n^2 2^16, so counts below 256 use the table
+            // and larger ones (sigma at radius >= 3) divide
+            const int z = z0 + s;
+#pragma unroll
+            for (int i = 0; i < kRows; ++i) {
+                u32 f[4];
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const u32 n = TP::PACK ? (acc[i][k] & ((1u << TP::CS) - 1u)) : cnt[i][k];
+                    const u32 sm = TP::PACK ? (acc[i][k] >> TP::CS) : acc[i][k];
+                    const u32 x = sm + (n >> 1);
+                    const u32 q = n == 1 ? sm : (n < 256 ? __umulhi(x, recip[n]) : x / n);
+                    f[k] = (n && p0[i][k] >= T_ && (u64)sm >= (u64)n * T_) ? q : 0u;
+                }
+                const int y = y0 + kRows * warp + i, x = x0 + 4 * lane;
+                if (MASK) {
+                    store_roi<T>(a, hist, z, y, x, f);
+                } else if (y < a.ny && x < a.nx) {
+                    store4<T>(a, z, y, x, f);
+                    hist4(hist, f);
+                }
+            }
+        }
+        if (!ok) {
+            if (threadIdx.x == 0) {
+                const u64 t0 = global_ns();
+                while (global_ns() - t0 < 2000000ull) {
+                }
+            }
+            __syncthreads();
+            break;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            for (int sl = 0; sl < G::NP; ++sl) {
+                mbar_inval(&bars[sl]);
+                mbar_init(&bars[sl], 1);
+            }
+            fence_mbar_init();
+        }
+        __syncthreads();
+    }
+}
+
+}  // namespace
+
 // Route mean / sigma / entropy / Okada jobs on TMA-able volumes (whole or a
 // region of interest) at radius 1..4 (sigma 1..2) to the specialised kernels.
 lnf_status lnf_fast2_dispatch(lnf_ctx *ctx, const FilterJob &job, const CUtensorMap *tmap, cudaStream_t stream,
