@@ -228,6 +228,10 @@ extern "C" void lnf_destroy(lnf_ctx *ctx)
     cudaFree(ctx->d_err);
     cudaFree(ctx->d_counter);
     cudaFree(ctx->pitched);
+    for (cudaEvent_t e : ctx->filter_done)
+        cudaEventDestroy(e);
+    if (ctx->copy_stream)
+        cudaStreamDestroy(ctx->copy_stream);
     cudaFree(ctx->d_ent_part);
     cudaFree(ctx->d_ent_done);
     cudaFree(ctx->st_in);
@@ -592,8 +596,19 @@ extern "C" lnf_status lnf_filter_roi(lnf_ctx *ctx, int filter_id, int radius, co
                        ctx->stream);
 }
 
+// lnf_filter_multi, recording `after[i]` on the context stream once filter i
+// has been enqueued (when `after` is not null)
+static lnf_status multi_impl(lnf_ctx *ctx, int radius, const void *in, const int64_t dims[3], int dtype, int n,
+                             const int *filter_ids, void *const *outs, double *d_entropy, cudaEvent_t *after);
+
 extern "C" lnf_status lnf_filter_multi(lnf_ctx *ctx, int radius, const void *in, const int64_t dims[3], int dtype,
                                        int n, const int *filter_ids, void *const *outs, double *d_entropy)
+{
+    return multi_impl(ctx, radius, in, dims, dtype, n, filter_ids, outs, d_entropy, nullptr);
+}
+
+static lnf_status multi_impl(lnf_ctx *ctx, int radius, const void *in, const int64_t dims[3], int dtype, int n,
+                             const int *filter_ids, void *const *outs, double *d_entropy, cudaEvent_t *after)
 {
     if (!ctx)
         return LNF_EINVAL;
@@ -632,6 +647,8 @@ extern "C" lnf_status lnf_filter_multi(lnf_ctx *ctx, int radius, const void *in,
         if ((s = lnf_run_one(ctx, filter_ids[i], radius, f ? src : in, outs[i], dims, dtype, nullptr, nullptr,
                              ctx->vs, oh, st, f ? pitch : 0)) != LNF_OK)
             return s;
+        if (after)
+            CK(cudaEventRecord(after[i], st));
     }
     if (d_entropy) {
         CK(cudaMemcpyAsync(d_entropy, &ctx->vs.prm->H_in, sizeof(double), cudaMemcpyDeviceToDevice, st));
@@ -688,16 +705,30 @@ extern "C" lnf_status lnf_filter_multi_host(lnf_ctx *ctx, int radius, const void
     for (int i = 0; i < n; ++i)
         if ((s = ensure_stage(ctx, &ctx->st_out[i], &ctx->st_out_cap[i], bytes)) != LNF_OK)
             return s;
-    cudaStream_t st = ctx->stream;
+    // each output goes back on a copy stream as soon as its filter is done, so
+    // the copies overlap the filters that follow
+    if (!ctx->copy_stream)
+        CK(cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking));
+    while ((int)ctx->filter_done.size() < n) {
+        cudaEvent_t e;
+        CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        ctx->filter_done.push_back(e);
+    }
+    cudaStream_t st = ctx->stream, cs = ctx->copy_stream;
     CK(cudaMemcpyAsync(ctx->st_in, in, bytes, cudaMemcpyHostToDevice, st));
-    if ((s = lnf_filter_multi(ctx, radius, ctx->st_in, dims, dtype, n, filter_ids, ctx->st_out.data(),
-                              ctx->d_H)) != LNF_OK)
+    if ((s = multi_impl(ctx, radius, ctx->st_in, dims, dtype, n, filter_ids, ctx->st_out.data(), ctx->d_H,
+                        ctx->filter_done.data())) != LNF_OK) {
+        cudaStreamSynchronize(st);
         return s;
-    for (int i = 0; i < n; ++i)
-        CK(cudaMemcpyAsync(outs[i], ctx->st_out[i], bytes, cudaMemcpyDeviceToHost, st));
+    }
+    for (int i = 0; i < n; ++i) {
+        CK(cudaStreamWaitEvent(cs, ctx->filter_done[i], 0));
+        CK(cudaMemcpyAsync(outs[i], ctx->st_out[i], bytes, cudaMemcpyDeviceToHost, cs));
+    }
     double hbuf[LNF_MAX_PACK + 1];
     CK(cudaMemcpyAsync(hbuf, ctx->d_H, sizeof(double) * (n + 1), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
+    CK(cudaStreamSynchronize(cs));
     if (entropy)
         std::memcpy(entropy, hbuf, sizeof(double) * (n + 1));
     return LNF_OK;

@@ -55,6 +55,8 @@ struct lnf_ctx {
     size_t st_in_cap = 0;
     std::vector<void *> st_out;
     std::vector<size_t> st_out_cap;
+    cudaStream_t copy_stream = nullptr;        // device-to-host copies that overlap the filters
+    std::vector<cudaEvent_t> filter_done;      // one per filter of a multi-filter call
     // plain calls: a copy of an input TMA cannot address, rows padded to 16 bytes
     void *pitched = nullptr;
     size_t pitched_cap = 0;
