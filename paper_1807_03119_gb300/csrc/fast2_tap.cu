@@ -16,6 +16,33 @@ struct TapPack {
     static constexpr bool PACK = MAXV * M3 * (1ull << CS) < (1ull << 32);
 };
 
+// four voxels at columns col..col+3 of a shared row as packed tap words
+// (v << CS) | 1; for CS = 8 one byte permute per voxel builds the word from the
+// loaded bytes directly
+template <typename T, int CS>
+__device__ __forceinline__ void ld4p(const unsigned char *row, int col, u32 pv[4])
+{
+    if (CS == 8 && sizeof(T) == 2) {
+        const uint2 w = *reinterpret_cast<const uint2 *>(row + col * 2);
+        pv[0] = __byte_perm(w.x, 1u, 0x5104);   // bytes: 1, v.lo, v.hi, 0
+        pv[1] = __byte_perm(w.x, 1u, 0x5324);
+        pv[2] = __byte_perm(w.y, 1u, 0x5104);
+        pv[3] = __byte_perm(w.y, 1u, 0x5324);
+    } else if (CS == 8) {
+        const u32 w = *reinterpret_cast<const u32 *>(row + col);
+        pv[0] = __byte_perm(w, 1u, 0x5504);     // bytes: 1, v, 0, 0
+        pv[1] = __byte_perm(w, 1u, 0x5514);
+        pv[2] = __byte_perm(w, 1u, 0x5524);
+        pv[3] = __byte_perm(w, 1u, 0x5534);
+    } else {
+        u32 v[4];
+        ld4<T>(row, col, v);
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            pv[k] = (v[k] << CS) | 1u;
+    }
+}
+
 template <typename T, int R, int FILTER, bool MASK>
 __device__ void tap_items(const Args2 &a, const CUtensorMap *tmap, unsigned char *smem, int *s_item, int *s_abort,
                           Hist2 &hist, const u32 *recip)
@@ -121,30 +148,37 @@ __device__ void tap_items(const Args2 &a, const CUtensorMap *tmap, unsigned char
                     acc[i][k] = 0;
                     cnt[i][k] = 0;
                 }
-            // per tap and voxel: d = v - lo (multiply-add: FMA pipe), in-band test
-            // (compare: ALU pipe), accumulate (alternately FMA and ALU pipe), so
-            // that the integer work is split between the two half-rate pipes
+            // per tap and voxel: d = pv - (lo << CS) (multiply-add: FMA pipe), in-band
+            // test (compare: ALU pipe), accumulate (alternately FMA and ALU pipe), so
+            // that the integer work is split between the two half-rate pipes.  On the
+            // packed word pv = (v << CS) | 1 the band test v - lo <= wd reads
+            // pv - (lo << CS) <= (wd << CS) + 1: for v >= lo both sides are the
+            // shifted difference plus 1, and for v < lo the left side wraps above
+            // 2^32 - 65535 * 2^CS, beyond any right side
             const u32 one = a.one;
-            u32 nlo[kRows][4];
+            u32 nlo[kRows][4], wdp[kRows][4];
 #pragma unroll
             for (int i = 0; i < kRows; ++i)
 #pragma unroll
-                for (int k = 0; k < 4; ++k)
-                    nlo[i][k] = 0u - lo[i][k];
+                for (int k = 0; k < 4; ++k) {
+                    nlo[i][k] = TP::PACK ? 0u - (lo[i][k] << TP::CS) : 0u - lo[i][k];
+                    wdp[i][k] = TP::PACK ? (wd[i][k] << TP::CS) + 1u : wd[i][k];
+                }
             auto take = [&](int i, int k, u32 v, u32 pv) {
                 if (TP::PACK) {
-                    // d = v - lo: a plain add (ALU) for even voxels, a multiply-add by
-                    // the runtime 1 (FMA pipe) for odd ones; the in-band test is a
-                    // compare (ALU) and the accumulate a predicated multiply-add (FMA)
+                    // d = pv - (lo << CS): a plain add (ALU) for even voxels, a
+                    // multiply-add by the runtime 1 (FMA pipe) for odd ones; the
+                    // in-band test is a compare (ALU) and the accumulate a predicated
+                    // multiply-add (FMA)
                     u32 d;
                     if (k & 1)
-                        asm("mad.lo.u32 %0, %1, %2, %3;" : "=r"(d) : "r"(v), "r"(one), "r"(nlo[i][k]));
+                        asm("mad.lo.u32 %0, %1, %2, %3;" : "=r"(d) : "r"(pv), "r"(one), "r"(nlo[i][k]));
                     else
-                        d = v + nlo[i][k];
+                        d = pv + nlo[i][k];
                     asm(
                         "{\n\t.reg .pred p;\n\tsetp.le.u32 p, %1, %2;\n\t@p mad.lo.u32 %0, %3, %4, %0;\n\t}"
                         : "+r"(acc[i][k])
-                        : "r"(d), "r"(wd[i][k]), "r"(pv), "r"(one));
+                        : "r"(d), "r"(wdp[i][k]), "r"(pv), "r"(one));
                 } else {
                     if (v - lo[i][k] <= wd[i][k]) {
                         acc[i][k] += v;
@@ -160,12 +194,21 @@ __device__ void tap_items(const Args2 &a, const CUtensorMap *tmap, unsigned char
                     for (int rr = 0; rr < kRows + 2 * R; ++rr) {   // rows r0 - R .. r0 + 3 + R
                         u32 v[12], pv[12];
                         const unsigned char *row = pl + (r0 - R + rr) * G::ROWB;
-                        ld4<T>(row, c0 - 4, v);
-                        ld4<T>(row, c0, v + 4);
-                        ld4<T>(row, c0 + 4, v + 8);
+                        if (TP::PACK) {   // the packed words only (the band test reads them)
+                            ld4p<T, TP::CS>(row, c0 - 4, pv);
+                            ld4p<T, TP::CS>(row, c0, pv + 4);
+                            ld4p<T, TP::CS>(row, c0 + 4, pv + 8);
 #pragma unroll
-                        for (int e = 0; e < 12; ++e)
-                            pv[e] = TP::PACK ? ((v[e] << TP::CS) | 1u) : v[e];
+                            for (int e = 0; e < 12; ++e)
+                                v[e] = pv[e];
+                        } else {
+                            ld4<T>(row, c0 - 4, v);
+                            ld4<T>(row, c0, v + 4);
+                            ld4<T>(row, c0 + 4, v + 8);
+#pragma unroll
+                            for (int e = 0; e < 12; ++e)
+                                pv[e] = v[e];
+                        }
 #pragma unroll
                         for (int i = 0; i < kRows; ++i) {
                             const int dy = rr - R - i;
@@ -183,18 +226,23 @@ __device__ void tap_items(const Args2 &a, const CUtensorMap *tmap, unsigned char
 #pragma unroll
                 for (int i = 0; i < kRows; ++i) {
                     const unsigned char *row = pc + (r0 + i) * G::ROWB;
-                    u32 v[12];
-                    ld4<T>(row, c0 - 4, v);
-                    ld4<T>(row, c0, v + 4);
-                    ld4<T>(row, c0 + 4, v + 8);
+                    u32 v[12];   // packed words (PACK) or values
+                    if (TP::PACK) {
+                        ld4p<T, TP::CS>(row, c0 - 4, v);
+                        ld4p<T, TP::CS>(row, c0, v + 4);
+                        ld4p<T, TP::CS>(row, c0 + 4, v + 8);
+                    } else {
+                        ld4<T>(row, c0 - 4, v);
+                        ld4<T>(row, c0, v + 4);
+                        ld4<T>(row, c0 + 4, v + 8);
+                    }
 #pragma unroll
                     for (int k = 0; k < 4; ++k) {
-                        auto pk = [&](u32 x) { return TP::PACK ? ((x << TP::CS) | 1u) : x; };
-                        take(i, k, v[4 + k], pk(v[4 + k]));   // the centre itself
+                        take(i, k, v[4 + k], v[4 + k]);   // the centre itself
 #pragma unroll
                         for (int t = 1; t <= R; ++t) {
-                            take(i, k, v[4 + k - t], pk(v[4 + k - t]));
-                            take(i, k, v[4 + k + t], pk(v[4 + k + t]));
+                            take(i, k, v[4 + k - t], v[4 + k - t]);
+                            take(i, k, v[4 + k + t], v[4 + k + t]);
                         }
                     }
                 }
@@ -205,13 +253,18 @@ __device__ void tap_items(const Args2 &a, const CUtensorMap *tmap, unsigned char
                         const unsigned char *plz = ring + ((s + R + sg * t) % G::NP) * G::PBYTES;
 #pragma unroll
                         for (int i = 0; i < kRows; ++i) {
-                            u32 vy[4], vz[4];
-                            ld4<T>(pc + (r0 + i + sg * t) * G::ROWB, c0, vy);
-                            ld4<T>(plz + (r0 + i) * G::ROWB, c0, vz);
+                            u32 vy[4], vz[4];   // packed words (PACK) or values
+                            if (TP::PACK) {
+                                ld4p<T, TP::CS>(pc + (r0 + i + sg * t) * G::ROWB, c0, vy);
+                                ld4p<T, TP::CS>(plz + (r0 + i) * G::ROWB, c0, vz);
+                            } else {
+                                ld4<T>(pc + (r0 + i + sg * t) * G::ROWB, c0, vy);
+                                ld4<T>(plz + (r0 + i) * G::ROWB, c0, vz);
+                            }
 #pragma unroll
                             for (int k = 0; k < 4; ++k) {
-                                take(i, k, vy[k], TP::PACK ? ((vy[k] << TP::CS) | 1u) : vy[k]);
-                                take(i, k, vz[k], TP::PACK ? ((vz[k] << TP::CS) | 1u) : vz[k]);
+                                take(i, k, vy[k], vy[k]);
+                                take(i, k, vz[k], vz[k]);
                             }
                         }
                     }
