@@ -266,9 +266,11 @@ __device__ __forceinline__ bool otsu_better(const OtsuJ &a, const OtsuJ &b)
     return c > 0 || (c == 0 && a.t < b.t);
 }
 
-// ---- parameter derivation over chunks of 1024 grey levels (a 16-bit
-// histogram has 64 chunks, an 8-bit one a single chunk of 256 levels)
-constexpr int kChunk = 1024;
+// ---- parameter derivation over chunks of 256 grey levels, one level per
+// thread (a 16-bit histogram has 256 chunks, an 8-bit one a single chunk): the
+// exact per-level work (128-bit Otsu quotients, the fixed-point logarithm)
+// runs on as many threads as there are levels
+constexpr int kChunk = 256;
 constexpr int kPThreads = 256;
 
 struct ParamPartial {          // one per chunk
@@ -342,11 +344,28 @@ __device__ void chunk_params(const u64 *hist, const DevStats *st, const ParamCfg
     const u32 L = st->levels;
     const u64 N = st->N, S = st->S, Q = st->Q;
     const int nc = n_chunks(L);
-    // prefix of the chunks before this one
+    // prefix of the chunks before this one (c < kPThreads: one total per thread)
     u64 n0 = 0, s0 = 0;
-    for (int k = 0; k < c; ++k) {
-        n0 += ps->tot_n[k];
-        s0 += ps->tot_s[k];
+    {
+        u64 an = 0, as = 0;
+        for (int k = tid; k < c; k += blockDim.x) {
+            an += ps->tot_n[k];
+            as += ps->tot_s[k];
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            an += __shfl_xor_sync(0xFFFFFFFFu, an, o);
+            as += __shfl_xor_sync(0xFFFFFFFFu, as, o);
+        }
+        if ((tid & 31) == 0) {
+            sm.pn[tid >> 5] = an;
+            sm.ps[tid >> 5] = as;
+        }
+        __syncthreads();
+        for (int w = 0; w < kPThreads / 32; ++w) {
+            n0 += sm.pn[w];
+            s0 += sm.ps[w];
+        }
+        __syncthreads();
     }
     for (int i = tid; i < kChunk; i += blockDim.x) {
         const u32 v = c * kChunk + i;
