@@ -60,7 +60,7 @@ def build(force=False):
         return _SO
     tmp = _SO + f".tmp{os.getpid()}"
     subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared",
-                           "-o", tmp, _SRC])
+                           "-o", tmp, _SRC, "-lm"])
     os.replace(tmp, _SO)
     return _SO
 
@@ -96,6 +96,9 @@ def lib():
             L.oracle_filter_points.restype = ctypes.c_int
             L.oracle_stats.argtypes = [vp, i64, ctypes.c_int, vp, vp, vp, vp, vp, vp]
             L.oracle_stats.restype = ctypes.c_int
+            L.oracle_render.argtypes = [vp, i64, i64, i64, ctypes.c_int, ctypes.POINTER(_Params), ctypes.c_int,
+                                        vp, vp, vp]
+            L.oracle_render.restype = ctypes.c_int
             _lib = L
     return _lib
 
@@ -333,6 +336,36 @@ def filter_points(vol, filter_id, radius, pts, params):
     if rc != 0:
         raise ValueError("oracle_filter_points rejected its arguments")
     return vals
+
+
+def render_extent(shape, view):
+    """(H, W) of the image rendered along view 0..5 (+x, -x, +y, -y, +z, -z)
+    from a volume of numpy shape (nz, ny, nx)."""
+    nz, ny, nx = shape
+    return {0: (nz, ny), 1: (nz, ny), 2: (nz, nx), 3: (nz, nx), 4: (ny, nx), 5: (ny, nx)}[view]
+
+
+def render(vol, filter_id, radius, view, params=None, cfg=None, st=None):
+    """Ray-cast the volume along `view` with the filter deciding at each
+    candidate surface point (the paper's use of its filter; readings in the C
+    source): returns (image uint8, depth int32, value uint32), each (H, W)."""
+    vol = np.ascontiguousarray(vol)
+    nx, ny, nz = _dims(vol)
+    if params is None:
+        params = derive_params(st or stats(vol), radius, cfg)
+    else:
+        params = dict(params, radius=radius)
+    H, W = render_extent(vol.shape, view)
+    image = np.zeros((H, W), np.uint8)
+    depth = np.zeros((H, W), np.int32)
+    value = np.zeros((H, W), np.uint32)
+    p, keep = _cparams(filter_id, params)
+    rc = lib().oracle_render(vol.ctypes.data, nx, ny, nz, _dtype_code(vol), ctypes.byref(p), int(view),
+                             image.ctypes.data, depth.ctypes.data, value.ctypes.data)
+    del keep
+    if rc != 0:
+        raise ValueError("oracle_render rejected its arguments")
+    return image, depth, value
 
 
 # --------------------------------------------------------------------------- Fig. 4

@@ -284,3 +284,124 @@ int oracle_stats(const void *vol, int64_t n, int dtype, uint64_t *hist,
     *maxv = hi;
     return 0;
 }
+
+/* ------------------------------------------------------------------ rendering
+ *
+ * The paper's use of its filter ("Introduction", "3D Spatial Noise Filters"):
+ * a ray caster marches each pixel's ray through the volume; the first sample
+ * at or above the threshold is a candidate surface point, where the filter
+ * decides between structure and noise; a candidate the filter keeps (output
+ * not 0) ends the ray and is shaded with a normal from a 3D Sobel operator and
+ * Phong illumination; a rejected candidate is noise and the ray goes on.
+ *
+ * Readings (the paper fixes no camera, sampling or shading constants):
+ *  - orthographic rays along one of the six axis directions (view 0..5 =
+ *    +x, -x, +y, -y, +z, -z), one ray per voxel column, samples at the voxel
+ *    centres, no interpolation;
+ *  - image axes (u, w): views +-x -> (y, z), +-y -> (x, z), +-z -> (x, y);
+ *    pixel index w * W + u;
+ *  - Sobel: g_x = sum over the 3x3x3 neighbourhood (clamp-to-edge) of
+ *    i * b(j) * b(k) * P(x+i, y+j, z+k) with b(-1) = b(1) = 1, b(0) = 2;
+ *    g_y and g_z likewise;
+ *  - headlight Phong: c = (g . d) / |g| with d the ray direction (c = 1 when
+ *    g = 0); I = (0.1 + 0.7 max(c, 0)) + 0.2 s^16 with s = 2 c^2 - 1 when
+ *    c > 0 and s > 0, else 0; pixel = min(255, floor(255 I + 1/2)); 0 where
+ *    the ray finds no surface;
+ *  - shading in IEEE double, the operations in the written order, no fused
+ *    multiply-add (built with -ffp-contract=off).
+ */
+#include <math.h>
+
+static int render_extent(int view, int64_t nx, int64_t ny, int64_t nz, int64_t *W, int64_t *H, int64_t *len)
+{
+    switch (view) {
+    case 0: case 1: *W = ny; *H = nz; *len = nx; return 0;
+    case 2: case 3: *W = nx; *H = nz; *len = ny; return 0;
+    case 4: case 5: *W = nx; *H = ny; *len = nz; return 0;
+    default: return -1;
+    }
+}
+
+/* the voxel of ray (u, w) at step k */
+static void render_voxel(int view, const vol_view *v, int64_t u, int64_t w, int64_t k,
+                         int64_t *x, int64_t *y, int64_t *z)
+{
+    switch (view) {
+    case 0: *x = k; *y = u; *z = w; break;
+    case 1: *x = v->nx - 1 - k; *y = u; *z = w; break;
+    case 2: *x = u; *y = k; *z = w; break;
+    case 3: *x = u; *y = v->ny - 1 - k; *z = w; break;
+    case 4: *x = u; *y = w; *z = k; break;
+    default: *x = u; *y = w; *z = v->nz - 1 - k; break;
+    }
+}
+
+static uint8_t shade(const vol_view *v, int view, int64_t x, int64_t y, int64_t z)
+{
+    static const int64_t b[3] = {1, 2, 1};
+    int64_t gx = 0, gy = 0, gz = 0;
+    for (int k = -1; k <= 1; ++k)
+        for (int j = -1; j <= 1; ++j)
+            for (int i = -1; i <= 1; ++i) {
+                const int64_t P = sample(v, x + i, y + j, z + k);
+                gx += i * b[j + 1] * b[k + 1] * P;
+                gy += j * b[i + 1] * b[k + 1] * P;
+                gz += k * b[i + 1] * b[j + 1] * P;
+            }
+    const int64_t ga[3] = {gx, gy, gz};
+    const int64_t along = ga[view / 2] * ((view & 1) ? -1 : 1);   /* g . d */
+    const int64_t n2 = gx * gx + gy * gy + gz * gz;
+    const double c = n2 > 0 ? (double)along / sqrt((double)n2) : 1.0;
+    const double diff = c > 0.0 ? c : 0.0;
+    double spec = 0.0;
+    if (c > 0.0) {
+        double s = 2.0 * (c * c) - 1.0;
+        if (s > 0.0) {
+            s = s * s;
+            s = s * s;
+            s = s * s;
+            s = s * s;
+            spec = s;
+        }
+    }
+    const double I = (0.1 + 0.7 * diff) + 0.2 * spec;
+    const double q = floor(255.0 * I + 0.5);
+    return q >= 255.0 ? (uint8_t)255 : (uint8_t)q;
+}
+
+/* Render the volume along `view` with the filter of `p` deciding at each
+ * candidate; image (W*H bytes), depth (W*H: step of the hit along the ray, or
+ * -1) and value (W*H: the filter's output at the hit, or 0). */
+int oracle_render(const void *vol, int64_t nx, int64_t ny, int64_t nz, int dtype, const oracle_params *p, int view,
+                  uint8_t *image, int32_t *depth, uint32_t *value)
+{
+    if (!vol || !p || !image || !depth || !value || nx < 1 || ny < 1 || nz < 1 || (dtype != 0 && dtype != 1))
+        return -1;
+    if (p->filter_id < 0 || p->filter_id > 4 || p->radius < 0)
+        return -1;
+    int64_t W, H, len;
+    if (render_extent(view, nx, ny, nz, &W, &H, &len) != 0)
+        return -1;
+    vol_view v = {vol, nx, ny, nz, dtype};
+    for (int64_t w = 0; w < H; ++w)
+        for (int64_t u = 0; u < W; ++u) {
+            const int64_t o = w * W + u;
+            image[o] = 0;
+            depth[o] = -1;
+            value[o] = 0;
+            for (int64_t k = 0; k < len; ++k) {
+                int64_t x, y, z;
+                render_voxel(view, &v, u, w, k, &x, &y, &z);
+                if (sample(&v, x, y, z) < p->threshold)
+                    continue;   /* below the threshold: not a candidate */
+                const uint32_t f = filter_at(&v, p, x, y, z);
+                if (f == 0)
+                    continue;   /* the filter calls it noise */
+                image[o] = shade(&v, view, x, y, z);
+                depth[o] = (int32_t)k;
+                value[o] = f;
+                break;
+            }
+        }
+    return 0;
+}
