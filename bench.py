@@ -273,7 +273,7 @@ def main():
     ap.add_argument("--impl", default="lnf", choices=["lnf", "reference"])
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--mode", default="plain", choices=["plain", "batched", "served"],
+    ap.add_argument("--mode", default="plain", choices=["plain", "batched", "served", "render"],
                     help="plain: the 512^3 five-filter step (default); batched / served: the delivery forms")
     ap.add_argument("--duration", type=float, default=10.0, help="served: seconds of Poisson arrivals")
     ap.add_argument("--rate", type=float, default=200.0, help="served: requests per second")
@@ -303,6 +303,8 @@ def main():
         return run_batched(args)
     if args.mode == "served":
         return run_served(args)
+    if args.mode == "render":
+        return run_render(args)
 
     import numpy as np
     import torch
@@ -606,6 +608,62 @@ def run_served(args):
                        "note": "all requests queued at once (capacity)"},
             "serial_plain": {"seconds": serial_s, "gvox_s": vox / serial_s / 1e9},
             "offered_gvox_s": vox / args.duration / 1e9}
+    print(json.dumps(line))
+    ctx.close()
+
+
+def run_render(args):
+    """The paper's use of its filter: ray-cast the 512^3 uint16 phantom along +z
+    (512 x 512 rays) with each filter at r = 2 deciding at the candidate surface
+    points.  Per filter: ms per frame for the whole lnf_render call (statistics,
+    parameters, rays) and for the ray kernel alone, with the oracle's renderer
+    timed on a bounded sample of the rays beside it."""
+    import numpy as np
+    import torch
+    import oracle
+    import phantoms
+    import paper_1807_03119_gb300 as lnf
+    from paper_1807_03119_gb300 import builder
+    builder.build()
+    lnf.load()
+    vol = phantoms.P2()
+    t = torch.from_numpy(vol).cuda()
+    ctx = lnf.Context()
+    rows = 8   # oracle sample: the rays of the first `rows` image rows
+    st = oracle.stats(vol)
+    res = {}
+    for name in FILTER_NAMES:
+        f = lnf.FILTERS[name]
+        for _ in range(args.warmup):
+            ctx.render(t, f, RADIUS, 4, with_depth=False, with_value=False)
+        torch.cuda.synchronize()
+        ctx.profile(True)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.steps):
+            im, _, _ = ctx.render(t, f, RADIUS, 4, with_depth=False, with_value=False)
+        e1.record()
+        torch.cuda.synchronize()
+        kern, _ = ctx.profile_read()
+        ctx.profile(False)
+        ms = e0.elapsed_time(e1) / args.steps
+        rk = kern.get("render", (1, float("nan")))
+        hit = float((im > 0).float().mean())
+        prm = oracle.derive_params(st, RADIUS)
+        c0 = time.perf_counter()
+        oracle.render(np.ascontiguousarray(vol[:, :rows, :]), f, RADIUS, 4, params=prm)
+        cpu_ms = (time.perf_counter() - c0) * 1e3 * (vol.shape[1] / rows)
+        res[name] = {"ms_per_frame": ms, "ray_kernel_ms": rk[1] / rk[0], "rays_per_s": 512 * 512 / (ms / 1e3),
+                     "hit_fraction": hit, "oracle_ms_per_frame": cpu_ms}
+    line = {"metric": "render ms per frame: 512x512 rays along +z through 512^3 uint16, r=2",
+            "mode": "render", "value": sum(v["ms_per_frame"] for v in res.values()) / len(res), "unit": "ms",
+            "higher_is_better": False, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "dtype": "u16", "data": "synthetic",
+            "config": {"workload": "512x512x512 uint16 insect-like phantom, orthographic rays along +z",
+                       "radius": RADIUS, "oracle_sample": f"the rays of {rows} image rows, scaled to 512 rows, "
+                                                          "1 host thread"},
+            "filters": res}
     print(json.dumps(line))
     ctx.close()
 

@@ -183,6 +183,32 @@ lnf_status lnf_entropy(lnf_ctx *ctx, const void *vol, const int64_t dims[3], int
 lnf_status lnf_get_params(lnf_ctx *ctx, lnf_params *out, uint32_t *weights);
 
 /*
+ * Ray-cast the volume with a filter deciding at each candidate surface point:
+ * the paper's use of its filter (sections "Introduction" and "3D Spatial
+ * Noise Filters": the first sample at or above the threshold is a candidate;
+ * the filter keeps it as structure, ending the ray, or rejects it as noise,
+ * and the ray goes on; the surface is shaded with a 3D Sobel normal and Phong
+ * illumination).  Orthographic rays along one of the six axis directions,
+ * one per voxel column, samples at voxel centres; headlight Phong in IEEE
+ * double: c = (g . d)/|g| (1 when g = 0), I = (0.1 + 0.7 max(c,0)) + 0.2 s^16
+ * with s = 2c^2 - 1 when c > 0 and s > 0, pixel = min(255, floor(255 I + 1/2)).
+ *   filter_id, radius  as lnf_filter_volume; the parameters (T, sigma band,
+ *              T_d, entropy weights) are derived from the whole volume first
+ *   in         device buffer of nx*ny*nz voxels (x-fastest)
+ *   view       0..5 = rays along +x, -x, +y, -y, +z, -z; image axes (u, w) =
+ *              (y, z) for +-x, (x, z) for +-y, (x, y) for +-z; pixel w*W + u
+ *   image      device, W*H bytes: the shaded surface, 0 where no surface
+ *   depth      device, W*H int32: step of the hit along the ray, -1 for none
+ *              (NULL: not written)
+ *   value      device, W*H uint32: the filter's output at the hit, 0 for none
+ *              (NULL: not written)
+ * Enqueued on the context's stream.  Returns LNF_EINVAL for a bad filter,
+ * radius, view, dtype, dims or a NULL image.
+ */
+lnf_status lnf_render(lnf_ctx *ctx, int filter_id, int radius, const void *in, const int64_t dims[3], int dtype,
+                      int view, uint8_t *image, int32_t *depth, uint32_t *value);
+
+/*
  * Image entropy of a volume, like lnf_entropy, for callers that must not
  * allocate device memory: no cudaMalloc, cudaFree or allocating library call
  * is made, and no lnf_ctx is needed (creating one allocates).  Typical users:

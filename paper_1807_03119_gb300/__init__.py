@@ -138,6 +138,8 @@ _SIGS = {
                                              ctypes.POINTER(ctypes.c_double)]),
     "lnf_filter_roi": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p, _i64p,
                                       ctypes.c_int, _i64p, _i64p, ctypes.c_void_p]),
+    "lnf_render": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p, _i64p, ctypes.c_int,
+                                  ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "lnf_entropy": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, _i64p, ctypes.c_int,
                                    ctypes.POINTER(ctypes.c_double)]),
     "lnf_get_params": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Params), ctypes.c_void_p]),
@@ -329,6 +331,25 @@ class Context:
                                             _dtype_of(vol), (ctypes.c_int64 * 3)(*origin),
                                             (ctypes.c_int64 * 3)(*size), out.data_ptr()))
         return out
+
+    def render(self, vol, filter_id, radius, view=4, with_depth=True, with_value=True):
+        """Ray-cast the volume along `view` (0..5 = +x, -x, +y, -y, +z, -z) with
+        the filter deciding at each candidate surface point; returns (image
+        uint8, depth int32 or None, value int32 or None), each of shape (H, W)."""
+        import torch
+        _check_dev(vol)
+        nz, ny, nx = vol.shape
+        if view not in range(6):
+            raise ValueError("view must be 0..5")
+        H, W = {0: (nz, ny), 1: (nz, ny), 2: (nz, nx), 3: (nz, nx), 4: (ny, nx), 5: (ny, nx)}[view]
+        image = torch.empty((H, W), dtype=torch.uint8, device=vol.device)
+        depth = torch.empty((H, W), dtype=torch.int32, device=vol.device) if with_depth else None
+        value = torch.empty((H, W), dtype=torch.int32, device=vol.device) if with_value else None
+        self._sync_stream()
+        self._check(self.lib.lnf_render(self.h, filter_id, radius, vol.data_ptr(), _dims_of(vol), _dtype_of(vol),
+                                        view, image.data_ptr(), depth.data_ptr() if depth is not None else None,
+                                        value.data_ptr() if value is not None else None))
+        return image, depth, value
 
     def entropy(self, vol):
         _check_dev(vol)

@@ -734,6 +734,29 @@ extern "C" lnf_status lnf_filter_multi_host(lnf_ctx *ctx, int radius, const void
     return LNF_OK;
 }
 
+extern "C" lnf_status lnf_render(lnf_ctx *ctx, int filter_id, int radius, const void *in, const int64_t dims[3],
+                                 int dtype, int view, uint8_t *image, int32_t *depth, uint32_t *value)
+{
+    if (!ctx)
+        return LNF_EINVAL;
+    lnf_status s;
+    if ((s = check_filter(ctx, filter_id, radius)) != LNF_OK)
+        return s;
+    if ((s = lnf_check_volume(ctx, in, dims, dtype)) != LNF_OK)
+        return s;
+    if (view < 0 || view > 5)
+        return lnf_fail(ctx, LNF_EINVAL, "view %d not in 0..5", view);
+    if (!image)
+        return lnf_fail(ctx, LNF_EINVAL, "null image");
+    if ((s = lnf_analyze(ctx, in, dims, dtype, ctx->vs, ctx->stream)) != LNF_OK)
+        return s;
+    const int rec = lnf_prof_begin(ctx, ctx->stream);
+    CK(lnf_launch_render(in, dims, dims[0], dtype, view, filter_id, radius, ctx->cfg.cluster_offset, ctx->vs.prm,
+                         ctx->vs.lut, image, depth, reinterpret_cast<u32 *>(value), ctx->stream));
+    lnf_prof_end(ctx, rec, "render", ctx->stream, 1);
+    return LNF_OK;
+}
+
 extern "C" lnf_status lnf_entropy(lnf_ctx *ctx, const void *vol, const int64_t dims[3], int dtype, double *H)
 {
     if (!ctx)

@@ -15,8 +15,11 @@
 // input type, the noise gate, and a fused per-CTA output histogram (for the
 // image entropy of the result, Fig. 4) flushed once per job.
 #include "lnf_internal.cuh"
+#include "filter_eval.cuh"
 
 namespace {
+
+using namespace lnfeval;
 
 constexpr int kThreads = 256;
 constexpr int kTX = 32;
@@ -49,7 +52,6 @@ __host__ __device__ inline int job_halo(int filter, int r, int d) { return filte
 
 __device__ __forceinline__ int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
 
-__device__ __forceinline__ u32 rnd_div(u64 a, u64 b) { return (u32)((2 * a + b) / (2 * b)); }
 
 // ------------------------------------------------------------------ histogram
 
@@ -121,106 +123,6 @@ struct Ring {
     }
 };
 
-struct StepParams {
-    u32 T;
-    u32 delta;
-    long long td;
-    long long te;
-    int r, d;
-    const u32 *lut;
-};
-
-template <typename T>
-__device__ __forceinline__ u32 eval_filter(int filter, const Ring<T> &R, const StepParams &p)
-{
-    const int r = p.r;
-    const int M = 2 * r + 1;
-    const u32 P0 = R.at(0, 0, 0);
-    switch (filter) {
-    case 0: {   // mean, Eq. 4
-        u64 B = 0;
-        for (int k = -r; k <= r; ++k)
-            for (int j = -r; j <= r; ++j)
-                for (int i = -r; i <= r; ++i)
-                    B += R.at(i, j, k);
-        const u64 n = (u64)M * M * M;
-        if (P0 < p.T || B < n * p.T)
-            return 0;
-        return rnd_div(B, n);
-    }
-    case 1: {   // sigma, Eq. 5: |P_i - P0| <= delta over the cube
-        u64 s = 0;
-        u32 n = 0;
-        const u32 dl = min(p.delta, 65535u);      // every value lies within 65535
-        const u32 lo = P0 > dl ? P0 - dl : 0u;
-        const u32 width = (P0 - lo) + dl;         // band [lo, lo + width]
-        for (int k = -r; k <= r; ++k)
-            for (int j = -r; j <= r; ++j)
-                for (int i = -r; i <= r; ++i) {
-                    const u32 v = R.at(i, j, k);
-                    if (v - lo <= width) {
-                        s += v;
-                        ++n;
-                    }
-                }
-        if (P0 < p.T || s < (u64)n * p.T)
-            return 0;
-        return rnd_div(s, n);
-    }
-    case 2: {   // entropy, Eq. 7
-        u64 E = 0;
-        for (int k = -r; k <= r; ++k)
-            for (int j = -r; j <= r; ++j)
-                for (int i = -r; i <= r; ++i)
-                    E += __ldg(p.lut + R.at(i, j, k));
-        if (P0 < p.T)
-            return 0;
-        return (long long)E > p.te ? P0 : 0u;
-    }
-    case 3: {   // Okada, Eq. 6: centre + axis cross of arm r, |P0 - P_i| < T_d
-        u64 s = 0;
-        u32 n = 0;
-        if (p.td > 0) {
-            s = P0;
-            n = 1;
-            for (int t = 1; t <= r; ++t) {
-                const u32 v[6] = {R.at(t, 0, 0), R.at(-t, 0, 0), R.at(0, t, 0),
-                                  R.at(0, -t, 0), R.at(0, 0, t), R.at(0, 0, -t)};
-#pragma unroll
-                for (int q = 0; q < 6; ++q) {
-                    const long long df = (long long)P0 - (long long)v[q];
-                    if ((df < 0 ? -df : df) < p.td) {
-                        s += v[q];
-                        ++n;
-                    }
-                }
-            }
-        }
-        if (n == 0 || P0 < p.T || s < (u64)n * p.T)
-            return 0;
-        return rnd_div(s, n);
-    }
-    default: {  // the paper's filter, Eq. 2-3: nine average clusters
-        u64 U = 0;
-        const int d = p.d;
-        for (int c = 0; c < 9; ++c) {
-            int cx = 0, cy = 0, cz = 0;
-            if (c > 0) {
-                cx = (c - 1) & 1 ? d : -d;
-                cy = (c - 1) & 2 ? d : -d;
-                cz = (c - 1) & 4 ? d : -d;
-            }
-            for (int t = -r; t <= r; ++t)
-                U += R.at(cx + t, cy, cz) + R.at(cx, cy + t, cz) + R.at(cx, cy, cz + t);
-        }
-        const u64 den = 27ull * M;
-        if (P0 < p.T || U < den * p.T)
-            return 0;
-        return rnd_div(U, den);
-    }
-    }
-}
-
 // ------------------------------------------------------------------ plane loading
 
 template <typename T>
@@ -291,22 +193,7 @@ __device__ void process_item(const FilterJob &J, const CUtensorMap *tmap, int it
 
     // parameters of this job
     const DevParams &P = *J.prm;
-    StepParams sp;
-    sp.T = P.T;
-    sp.delta = P.delta;
-    sp.td = P.td;
-    sp.r = J.radius;
-    sp.d = J.offset;
-    sp.lut = J.lut;
-    {
-        const u64 M = 2 * J.radius + 1;
-        if (P.te_cfg == -2) {
-            const unsigned __int128 num = (unsigned __int128)(M * M * M) * P.hw_sum;
-            sp.te = (long long)(num / P.N);
-        } else {
-            sp.te = P.te_cfg;
-        }
-    }
+    const StepParams sp = make_step_params(P, J.radius, J.offset, J.lut);
     // stage loader for plain loads
     auto load_plane_plain = [&](int p, T *dst) {
         const int z = clampi(z0 - h + p, 0, J.nz - 1);
@@ -377,7 +264,7 @@ __device__ void process_item(const FilterJob &J, const CUtensorMap *tmap, int it
         // compute output plane z = z0 + s from planes s .. s + 2h
         R.slot0 = (s + h) % g.NP;
         if (active) {
-            const u32 f = eval_filter<T>(J.filter, R, sp);
+            const u32 f = eval_filter(J.filter, R, sp);
             const size_t o = ((size_t)(lz0 + s) * J.by + (ly0 + tr)) * J.bx + (lx0 + tl);
             vout[o] = (T)f;
             if (gh)

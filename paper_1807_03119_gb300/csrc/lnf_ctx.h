@@ -118,6 +118,10 @@ lnf_status lnf_fast2_dispatch(lnf_ctx *ctx, const FilterJob &job, const CUtensor
                               int *handled, u32 *counter = nullptr);
 // fast2_box.cu: the mean / entropy-filter job through its box kernel
 lnf_status lnf_fast2_box(lnf_ctx *ctx, const FilterJob &job, cudaStream_t stream, u32 *counter, int *handled);
+// render.cu: one ray per pixel (see lnf_render)
+cudaError_t lnf_launch_render(const void *vol, const int64_t dims[3], int64_t pitch, int dtype, int view,
+                              int filter, int radius, int offset, const DevParams *prm, const u32 *lut,
+                              unsigned char *image, int *depth, u32 *value, cudaStream_t st);
 // batch.cu
 void lnf_batch_cache_clear(lnf_ctx *ctx);
 // serve.cu
