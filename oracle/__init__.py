@@ -38,6 +38,9 @@ __all__ = [
 ]
 
 MEAN, SIGMA, ENTROPY, OKADA, OURS = 0, 1, 2, 3, 4
+# cluster-layout variants of the paper's filter: axis-cross clusters (the
+# commented-out S_0 at r = 1) and cube clusters
+OURS_CROSS7, OURS_CUBE = 5, 6
 FILTER_NAMES = {MEAN: "mean", SIGMA: "sigma", ENTROPY: "entropy", OKADA: "okada", OURS: "ours"}
 
 # fixed point of the entropy-filter criterion (a stated reading: the paper gives

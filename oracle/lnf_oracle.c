@@ -17,7 +17,8 @@
  *     otherwise the output is 0 (the "0, otherwise" branch of Eq. 6 / Eq. 7).
  *
  * Filter ids follow the order of the paper's Fig. 5: 0 mean, 1 sigma,
- * 2 entropy, 3 Okada, 4 the paper's own filter ("ours").
+ * 2 entropy, 3 Okada, 4 the paper's own filter ("ours"); 5 and 6 are two
+ * cluster-layout variants of it (see filter_ours_variant).
  */
 #include <stdint.h>
 #include <stddef.h>
@@ -200,6 +201,47 @@ static uint32_t filter_entropy(const vol_view *v, const oracle_params *p, int64_
     return 0;
 }
 
+/* Cluster-layout variants of the paper's filter ("Our Method": the source
+ * carries a commented-out S_0 that averages the centre and its six direct
+ * neighbours, and the conclusion proposes analysing other cluster layouts).
+ * The nine cluster centres are those of filter_ours; each cluster is
+ *   id 5: the centre and the 6r voxels of its axis cross of arm r, averaged
+ *         (r = 1 is the commented-out form: (1/7)(P0 + six neighbours));
+ *   id 6: the M^3 cube around the centre, averaged;
+ * and the voxel is replaced by the mean of the nine cluster averages, gated as
+ * filter_ours. */
+static uint32_t filter_ours_variant(const vol_view *v, const oracle_params *p, int64_t x, int64_t y, int64_t z)
+{
+    const int r = p->radius;
+    const int64_t d = p->offset;
+    const uint64_t M = 2 * (uint64_t)r + 1;
+    const uint64_t per = p->filter_id == 5 ? 6 * (uint64_t)r + 1 : M * M * M;   /* voxels per cluster */
+    uint64_t U = 0;
+    for (int c = 0; c < 9; ++c) {
+        int64_t cx = x, cy = y, cz = z;
+        if (c > 0) {
+            cx += ((c - 1) & 1) ? d : -d;
+            cy += ((c - 1) & 2) ? d : -d;
+            cz += ((c - 1) & 4) ? d : -d;
+        }
+        if (p->filter_id == 5) {
+            U += sample(v, cx, cy, cz);
+            for (int t = 1; t <= r; ++t)
+                U += sample(v, cx - t, cy, cz) + sample(v, cx + t, cy, cz) + sample(v, cx, cy - t, cz) +
+                     sample(v, cx, cy + t, cz) + sample(v, cx, cy, cz - t) + sample(v, cx, cy, cz + t);
+        } else {
+            for (int k = -r; k <= r; ++k)
+                for (int j = -r; j <= r; ++j)
+                    for (int i = -r; i <= r; ++i)
+                        U += sample(v, cx + i, cy + j, cz + k);
+        }
+    }
+    const uint64_t den = 9 * per;
+    if (sample(v, x, y, z) < p->threshold || U < den * p->threshold)
+        return 0;
+    return round_div(U, den);
+}
+
 static uint32_t filter_at(const vol_view *v, const oracle_params *p, int64_t x, int64_t y, int64_t z)
 {
     switch (p->filter_id) {
@@ -208,6 +250,8 @@ static uint32_t filter_at(const vol_view *v, const oracle_params *p, int64_t x, 
     case 2: return filter_entropy(v, p, x, y, z);
     case 3: return filter_okada(v, p, x, y, z);
     case 4: return filter_ours(v, p, x, y, z);
+    case 5:
+    case 6: return filter_ours_variant(v, p, x, y, z);
     default: return 0;
     }
 }
@@ -223,7 +267,7 @@ int oracle_filter_box(const void *vol, int64_t nx, int64_t ny, int64_t nz, int d
         return -1;
     if (x0 < 0 || y0 < 0 || z0 < 0 || x1 > nx || y1 > ny || z1 > nz || x1 < x0 || y1 < y0 || z1 < z0)
         return -1;
-    if (p->filter_id < 0 || p->filter_id > 4 || p->radius < 0)
+    if (p->filter_id < 0 || p->filter_id > 6 || p->radius < 0)
         return -1;
     vol_view v = {vol, nx, ny, nz, dtype};
     int64_t bx = x1 - x0, by = y1 - y0;
@@ -377,7 +421,7 @@ int oracle_render(const void *vol, int64_t nx, int64_t ny, int64_t nz, int dtype
 {
     if (!vol || !p || !image || !depth || !value || nx < 1 || ny < 1 || nz < 1 || (dtype != 0 && dtype != 1))
         return -1;
-    if (p->filter_id < 0 || p->filter_id > 4 || p->radius < 0)
+    if (p->filter_id < 0 || p->filter_id > 6 || p->radius < 0)
         return -1;
     int64_t W, H, len;
     if (render_extent(view, nx, ny, nz, &W, &H, &len) != 0)

@@ -19,6 +19,7 @@ import oracle
 import phantoms
 
 MEAN, SIGMA, ENTROPY, OKADA, OURS = 0, 1, 2, 3, 4
+OURS_CROSS7, OURS_CUBE = 5, 6
 
 
 # --------------------------------------------------------------------------------------
@@ -64,6 +65,27 @@ class Brute:
             return self.rnd(A)
         return 0
 
+    def ours_layout(self, layout, r, d, T, x, y, z):
+        """The paper's combination (the mean of the nine cluster averages at the
+        centre and the corners (+-d, +-d, +-d)) over other cluster shapes:
+        'cross' = the centre and its axis cross of arm r, 'cube' = the M^3 cube."""
+        centres = [(x, y, z)] + [(x + sx * d, y + sy * d, z + sz * d)
+                                 for sx in (-1, 1) for sy in (-1, 1) for sz in (-1, 1)]
+        avgs = []
+        for cx, cy, cz in centres:
+            if layout == "cross":
+                vals = [self.P(cx, cy, cz)]
+                for t in range(1, r + 1):
+                    vals += [self.P(cx + t, cy, cz), self.P(cx - t, cy, cz), self.P(cx, cy + t, cz),
+                             self.P(cx, cy - t, cz), self.P(cx, cy, cz + t), self.P(cx, cy, cz - t)]
+            else:
+                vals = self.cube(r, cx, cy, cz)
+            avgs.append(Fraction(sum(vals), len(vals)))
+        A = sum(avgs, Fraction(0)) / 9
+        if self.P(x, y, z) >= T and A >= T:
+            return self.rnd(A)
+        return 0
+
     def cube(self, r, x, y, z):
         return [self.P(x + i, y + j, z + k) for k in range(-r, r + 1)
                 for j in range(-r, r + 1) for i in range(-r, r + 1)]
@@ -94,6 +116,40 @@ class Brute:
             return 0
         A = Fraction(sum(sel), len(sel))
         return self.rnd(A) if (P0 >= T and A >= T) else 0
+
+
+@pytest.mark.parametrize("dims,dt,seed", [((4, 5, 6), "u8", 51), ((6, 4, 5), "u16", 52), ((5, 6, 4), "u16", 53)])
+@pytest.mark.parametrize("mode", ["none", "otsu", "fixed"])
+def test_brute_force_cluster_variants(dims, dt, seed, mode):
+    vol = phantoms.random_volume(dims, seed, dt)
+    T, cfg = _fixed_T(vol, mode, seed)
+    b = Brute(vol)
+    st = oracle.stats(vol)
+    nx, ny, nz = dims
+    for r in (0, 1, 2):
+        prm = oracle.derive_params(st, r, cfg)
+        for d in (1, 0, 2):
+            for f, layout in ((OURS_CROSS7, "cross"), (OURS_CUBE, "cube")):
+                got = oracle.filter_volume(vol, f, r, params=dict(prm, offset=d))
+                for z, y, x in itertools.product(range(nz), range(ny), range(nx)):
+                    assert got[z, y, x] == b.ours_layout(layout, r, d, T, x, y, z), (layout, r, d, x, y, z)
+
+
+@pytest.mark.parametrize("r", [1, 2])
+def test_cluster_variants_spike(r):
+    """A lone spike s on a background b: only the centre cluster's axis cross
+    holds it (each corner centre is off every axis through it), while every
+    cube of side M >= 3 around a corner at distance 1 holds it."""
+    n, c, b, s = 11, 5, 100, 4000
+    vol = np.full((n, n, n), b, np.uint16)
+    vol[c, c, c] = s
+    prm = dict(oracle.derive_params(oracle.stats(vol), r, oracle.Config(threshold_mode="none")), offset=1)
+    M = 2 * r + 1
+    cross = oracle.filter_volume(vol, OURS_CROSS7, r, params=prm)
+    cube = oracle.filter_volume(vol, OURS_CUBE, r, params=prm)
+    assert cross[c, c, c] == math.floor(b + Fraction(s - b, 9 * (6 * r + 1)) + Fraction(1, 2))
+    assert cube[c, c, c] == math.floor(b + Fraction(s - b, M ** 3) + Fraction(1, 2))
+    assert (oracle.filter_volume(vol, OURS_CROSS7, r, params=prm)[0] == b).all()
 
 
 def _fixed_T(vol, mode, seed):
@@ -329,7 +385,7 @@ def test_constant_volume(dt, c):
     for r in (0, 1, 2):
         prm = oracle.derive_params(st, r)
         assert prm["T"] == c
-        for f in (MEAN, SIGMA, OKADA, OURS):
+        for f in (MEAN, SIGMA, OKADA, OURS, OURS_CROSS7, OURS_CUBE):
             assert (oracle.filter_volume(vol, f, r, params=prm) == c).all(), (f, r)
         # all weights are 0, so the criterion is 0 and 0 > T_e = 0 fails
         assert not oracle.filter_volume(vol, ENTROPY, r, params=prm).any()
@@ -468,12 +524,12 @@ def test_symmetry_48(dt):
     vol = phantoms.random_volume((6, 6, 6), 31, dt, p_extreme=0.2)
     st = oracle.stats(vol)
     outs = {}
-    for f in range(5):
+    for f in range(7):
         prm = oracle.derive_params(st, 1)
         outs[f] = (prm, oracle.filter_volume(vol, f, 1, params=prm))
     for perm, flips in _transforms():
         tv = _apply(vol, perm, flips)
-        for f in range(5):
+        for f in range(7):
             prm, ref = outs[f]
             got = oracle.filter_volume(tv, f, 1, params=prm)
             assert (got == _apply(ref, perm, flips)).all(), (f, perm, flips)
