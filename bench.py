@@ -273,7 +273,7 @@ def main():
     ap.add_argument("--impl", default="lnf", choices=["lnf", "reference"])
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--mode", default="plain", choices=["plain", "batched", "served", "render"],
+    ap.add_argument("--mode", default="plain", choices=["plain", "batched", "served", "render", "variants"],
                     help="plain: the 512^3 five-filter step (default); batched / served: the delivery forms")
     ap.add_argument("--duration", type=float, default=10.0, help="served: seconds of Poisson arrivals")
     ap.add_argument("--rate", type=float, default=200.0, help="served: requests per second")
@@ -305,6 +305,8 @@ def main():
         return run_served(args)
     if args.mode == "render":
         return run_render(args)
+    if args.mode == "variants":
+        return run_variants(args)
 
     import numpy as np
     import torch
@@ -664,6 +666,45 @@ def run_render(args):
                        "radius": RADIUS, "oracle_sample": f"the rays of {rows} image rows, scaled to 512 rows, "
                                                           "1 host thread"},
             "filters": res}
+    print(json.dumps(line))
+    ctx.close()
+
+
+def run_variants(args):
+    """Cluster-layout variants of the paper's filter (axis-cross clusters, cube
+    clusters) beside the paper's own layout, on the 512^3 uint16 phantom at
+    r = 2: device ms per launch of each filter kernel (the variants run on the
+    generic kernel, the paper's filter on its specialised one)."""
+    import torch
+    import phantoms
+    import paper_1807_03119_gb300 as lnf
+    from paper_1807_03119_gb300 import builder
+    builder.build()
+    lnf.load()
+    vol = phantoms.P2()
+    t = torch.from_numpy(vol).cuda()
+    out = torch.empty_like(t)
+    ctx = lnf.Context()
+    res = {}
+    for name in ("ours", "ours_cross", "ours_cube"):
+        f = lnf.FILTERS[name]
+        for _ in range(args.warmup):
+            ctx.filter_volume(t, f, RADIUS, out=out)
+        torch.cuda.synchronize()
+        ctx.profile(True)
+        for _ in range(args.steps):
+            ctx.filter_volume(t, f, RADIUS, out=out)
+        torch.cuda.synchronize()
+        kern, _ = ctx.profile_read()
+        ctx.profile(False)
+        n, tot = kern["filter:" + name]
+        ms = tot / n
+        res[name] = {"ms_per_launch": ms, "gvox_s": N_VOX / (ms / 1e3) / 1e9,
+                     "hbm_frac": N_VOX * ES * 2 / (ms / 1e3) / 1e9 / peaks()["hbm_gbs"]}
+    line = {"metric": "cluster-layout variants of the paper's filter, 512^3 uint16, r=2", "mode": "variants",
+            "value": res["ours_cube"]["gvox_s"], "unit": UNIT, "higher_is_better": True, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "dtype": "u16", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "radius": RADIUS}, "filters": res}
     print(json.dumps(line))
     ctx.close()
 

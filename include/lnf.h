@@ -69,7 +69,12 @@ typedef enum lnf_filter_id {
     LNF_SIGMA = 1,    /* Eq. 5: mean of cube voxels with |P_i - P0| <= k*sigma (global sigma) */
     LNF_ENTROPY = 2,  /* Eq. 7: P0 if the cube's criterion -sum p_i log2 p_i exceeds T_e, else 0 */
     LNF_OKADA = 3,    /* Eq. 6: mean of the centre and its axis-cross neighbours with |P0 - P_i| < T_d */
-    LNF_OURS = 4      /* Eq. 2-3: mean of the nine average clusters S_0..S_8 */
+    LNF_OURS = 4,     /* Eq. 2-3: mean of the nine average clusters S_0..S_8 */
+    /* Cluster-layout variants of the paper's filter ("Our Method" carries a
+       commented-out S_0; the conclusion proposes other layouts): the same nine
+       cluster centres and combination, each cluster being */
+    LNF_OURS_CROSS7 = 5,  /* its centre and axis cross of arm r, averaged (r = 1: (P0 + 6 neighbours) / 7) */
+    LNF_OURS_CUBE = 6     /* the M^3 cube around its centre, averaged */
 } lnf_filter_id;
 
 typedef enum lnf_threshold_mode {

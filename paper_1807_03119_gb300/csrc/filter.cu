@@ -48,7 +48,8 @@ __host__ __device__ inline Geo make_geo(int h, int esize)
     return g;
 }
 
-__host__ __device__ inline int job_halo(int filter, int r, int d) { return filter == 4 ? r + d : r; }
+// the paper's filter and its cluster-layout variants reach r past the cluster centres at offset d
+__host__ __device__ inline int job_halo(int filter, int r, int d) { return filter >= 4 ? r + d : r; }
 
 __device__ __forceinline__ int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
 

@@ -91,6 +91,34 @@ __device__ __forceinline__ u32 eval_filter(int filter, const S &R, const StepPar
             return 0;
         return rnd_div(s, n);
     }
+    case 5:     // cluster-layout variants of the paper's filter: the nine cluster
+    case 6: {   // centres of Eq. 2-3, each cluster its axis cross of arm r (5) or its M^3 cube (6)
+        u64 U = 0;
+        const int d = p.d;
+        for (int c = 0; c < 9; ++c) {
+            int cx = 0, cy = 0, cz = 0;
+            if (c > 0) {
+                cx = (c - 1) & 1 ? d : -d;
+                cy = (c - 1) & 2 ? d : -d;
+                cz = (c - 1) & 4 ? d : -d;
+            }
+            if (filter == 5) {
+                U += R.at(cx, cy, cz);
+                for (int t = 1; t <= r; ++t)
+                    U += R.at(cx - t, cy, cz) + R.at(cx + t, cy, cz) + R.at(cx, cy - t, cz) + R.at(cx, cy + t, cz) +
+                         R.at(cx, cy, cz - t) + R.at(cx, cy, cz + t);
+            } else {
+                for (int k = -r; k <= r; ++k)
+                    for (int j = -r; j <= r; ++j)
+                        for (int i = -r; i <= r; ++i)
+                            U += R.at(cx + i, cy + j, cz + k);
+            }
+        }
+        const u64 den = 9ull * (filter == 5 ? 6ull * r + 1 : (u64)M * M * M);
+        if (P0 < p.T || U < den * p.T)
+            return 0;
+        return rnd_div(U, den);
+    }
     default: {  // the paper's filter, Eq. 2-3: nine average clusters
         u64 U = 0;
         const int d = p.d;
