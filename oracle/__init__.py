@@ -41,6 +41,8 @@ MEAN, SIGMA, ENTROPY, OKADA, OURS = 0, 1, 2, 3, 4
 # cluster-layout variants of the paper's filter: axis-cross clusters (the
 # commented-out S_0 at r = 1) and cube clusters
 OURS_CROSS7, OURS_CUBE = 5, 6
+# the sigma filter with the local standard deviation of its cube (Lee's original form)
+SIGMA_LOCAL = 7
 FILTER_NAMES = {MEAN: "mean", SIGMA: "sigma", ENTROPY: "entropy", OKADA: "okada", OURS: "ours"}
 
 # fixed point of the entropy-filter criterion (a stated reading: the paper gives
@@ -78,6 +80,7 @@ class _Params(ctypes.Structure):
         ("okada_td", ctypes.c_int64),
         ("entropy_te", ctypes.c_int64),
         ("entropy_w", ctypes.POINTER(ctypes.c_uint32)),
+        ("sigma_k", ctypes.c_int32),
     ]
 
 
@@ -287,7 +290,7 @@ def derive_params(st, radius, cfg=None):
     w = entropy_weights(st.hist)
     te = entropy_te_default(st.hist, w, M ** 3) if cfg.entropy_te is None else int(cfg.entropy_te)
     return {"T": T, "delta": delta, "td": td, "w": w, "te": te, "offset": cfg.offset,
-            "radius": radius}
+            "radius": radius, "k": int(cfg.sigma_k)}
 
 
 def _cparams(filter_id, prm):
@@ -301,6 +304,7 @@ def _cparams(filter_id, prm):
     p.entropy_te = prm["te"]
     w = np.ascontiguousarray(prm["w"], dtype=np.uint32)
     p.entropy_w = w.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32))
+    p.sigma_k = int(prm.get("k", 2))
     return p, w
 
 

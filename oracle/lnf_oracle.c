@@ -18,7 +18,8 @@
  *
  * Filter ids follow the order of the paper's Fig. 5: 0 mean, 1 sigma,
  * 2 entropy, 3 Okada, 4 the paper's own filter ("ours"); 5 and 6 are two
- * cluster-layout variants of it (see filter_ours_variant).
+ * cluster-layout variants of it (see filter_ours_variant); 7 is the sigma
+ * filter with the local standard deviation (see filter_sigma_local).
  */
 #include <stdint.h>
 #include <stddef.h>
@@ -32,6 +33,7 @@ typedef struct oracle_params {
     int64_t okada_td;      /* T_d: |P0 - P_i| < T_d (Eq. 6) */
     int64_t entropy_te;    /* T_e (fixed point): keep P0 iff E > T_e (Eq. 7) */
     const uint32_t *entropy_w; /* w[v] = fixed-point -p_v log2 p_v, one entry per grey level */
+    int32_t sigma_k;       /* k of the local sigma filter: |P_i - P0| <= k sigma_local */
 } oracle_params;
 
 typedef struct vol_view {
@@ -135,6 +137,43 @@ static uint32_t filter_sigma(const vol_view *v, const oracle_params *p, int64_t 
                 if (diff < 0)
                     diff = -diff;
                 if (diff <= (int64_t)p->sigma_band) {
+                    s += Pi;
+                    n += 1;
+                }
+            }
+    if (P0 < p->threshold || s < n * (uint64_t)p->threshold)
+        return 0;
+    return round_div(s, n);
+}
+
+/* Sigma filter with the local standard deviation (Lee's original form, named
+ * in "Related Work"): the band |P_i - P0| <= k sigma_local, where sigma_local
+ * is the population standard deviation of the M^3 cube itself; with m = M^3,
+ * S1 and S2 the sum and the sum of squares over the cube,
+ *   (P_i - P0)^2 <= k^2 (m S2 - S1^2) / m^2  <=>  m^2 (P_i - P0)^2 <= k^2 (m S2 - S1^2),
+ * compared exactly in integers; then as filter_sigma (mean of the band, gate). */
+static uint32_t filter_sigma_local(const vol_view *v, const oracle_params *p, int64_t x, int64_t y, int64_t z)
+{
+    const int r = p->radius, M = 2 * r + 1;
+    const uint32_t P0 = sample(v, x, y, z);
+    const unsigned __int128 m = (unsigned __int128)M * M * M;
+    unsigned __int128 S1 = 0, S2 = 0;
+    for (int k = -r; k <= r; ++k)
+        for (int j = -r; j <= r; ++j)
+            for (int i = -r; i <= r; ++i) {
+                const uint64_t Pi = sample(v, x + i, y + j, z + k);
+                S1 += Pi;
+                S2 += (unsigned __int128)Pi * Pi;
+            }
+    const unsigned __int128 kk = (unsigned __int128)p->sigma_k * p->sigma_k;
+    const unsigned __int128 rhs = kk * (m * S2 - S1 * S1);
+    uint64_t s = 0, n = 0;
+    for (int k = -r; k <= r; ++k)
+        for (int j = -r; j <= r; ++j)
+            for (int i = -r; i <= r; ++i) {
+                const uint32_t Pi = sample(v, x + i, y + j, z + k);
+                const unsigned __int128 d = Pi > P0 ? Pi - P0 : P0 - Pi;
+                if (m * m * d * d <= rhs) {
                     s += Pi;
                     n += 1;
                 }
@@ -252,6 +291,7 @@ static uint32_t filter_at(const vol_view *v, const oracle_params *p, int64_t x, 
     case 4: return filter_ours(v, p, x, y, z);
     case 5:
     case 6: return filter_ours_variant(v, p, x, y, z);
+    case 7: return filter_sigma_local(v, p, x, y, z);
     default: return 0;
     }
 }
@@ -267,7 +307,7 @@ int oracle_filter_box(const void *vol, int64_t nx, int64_t ny, int64_t nz, int d
         return -1;
     if (x0 < 0 || y0 < 0 || z0 < 0 || x1 > nx || y1 > ny || z1 > nz || x1 < x0 || y1 < y0 || z1 < z0)
         return -1;
-    if (p->filter_id < 0 || p->filter_id > 6 || p->radius < 0)
+    if (p->filter_id < 0 || p->filter_id > 7 || p->radius < 0)
         return -1;
     vol_view v = {vol, nx, ny, nz, dtype};
     int64_t bx = x1 - x0, by = y1 - y0;
@@ -421,7 +461,7 @@ int oracle_render(const void *vol, int64_t nx, int64_t ny, int64_t nz, int dtype
 {
     if (!vol || !p || !image || !depth || !value || nx < 1 || ny < 1 || nz < 1 || (dtype != 0 && dtype != 1))
         return -1;
-    if (p->filter_id < 0 || p->filter_id > 6 || p->radius < 0)
+    if (p->filter_id < 0 || p->filter_id > 7 || p->radius < 0)
         return -1;
     int64_t W, H, len;
     if (render_extent(view, nx, ny, nz, &W, &H, &len) != 0)

@@ -20,6 +20,7 @@ import phantoms
 
 MEAN, SIGMA, ENTROPY, OKADA, OURS = 0, 1, 2, 3, 4
 OURS_CROSS7, OURS_CUBE = 5, 6
+SIGMA_LOCAL = 7
 
 
 # --------------------------------------------------------------------------------------
@@ -102,6 +103,15 @@ class Brute:
         A = Fraction(sum(sel), len(sel))
         return self.rnd(A) if (P0 >= T and A >= T) else 0
 
+    def sigma_local(self, r, k, T, x, y, z):
+        # Lee's original: the band uses the population variance of the cube itself
+        P0 = self.P(x, y, z)
+        c = self.cube(r, x, y, z)
+        var = Fraction(sum(v * v for v in c), len(c)) - Fraction(sum(c), len(c)) ** 2
+        sel = [v for v in c if (v - P0) ** 2 <= k * k * var]
+        A = Fraction(sum(sel), len(sel))
+        return self.rnd(A) if (P0 >= T and A >= T) else 0
+
     def okada(self, r, td, T, x, y, z):
         P0 = self.P(x, y, z)
         nb = [P0]
@@ -133,6 +143,34 @@ def test_brute_force_cluster_variants(dims, dt, seed, mode):
                 got = oracle.filter_volume(vol, f, r, params=dict(prm, offset=d))
                 for z, y, x in itertools.product(range(nz), range(ny), range(nx)):
                     assert got[z, y, x] == b.ours_layout(layout, r, d, T, x, y, z), (layout, r, d, x, y, z)
+
+
+@pytest.mark.parametrize("dims,dt,seed", [((4, 5, 6), "u8", 71), ((6, 4, 5), "u16", 72), ((5, 5, 5), "u8", 73)])
+@pytest.mark.parametrize("mode", ["none", "otsu", "fixed"])
+def test_brute_force_sigma_local(dims, dt, seed, mode):
+    vol = phantoms.random_volume(dims, seed, dt)
+    T, cfg = _fixed_T(vol, mode, seed)
+    b = Brute(vol)
+    st = oracle.stats(vol)
+    nx, ny, nz = dims
+    for r in (0, 1, 2):
+        for k in (1, 2, 3):
+            prm = dict(oracle.derive_params(st, r, cfg), k=k)
+            got = oracle.filter_volume(vol, SIGMA_LOCAL, r, params=prm)
+            for z, y, x in itertools.product(range(nz), range(ny), range(nx)):
+                assert got[z, y, x] == b.sigma_local(r, k, T, x, y, z), (r, k, x, y, z)
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_sigma_local_is_global_when_the_cube_is_the_volume(seed):
+    """On a 3^3 volume the centre voxel's cube at r = 1 is the whole volume, so
+    its local sigma is the global one and both filters agree there."""
+    vol = phantoms.random_volume((3, 3, 3), 80 + seed, "u16" if seed % 2 else "u8")
+    st = oracle.stats(vol)
+    for k in (1, 2):
+        prm = oracle.derive_params(st, 1, oracle.Config(sigma_k=k, threshold_mode="none"))
+        pt = np.array([[1, 1, 1]])
+        assert oracle.filter_points(vol, SIGMA_LOCAL, 1, pt, prm)[0] == oracle.filter_points(vol, SIGMA, 1, pt, prm)[0]
 
 
 @pytest.mark.parametrize("r", [1, 2])
@@ -385,7 +423,7 @@ def test_constant_volume(dt, c):
     for r in (0, 1, 2):
         prm = oracle.derive_params(st, r)
         assert prm["T"] == c
-        for f in (MEAN, SIGMA, OKADA, OURS, OURS_CROSS7, OURS_CUBE):
+        for f in (MEAN, SIGMA, OKADA, OURS, OURS_CROSS7, OURS_CUBE, SIGMA_LOCAL):
             assert (oracle.filter_volume(vol, f, r, params=prm) == c).all(), (f, r)
         # all weights are 0, so the criterion is 0 and 0 > T_e = 0 fails
         assert not oracle.filter_volume(vol, ENTROPY, r, params=prm).any()
@@ -524,12 +562,12 @@ def test_symmetry_48(dt):
     vol = phantoms.random_volume((6, 6, 6), 31, dt, p_extreme=0.2)
     st = oracle.stats(vol)
     outs = {}
-    for f in range(7):
+    for f in range(8):
         prm = oracle.derive_params(st, 1)
         outs[f] = (prm, oracle.filter_volume(vol, f, 1, params=prm))
     for perm, flips in _transforms():
         tv = _apply(vol, perm, flips)
-        for f in range(7):
+        for f in range(8):
             prm, ref = outs[f]
             got = oracle.filter_volume(tv, f, 1, params=prm)
             assert (got == _apply(ref, perm, flips)).all(), (f, perm, flips)
