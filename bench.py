@@ -671,10 +671,11 @@ def run_render(args):
 
 
 def run_variants(args):
-    """Cluster-layout variants of the paper's filter (axis-cross clusters, cube
-    clusters) beside the paper's own layout, on the 512^3 uint16 phantom at
-    r = 2: device ms per launch of each filter kernel (the variants run on the
-    generic kernel, the paper's filter on its specialised one)."""
+    """The variants beside the filters they vary, on the 512^3 uint16 phantom at
+    r = 2: the cluster-layout variants of the paper's filter (axis-cross and cube
+    clusters) and the sigma filter with the local sigma of its cube; device ms
+    per launch (the variants run on the generic kernel, the paper's filter and
+    the sigma filter on their specialised ones)."""
     import torch
     import phantoms
     import paper_1807_03119_gb300 as lnf
@@ -686,7 +687,7 @@ def run_variants(args):
     out = torch.empty_like(t)
     ctx = lnf.Context()
     res = {}
-    for name in ("ours", "ours_cross", "ours_cube"):
+    for name in ("ours", "ours_cross", "ours_cube", "sigma", "sigma_local"):
         f = lnf.FILTERS[name]
         for _ in range(args.warmup):
             ctx.filter_volume(t, f, RADIUS, out=out)
@@ -701,7 +702,7 @@ def run_variants(args):
         ms = tot / n
         res[name] = {"ms_per_launch": ms, "gvox_s": N_VOX / (ms / 1e3) / 1e9,
                      "hbm_frac": N_VOX * ES * 2 / (ms / 1e3) / 1e9 / peaks()["hbm_gbs"]}
-    line = {"metric": "cluster-layout variants of the paper's filter, 512^3 uint16, r=2", "mode": "variants",
+    line = {"metric": "filter variants (cluster layouts, local sigma), 512^3 uint16, r=2", "mode": "variants",
             "value": res["ours_cube"]["gvox_s"], "unit": UNIT, "higher_is_better": True, "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "dtype": "u16", "data": "synthetic",
             "config": {"workload": WORKLOAD, "radius": RADIUS}, "filters": res}

@@ -74,7 +74,9 @@ typedef enum lnf_filter_id {
        commented-out S_0; the conclusion proposes other layouts): the same nine
        cluster centres and combination, each cluster being */
     LNF_OURS_CROSS7 = 5,  /* its centre and axis cross of arm r, averaged (r = 1: (P0 + 6 neighbours) / 7) */
-    LNF_OURS_CUBE = 6     /* the M^3 cube around its centre, averaged */
+    LNF_OURS_CUBE = 6,    /* the M^3 cube around its centre, averaged */
+    LNF_SIGMA_LOCAL = 7   /* Eq. 5 with the local sigma of the M^3 cube (Lee's original, "Related Work"):
+                             |P_i - P0| <= k sigma_cube, k = sigma_k */
 } lnf_filter_id;
 
 typedef enum lnf_threshold_mode {

@@ -22,8 +22,9 @@ __all__ = [
 
 MEAN, SIGMA, ENTROPY, OKADA, OURS = 0, 1, 2, 3, 4
 OURS_CROSS7, OURS_CUBE = 5, 6   # cluster-layout variants of the paper's filter
+SIGMA_LOCAL = 7                 # the sigma filter with the local sigma of its cube
 FILTERS = {"mean": MEAN, "sigma": SIGMA, "entropy": ENTROPY, "okada": OKADA, "ours": OURS,
-           "ours_cross": OURS_CROSS7, "ours_cube": OURS_CUBE}
+           "ours_cross": OURS_CROSS7, "ours_cube": OURS_CUBE, "sigma_local": SIGMA_LOCAL}
 THRESH_OTSU, THRESH_FIXED, THRESH_NONE = 0, 1, 2
 TD_AUTO, TE_AUTO, TE_PASS_ALL = -1, -2, -1
 STATUS = {0: "LNF_OK", 1: "LNF_EINVAL", 2: "LNF_ENOMEM", 3: "LNF_EBUDGET", 4: "LNF_EPENDING",

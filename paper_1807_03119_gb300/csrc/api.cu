@@ -58,8 +58,8 @@ lnf_status lnf_check_volume(lnf_ctx *ctx, const void *p, const int64_t dims[3], 
 
 static lnf_status check_filter(lnf_ctx *ctx, int filter_id, int radius)
 {
-    if (filter_id < LNF_MEAN || filter_id > LNF_OURS_CUBE)
-        return lnf_fail(ctx, LNF_EINVAL, "filter_id %d not in 0..6", filter_id);
+    if (filter_id < LNF_MEAN || filter_id > LNF_SIGMA_LOCAL)
+        return lnf_fail(ctx, LNF_EINVAL, "filter_id %d not in 0..7", filter_id);
     if (radius < 0 || radius > LNF_MAX_RADIUS)
         return lnf_fail(ctx, LNF_EINVAL, "radius %d not in 0..%d", radius, LNF_MAX_RADIUS);
     return LNF_OK;
@@ -349,8 +349,8 @@ extern "C" lnf_status lnf_profile_read(lnf_ctx *ctx, lnf_kernel_time *out, int m
 static const char *filter_name(int f)
 {
     static const char *names[] = {"filter:mean", "filter:sigma", "filter:entropy", "filter:okada",
-                                  "filter:ours", "filter:ours_cross", "filter:ours_cube"};
-    return f >= 0 && f <= 6 ? names[f] : "filter:?";
+                                  "filter:ours", "filter:ours_cross", "filter:ours_cube", "filter:sigma_local"};
+    return f >= 0 && f <= 7 ? names[f] : "filter:?";
 }
 
 // ------------------------------------------------------------------ device steps

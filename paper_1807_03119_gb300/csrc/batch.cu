@@ -110,7 +110,7 @@ static lnf_status check_job(lnf_ctx *ctx, const lnf_job &j, int i)
     lnf_status s = lnf_check_volume(ctx, j.in, j.dims, j.dtype);
     if (s != LNF_OK)
         return s;
-    if (j.filter_id < LNF_MEAN || j.filter_id > LNF_OURS_CUBE || j.radius < 0 || j.radius > LNF_MAX_RADIUS)
+    if (j.filter_id < LNF_MEAN || j.filter_id > LNF_SIGMA_LOCAL || j.radius < 0 || j.radius > LNF_MAX_RADIUS)
         return lnf_fail(ctx, LNF_EINVAL, "job %d: filter %d / radius %d out of range", i, j.filter_id, j.radius);
     if (!j.out)
         return lnf_fail(ctx, LNF_EINVAL, "job %d: null output", i);

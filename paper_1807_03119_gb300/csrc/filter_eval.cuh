@@ -15,6 +15,7 @@ __device__ __forceinline__ u32 rnd_div(u64 a, u64 b) { return (u32)((2 * a + b) 
 struct StepParams {
     u32 T;
     u32 delta;
+    u32 k;              // sigma_k, for the local sigma filter
     long long td;
     long long te;
     int r, d;
@@ -91,6 +92,34 @@ __device__ __forceinline__ u32 eval_filter(int filter, const S &R, const StepPar
             return 0;
         return rnd_div(s, n);
     }
+    case 7: {   // sigma with the local standard deviation of the cube (Lee's original):
+        // m^2 (P_i - P0)^2 <= k^2 (m S2 - S1^2), exactly
+        u64 S1 = 0, S2 = 0;
+        for (int k = -r; k <= r; ++k)
+            for (int j = -r; j <= r; ++j)
+                for (int i = -r; i <= r; ++i) {
+                    const u64 v = R.at(i, j, k);
+                    S1 += v;
+                    S2 += v * v;
+                }
+        const unsigned __int128 m = (unsigned __int128)M * M * M;
+        const unsigned __int128 rhs = (unsigned __int128)p.k * p.k * (m * S2 - (unsigned __int128)S1 * S1);
+        u64 s = 0;
+        u32 n = 0;
+        for (int k = -r; k <= r; ++k)
+            for (int j = -r; j <= r; ++j)
+                for (int i = -r; i <= r; ++i) {
+                    const u32 v = R.at(i, j, k);
+                    const u64 d = v > P0 ? v - P0 : P0 - v;
+                    if (m * m * d * d <= rhs) {
+                        s += v;
+                        ++n;
+                    }
+                }
+        if (P0 < p.T || s < (u64)n * p.T)
+            return 0;
+        return rnd_div(s, n);
+    }
     case 5:     // cluster-layout variants of the paper's filter: the nine cluster
     case 6: {   // centres of Eq. 2-3, each cluster its axis cross of arm r (5) or its M^3 cube (6)
         u64 U = 0;
@@ -148,6 +177,7 @@ __device__ __forceinline__ StepParams make_step_params(const DevParams &P, int r
     StepParams sp;
     sp.T = P.T;
     sp.delta = P.delta;
+    sp.k = P.sigma_k;
     sp.td = P.td;
     sp.r = radius;
     sp.d = offset;

@@ -45,6 +45,8 @@ struct DevParams {
     u32 levels;
     u32 valid;                  // 1 once written
     double H_in;                // image entropy of the input
+    u32 sigma_k;                // k of the sigma bands (global: in delta; local: applied per cube)
+    u32 pad;
 };
 
 // One unit of filter work: a volume (or ROI of it) with a filter and radius.

@@ -538,6 +538,8 @@ __device__ void chunk_params(const u64 *hist, const DevStats *st, const ParamCfg
     p.levels = L;
     p.valid = 1;
     p.H_in = Hs;
+    p.sigma_k = (u32)cfg.sigma_k;
+    p.pad = 0;
     *prm = p;
 }
 

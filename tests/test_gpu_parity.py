@@ -298,7 +298,7 @@ def test_batched_mixed(lnf):
 def test_invalid_arguments(ctx, lnf):
     t = dev(np.zeros((4, 4, 4), np.uint8))
     with pytest.raises(lnf.LnfError):
-        ctx.filter_volume(t, 7, 1)              # filter ids are 0..6
+        ctx.filter_volume(t, 8, 1)              # filter ids are 0..7
     with pytest.raises(lnf.LnfError):
         ctx.filter_volume(t, 0, 9)
     with pytest.raises(lnf.LnfError):

@@ -1,6 +1,8 @@
-"""Parity of the cluster-layout variants of the paper's filter (axis-cross and
-cube clusters) with the oracle, through the C ABI: whole volumes and ROIs,
-both dtypes, radii 0..2, cluster offsets 1 and 2, and the ray caster."""
+"""Parity of the variants with the oracle, through the C ABI: the
+cluster-layout variants of the paper's filter (axis-cross and cube clusters)
+and the sigma filter with the local sigma of its cube; whole volumes and
+ROIs, both dtypes, radii 0..2, cluster offsets 1 and 2 or k = 1..3, and the
+ray caster."""
 import numpy as np
 import pytest
 
@@ -61,3 +63,25 @@ def test_variants_render(lnf):
                     assert np.array_equal(dep.cpu().numpy(), wd), (f, view)
                     assert np.array_equal(val.cpu().numpy().astype(np.uint32), wv), (f, view)
                     assert np.array_equal(im.cpu().numpy(), wim), (f, view)
+
+
+@pytest.mark.parametrize("k", [1, 2, 3])
+def test_sigma_local_matches_oracle(lnf, k):
+    with lnf.Context(sigma_k=k) as c:
+        for vol in _vols():
+            t = torch.from_numpy(vol).cuda()
+            st = oracle.stats(vol)
+            for r in (0, 1, 2):
+                prm = dict(oracle.derive_params(st, r, oracle.Config(sigma_k=k)), k=k)
+                got = c.filter_volume(t, oracle.SIGMA_LOCAL, r).cpu().numpy()
+                want = oracle.filter_volume(vol, oracle.SIGMA_LOCAL, r, params=prm)
+                assert np.array_equal(got, want), (vol.dtype, r, k)
+                roi = (5, 1, 2, 13, 11, 9)
+                got = c.filter_roi(t, oracle.SIGMA_LOCAL, r, roi[:3], roi[3:]).cpu().numpy()
+                want = oracle.filter_volume(vol, oracle.SIGMA_LOCAL, r, params=prm, roi=roi)
+                assert np.array_equal(got, want), ("roi", vol.dtype, r, k)
+            im, dep, val = c.render(t, oracle.SIGMA_LOCAL, 1, 4)
+            prm = dict(oracle.derive_params(st, 1, oracle.Config(sigma_k=k)), k=k)
+            wim, wd, wv = oracle.render(vol, oracle.SIGMA_LOCAL, 1, 4, params=prm)
+            assert np.array_equal(dep.cpu().numpy(), wd) and np.array_equal(im.cpu().numpy(), wim)
+            c.params()
