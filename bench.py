@@ -52,6 +52,18 @@ def peaks():
     return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0, "source": "fallback"}
 
 
+def max_over_ranks(value, world, device):
+    """The slowest rank's figure, which is the job's: a MAX all-reduce over the
+    ranks of the process group (replicas; no data-path collective)."""
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 # plain integer ALU peak: 152 SMs x 128 INT32 lanes x max SM clock
 def alu_peak_tops(sm_mhz):
     return 152 * 128 * sm_mhz * 1e6 / 1e12
@@ -363,10 +375,7 @@ def main():
     ms = e0.elapsed_time(e1) / args.steps
     kern, launches = ctx.profile_read()
     ctx.profile(False)
-    if world > 1:
-        tt = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt.item())
+    ms = max_over_ranks(ms, world, "cuda")
     value = world * 5 * N_VOX / (ms / 1e3) / 1e9
 
     if args.no_e2e:
@@ -384,10 +393,7 @@ def main():
     for _ in range(args.e2e_steps):
         ctx.filter_multi_host(in_np, filters, RADIUS, outs=outs_np)
     e2e_s = (time.perf_counter() - t0) / max(1, args.e2e_steps) if args.e2e_steps > 0 else float("nan")
-    if world > 1:
-        tt = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e_s = float(tt.item())
+    e2e_s = max_over_ranks(e2e_s, world, "cuda")
     e2e = None
     if args.e2e_steps > 0:
         e2e = {"value": world * 5 * N_VOX / e2e_s / 1e9, "unit": UNIT,

@@ -216,6 +216,19 @@ lnf_status lnf_render(lnf_ctx *ctx, int filter_id, int radius, const void *in, c
                       int view, uint8_t *image, int32_t *depth, uint32_t *value);
 
 /*
+ * Failure-detection self-test (no counterpart in the paper): launches one
+ * kernel that waits, through the same bounded wait the filter kernels use on
+ * their TMA barriers, on a barrier that nothing will ever complete.  The wait
+ * must give up after limit_ms, record the failure in a device status word and
+ * return, leaving the context usable.  elapsed_ms (may be NULL) receives the
+ * host-side time of the call.  Returns LNF_ETIMEOUT when the wait gave up as
+ * designed (the expected outcome), LNF_OK if it somehow completed,
+ * LNF_EINVAL for limit_ms outside (0, 2000], LNF_ECUDA if the launch failed.
+ * Synchronises the context's stream.
+ */
+lnf_status lnf_selftest_wait(lnf_ctx *ctx, double limit_ms, double *elapsed_ms);
+
+/*
  * Image entropy of a volume, like lnf_entropy, for callers that must not
  * allocate device memory: no cudaMalloc, cudaFree or allocating library call
  * is made, and no lnf_ctx is needed (creating one allocates).  Typical users:

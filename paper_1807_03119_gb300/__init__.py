@@ -143,6 +143,7 @@ _SIGS = {
                                       ctypes.c_int, _i64p, _i64p, ctypes.c_void_p]),
     "lnf_render": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p, _i64p, ctypes.c_int,
                                   ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "lnf_selftest_wait": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.POINTER(ctypes.c_double)]),
     "lnf_entropy": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, _i64p, ctypes.c_int,
                                    ctypes.POINTER(ctypes.c_double)]),
     "lnf_get_params": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Params), ctypes.c_void_p]),
@@ -353,6 +354,14 @@ class Context:
                                         view, image.data_ptr(), depth.data_ptr() if depth is not None else None,
                                         value.data_ptr() if value is not None else None))
         return image, depth, value
+
+    def selftest_wait(self, limit_ms=50.0):
+        """Failure-detection self-test: returns (status code, elapsed ms); the
+        expected status is LNF_ETIMEOUT (6), the wait having given up."""
+        el = ctypes.c_double()
+        self._sync_stream()
+        rc = self.lib.lnf_selftest_wait(self.h, limit_ms, ctypes.byref(el))
+        return rc, el.value
 
     def entropy(self, vol):
         _check_dev(vol)

@@ -45,7 +45,9 @@ struct lnf_ctx {
     u64 *out_hist = nullptr;    // LNF_MAX_PACK output histograms of 65536 bins
     double *d_H = nullptr;
     u32 *d_err = nullptr;
-    u32 *d_counter = nullptr;
+    u32 *d_counter = nullptr;   // work counters: [0] generic, [1..4] serving streams (generic),
+                                // [8] paper's filter, [9] comparison filters, [10..13] serving
+                                // streams (specialised), [15] the self-test's status word
     double *d_ent_part = nullptr;   // entropy reduction partials (LNF_ENT_SPLIT x LNF_MAX_ENT)
     u32 *d_ent_done = nullptr;      // entropy reduction tickets (LNF_MAX_ENT)
     PFN_encodeTiled encode = nullptr;
