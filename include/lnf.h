@@ -124,7 +124,17 @@ typedef struct lnf_ctx lnf_ctx;
 void lnf_config_default(lnf_config *cfg);
 
 /* Create a context on the current CUDA device.  Allocates the fixed scratch
- * (about 3 MiB).  Returns LNF_EINVAL for a bad config, LNF_ENOMEM/LNF_ECUDA. */
+ * (about 3 MiB).  Returns LNF_EINVAL for a bad config, LNF_ENOMEM/LNF_ECUDA.
+ *
+ * Testing: the environment variable LNF_FAULT, read here, injects host-side
+ * failures into this context.  It lists sites, separated by commas, each as
+ * "site" (every time) or "site@n" (the n-th time only, from 1):
+ *   scratch   scratch allocation of an analysed volume   -> LNF_ENOMEM
+ *   resident  lnf_volume_register's resident copy        -> LNF_ENOMEM, budget restored
+ *   output    a served request's output allocation       -> that request ends LNF_ENOMEM
+ *   launch    a filter launch (plain call, served request) -> LNF_ECUDA
+ *   stage     the padded copy of an input TMA cannot read -> none: the generic kernel runs
+ * An unknown site or a bad count returns LNF_EINVAL before the device is touched. */
 lnf_status lnf_create(const lnf_config *cfg, lnf_ctx **out);
 
 /* Wait for the context's work, stop its scheduler and free everything it owns. */

@@ -56,6 +56,43 @@ lnf_status lnf_check_volume(lnf_ctx *ctx, const void *p, const int64_t dims[3], 
     return LNF_OK;
 }
 
+bool lnf_fault_parse(const char *spec, FaultPlan &plan)
+{
+    static const char *const names[FAULT_NSITES] = {"scratch", "resident", "output", "stage", "launch"};
+    if (!spec)
+        return true;
+    const char *p = spec;
+    while (*p) {
+        const char *end = p;
+        while (*end && *end != ',')
+            ++end;
+        const char *at = p;
+        while (at < end && *at != '@')
+            ++at;
+        int site = -1;
+        for (int i = 0; i < FAULT_NSITES; ++i)
+            if ((size_t)(at - p) == std::strlen(names[i]) && std::strncmp(p, names[i], at - p) == 0)
+                site = i;
+        if (site < 0 && at > p)
+            return false;
+        int64_t n = -1;
+        if (at < end) {
+            n = 0;
+            for (const char *c = at + 1; c < end; ++c) {
+                if (*c < '0' || *c > '9' || n > (1ll << 40))
+                    return false;
+                n = n * 10 + (*c - '0');
+            }
+            if (n < 1)
+                return false;
+        }
+        if (site >= 0)
+            plan.nth[site] = n;
+        p = *end ? end + 1 : end;
+    }
+    return true;
+}
+
 static lnf_status check_filter(lnf_ctx *ctx, int filter_id, int radius)
 {
     if (filter_id < LNF_MEAN || filter_id > LNF_SIGMA_LOCAL)
@@ -108,6 +145,8 @@ ParamCfg lnf_param_cfg(const lnf_config &c)
 
 static lnf_status alloc_scratch(lnf_ctx *ctx, VolScratch &vs)
 {
+    if (lnf_fault(ctx, FAULT_SCRATCH))
+        return lnf_fail(ctx, LNF_ENOMEM, "injected fault: scratch allocation failed");
     CK(cudaMalloc(&vs.hist, sizeof(u64) * LNF_LEVELS_U16));
     CK(cudaMalloc(&vs.st, sizeof(DevStats)));
     CK(cudaMalloc(&vs.prm, sizeof(DevParams)));
@@ -133,8 +172,10 @@ lnf_status lnf_scratch_pool(lnf_ctx *ctx, size_t n)
     while (ctx->pool.size() < n) {
         VolScratch vs{};
         lnf_status s = alloc_scratch(ctx, vs);
-        if (s != LNF_OK)
+        if (s != LNF_OK) {
+            free_scratch(vs);
             return s;
+        }
         ctx->pool.push_back(vs);
     }
     return LNF_OK;
@@ -144,6 +185,7 @@ static void prof_clear(lnf_ctx *ctx);
 
 extern "C" lnf_status lnf_create(const lnf_config *cfg_in, lnf_ctx **out)
 {
+    LNF_RANGE("lnf_create");
     if (!out)
         return LNF_EINVAL;
     *out = nullptr;
@@ -160,10 +202,15 @@ extern "C" lnf_status lnf_create(const lnf_config *cfg_in, lnf_ctx **out)
         cfg.hbm_budget_bytes = 40ull << 30;
     if (cfg.max_inflight <= 0)
         cfg.max_inflight = 64;
+    FaultPlan plan;
+    if (!lnf_fault_parse(getenv("LNF_FAULT"), plan))
+        return LNF_EINVAL;
     lnf_ctx *ctx = new (std::nothrow) lnf_ctx();
     if (!ctx)
         return LNF_ENOMEM;
     ctx->cfg = cfg;
+    for (int i = 0; i < FAULT_NSITES; ++i)
+        ctx->fault.nth[i] = plan.nth[i];
     ctx->stream = static_cast<cudaStream_t>(cfg.stream);
     lnf_status s = LNF_OK;
     do {
@@ -506,8 +553,11 @@ static lnf_status stage_input(lnf_ctx *ctx, const void *in, const int64_t dims[3
         cudaFree(ctx->pitched);   // waits for the work that still reads it
         ctx->pitched = nullptr;
         ctx->pitched_cap = 0;
-        if (cudaMalloc(&ctx->pitched, need) != cudaSuccess)
+        if (lnf_fault(ctx, FAULT_STAGE) || cudaMalloc(&ctx->pitched, need) != cudaSuccess) {
+            ctx->pitched = nullptr;
+            cudaGetLastError();
             return LNF_OK;   // no room for the copy: the generic kernel reads the input itself
+        }
         ctx->pitched_cap = need;
     }
     lnf_status s = lnf_copy_pitched(ctx, ctx->pitched, prow, in, dims, dtype, st);
@@ -529,6 +579,9 @@ lnf_status lnf_run_one(lnf_ctx *ctx, int filter, int radius, const void *in, voi
         lnf_make_job(ctx, pk, 0, filter, radius, in, out, dims, dtype, roi_o, roi_d, vs, out_hist, pitch);
     if (s != LNF_OK)
         return s;
+    if (lnf_fault(ctx, FAULT_LAUNCH))
+        return lnf_fail(ctx, LNF_ECUDA, "injected fault: filter launch failed");
+    LNF_RANGE(filter_name(filter));
     const int rec = lnf_prof_begin(ctx, stream);
     if (!ctx->no_fast) {
         int handled = 0;
@@ -548,6 +601,7 @@ lnf_status lnf_run_one(lnf_ctx *ctx, int filter, int radius, const void *in, voi
 extern "C" lnf_status lnf_filter_volume(lnf_ctx *ctx, int filter_id, int radius, const void *in, void *out,
                                         const int64_t dims[3], int dtype)
 {
+    LNF_RANGE("lnf_filter_volume");
     if (!ctx)
         return LNF_EINVAL;
     lnf_status s;
@@ -575,6 +629,7 @@ extern "C" lnf_status lnf_filter_roi(lnf_ctx *ctx, int filter_id, int radius, co
                                      const int64_t dims[3], int dtype, const int64_t roi_origin[3],
                                      const int64_t roi_dims[3], void *out)
 {
+    LNF_RANGE("lnf_filter_roi");
     if (!ctx)
         return LNF_EINVAL;
     lnf_status s;
@@ -605,6 +660,7 @@ static lnf_status multi_impl(lnf_ctx *ctx, int radius, const void *in, const int
 extern "C" lnf_status lnf_filter_multi(lnf_ctx *ctx, int radius, const void *in, const int64_t dims[3], int dtype,
                                        int n, const int *filter_ids, void *const *outs, double *d_entropy)
 {
+    LNF_RANGE("lnf_filter_multi");
     return multi_impl(ctx, radius, in, dims, dtype, n, filter_ids, outs, d_entropy, nullptr);
 }
 
@@ -686,6 +742,7 @@ extern "C" lnf_status lnf_filter_multi_host(lnf_ctx *ctx, int radius, const void
                                             int dtype, int n, const int *filter_ids, void *const *outs,
                                             double *entropy)
 {
+    LNF_RANGE("lnf_filter_multi_host");
     if (!ctx)
         return LNF_EINVAL;
     lnf_status s;
@@ -738,6 +795,7 @@ extern "C" lnf_status lnf_filter_multi_host(lnf_ctx *ctx, int radius, const void
 extern "C" lnf_status lnf_render(lnf_ctx *ctx, int filter_id, int radius, const void *in, const int64_t dims[3],
                                  int dtype, int view, uint8_t *image, int32_t *depth, uint32_t *value)
 {
+    LNF_RANGE("lnf_render");
     if (!ctx)
         return LNF_EINVAL;
     lnf_status s;
@@ -760,6 +818,7 @@ extern "C" lnf_status lnf_render(lnf_ctx *ctx, int filter_id, int radius, const 
 
 extern "C" lnf_status lnf_entropy(lnf_ctx *ctx, const void *vol, const int64_t dims[3], int dtype, double *H)
 {
+    LNF_RANGE("lnf_entropy");
     if (!ctx)
         return LNF_EINVAL;
     lnf_status s;

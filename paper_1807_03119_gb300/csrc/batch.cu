@@ -92,7 +92,7 @@ static lnf_status alloc_stage(lnf_ctx *ctx, const lnf_job *jobs, int n, std::vec
         const size_t prow = lnf_pitched_row(j.in, j.dims, j.dtype);
         if (prow == 0)
             continue;
-        if (cudaMalloc(&stage[v], prow * j.dims[1] * j.dims[2]) != cudaSuccess) {
+        if (lnf_fault(ctx, FAULT_STAGE) || cudaMalloc(&stage[v], prow * j.dims[1] * j.dims[2]) != cudaSuccess) {
             stage[v] = nullptr;   // no room: the generic kernel reads the input itself
             cudaGetLastError();
         }
@@ -251,6 +251,7 @@ static float time_batch(lnf_ctx *ctx, const lnf_job *jobs, int n, int zc, const 
 
 extern "C" lnf_status lnf_filter_batch(lnf_ctx *ctx, const lnf_job *jobs, int n_jobs)
 {
+    LNF_RANGE("lnf_filter_batch");
     if (!ctx)
         return LNF_EINVAL;
     if (n_jobs < 0 || (n_jobs > 0 && !jobs))
@@ -276,8 +277,13 @@ extern "C" lnf_status lnf_filter_batch(lnf_ctx *ctx, const lnf_job *jobs, int n_
             return LNF_OK;
         }
     std::unique_ptr<BatchEntry> e(new BatchEntry());
-    lnf_status ss = alloc_stage(ctx, jobs, n_jobs, e->stage);
+    // every allocation happens before the capture (none is allowed inside it):
+    // one scratch per distinct input, the padded copies
+    std::vector<int> vol_of;
+    lnf_status ss = lnf_scratch_pool(ctx, distinct_inputs(jobs, n_jobs, vol_of).size());
     if (ss != LNF_OK)
+        return ss;
+    if ((ss = alloc_stage(ctx, jobs, n_jobs, e->stage)) != LNF_OK)
         return ss;
     // autotune the z chunk once per context
     if (ctx->cfg.autotune && ctx->tuned_zchunk == 0) {

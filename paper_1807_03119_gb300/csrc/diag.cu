@@ -25,6 +25,7 @@ __global__ void k_wait_probe(u32 *status, u64 limit_ns)
 
 extern "C" lnf_status lnf_selftest_wait(lnf_ctx *ctx, double limit_ms, double *elapsed_ms)
 {
+    LNF_RANGE("lnf_selftest_wait");
     if (!ctx)
         return LNF_EINVAL;
     if (!(limit_ms > 0.0) || limit_ms > 2000.0)

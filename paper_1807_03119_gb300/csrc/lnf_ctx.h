@@ -4,6 +4,7 @@
 #include "lnf.h"
 #include "lnf_internal.cuh"
 
+#include <atomic>
 #include <condition_variable>
 #include <deque>
 #include <map>
@@ -12,6 +13,21 @@
 #include <string>
 #include <thread>
 #include <vector>
+
+// NVTX ranges around the entry points and the filter launches (header-only
+// NVTX 3: free when no profiler is attached)
+#if __has_include(<nvtx3/nvToolsExt.h>)
+#include <nvtx3/nvToolsExt.h>
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
+#define LNF_RANGE(name) NvtxRange lnf_range_(name)
+#else
+#define LNF_RANGE(name) ((void)0)
+#endif
 
 typedef CUresult (*PFN_encodeTiled)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
                                     const cuuint64_t *, const cuuint32_t *, const cuuint32_t *,
@@ -25,6 +41,24 @@ struct VolScratch {
     DevParams *prm = nullptr;
     u32 *lut = nullptr;
     void *pscr = nullptr;       // parameter-derivation scratch (zeroed once)
+};
+
+// Host-side fault injection (testing).  LNF_FAULT, read when a context is
+// created, lists sites as "site" (every time) or "site@n" (the n-th time only,
+// counted from 1), separated by commas; at a listed site the library behaves as
+// if the CUDA call there had failed.  No device code is involved.
+enum FaultSite {
+    FAULT_SCRATCH = 0,   // lnf_create: the context's scratch allocation
+    FAULT_RESIDENT,      // lnf_volume_register: the resident copy's allocation
+    FAULT_OUTPUT,        // serving: a request's output allocation
+    FAULT_STAGE,         // plain / batched calls: the padded staging copy's allocation
+    FAULT_LAUNCH,        // plain / served calls: a filter launch
+    FAULT_NSITES
+};
+
+struct FaultPlan {
+    int64_t nth[FAULT_NSITES] = {};            // 0: off, -1: every time, n: the n-th time
+    std::atomic<int64_t> seen[FAULT_NSITES] = {};
 };
 
 struct BatchEntry;
@@ -75,6 +109,7 @@ struct lnf_ctx {
     };
     std::vector<ProfRec> prof_recs;
     std::vector<cudaEvent_t> prof_free;
+    FaultPlan fault;            // host-side fault injection (testing)
     // serving
     Server *srv = nullptr;
     std::mutex err_mu;
@@ -82,6 +117,17 @@ struct lnf_ctx {
 };
 
 lnf_status lnf_fail(lnf_ctx *ctx, lnf_status s, const char *fmt, ...);
+// Parse an LNF_FAULT list into `plan` (false: an unknown site or a bad count)
+bool lnf_fault_parse(const char *spec, FaultPlan &plan);
+// Whether the injected fault at `site` fires now (counts the visit)
+inline bool lnf_fault(lnf_ctx *ctx, FaultSite site)
+{
+    const int64_t n = ctx->fault.nth[site];
+    if (n == 0)
+        return false;
+    const int64_t k = ctx->fault.seen[site].fetch_add(1) + 1;
+    return n < 0 || k == n;
+}
 lnf_status lnf_check_volume(lnf_ctx *ctx, const void *p, const int64_t dims[3], int dtype);
 ParamCfg lnf_param_cfg(const lnf_config &c);
 lnf_status lnf_scratch_pool(lnf_ctx *ctx, size_t n);

@@ -200,8 +200,10 @@ lnf_status launch_wave(Server *s, Wave *w)
             std::lock_guard<std::mutex> g(s->mu);
             v = &s->vols[q->r.vol_id];
         }
-        if (cudaMallocAsync(&q->d_out, q->out_bytes, st) != cudaSuccess)
+        if (lnf_fault(ctx, FAULT_OUTPUT) || cudaMallocAsync(&q->d_out, q->out_bytes, st) != cudaSuccess) {
+            q->d_out = nullptr;
             return lnf_fail(ctx, LNF_ENOMEM, "serving: output allocation of %zu bytes failed", q->out_bytes);
+        }
         u64 *oh = nullptr;
         if (q->r.want_entropy) {
             oh = s->hists + (size_t)q->slot * LNF_LEVELS_U16;
@@ -221,6 +223,8 @@ lnf_status launch_wave(Server *s, Wave *w)
                                     oh, v->pitch);
         if (r != LNF_OK)
             return r;
+        if (lnf_fault(ctx, FAULT_LAUNCH))
+            return lnf_fail(ctx, LNF_ECUDA, "injected fault: filter launch failed");
         int handled = 0;
         if (!ctx->no_fast) {
             const FilterJob &j = pk.jobs[0];
@@ -282,7 +286,12 @@ void scheduler(Server *s)
         lnf_status r = launch_wave(s, w);
         lk.lock();
         if (r != LNF_OK) {
-            // the wave never reached the device: fail its requests
+            // the wave did not reach the device whole: fail its requests.  What
+            // it did enqueue finishes first, so that no slot (histogram, entropy)
+            // or output is handed on while a kernel of this wave may still write it
+            lk.unlock();
+            cudaStreamSynchronize(s->streams[w->stream_idx]);
+            lk.lock();
             s->last_err = lnf_last_error(s->ctx);
             for (Req *q : w->reqs) {
                 if (q->d_out)
@@ -300,6 +309,10 @@ void scheduler(Server *s)
                 q->wave = nullptr;
             }
             s->waves.erase(std::find(s->waves.begin(), s->waves.end(), w));
+            if (w->ev_start)
+                cudaEventDestroy(w->ev_start);
+            if (w->ev_done)
+                cudaEventDestroy(w->ev_done);
             delete w;
             s->done_cv.notify_all();
         }
@@ -405,6 +418,7 @@ extern "C" double lnf_now(void) { return now_s(); }
 extern "C" lnf_status lnf_volume_register(lnf_ctx *ctx, const void *src, int src_is_host, const int64_t dims[3],
                                           int dtype, int *vol_id)
 {
+    LNF_RANGE("lnf_volume_register");
     if (!ctx || !vol_id)
         return LNF_EINVAL;
     lnf_status st = lnf_check_volume(ctx, src, dims, dtype);
@@ -436,8 +450,10 @@ extern "C" lnf_status lnf_volume_register(lnf_ctx *ctx, const void *src, int src
         return e;
     };
     cudaStream_t st0 = s->streams[0];
-    if (cudaMalloc(&v.d_vol, v.bytes) != cudaSuccess)
+    if (lnf_fault(ctx, FAULT_RESIDENT) || cudaMalloc(&v.d_vol, v.bytes) != cudaSuccess) {
+        v.d_vol = nullptr;
         return undo(lnf_fail(ctx, LNF_ENOMEM, "resident volume allocation failed"));
+    }
     if (cudaMalloc(&v.vs.hist, sizeof(u64) * LNF_LEVELS_U16) != cudaSuccess ||
         cudaMalloc(&v.vs.st, sizeof(DevStats)) != cudaSuccess ||
         cudaMalloc(&v.vs.prm, sizeof(DevParams)) != cudaSuccess ||
@@ -523,6 +539,7 @@ extern "C" lnf_status lnf_volume_unregister(lnf_ctx *ctx, int vol_id)
 
 extern "C" lnf_status lnf_submit(lnf_ctx *ctx, const lnf_request *req, uint64_t *ticket)
 {
+    LNF_RANGE("lnf_submit");
     if (!ctx || !req || !ticket)
         return LNF_EINVAL;
     lnf_status st = ensure_server(ctx);
@@ -591,6 +608,7 @@ extern "C" lnf_status lnf_poll(lnf_ctx *ctx, uint64_t ticket, lnf_result *res)
 
 extern "C" lnf_status lnf_wait(lnf_ctx *ctx, uint64_t ticket, double timeout_s, lnf_result *res)
 {
+    LNF_RANGE("lnf_wait");
     if (!ctx || !ctx->srv)
         return LNF_EINVAL;
     Server *s = ctx->srv;
@@ -607,6 +625,7 @@ extern "C" lnf_status lnf_wait(lnf_ctx *ctx, uint64_t ticket, double timeout_s, 
 
 extern "C" lnf_status lnf_result_copy(lnf_ctx *ctx, uint64_t ticket, void *dst_host, size_t bytes)
 {
+    LNF_RANGE("lnf_result_copy");
     if (!ctx || !ctx->srv || !dst_host)
         return LNF_EINVAL;
     Server *s = ctx->srv;

@@ -59,3 +59,18 @@ def test_oracle_builds_and_loads():
     import oracle
     oracle.build()
     assert oracle.lib() is not None
+
+
+@pytest.mark.parametrize("spec", ["bogus", "output@0", "launch@x", "stage@", "resident,nope@2", "output@-1"])
+def test_fault_spec_is_checked_before_any_device_call(libpath, monkeypatch, spec):
+    """An LNF_FAULT list naming an unknown site or a bad count makes lnf_create
+    fail with LNF_EINVAL, before it touches the device."""
+    import ctypes
+    try:
+        lib = ctypes.CDLL(libpath)
+    except OSError as e:
+        pytest.skip(f"cannot dlopen: {e}")
+    monkeypatch.setenv("LNF_FAULT", spec)
+    h = ctypes.c_void_p()
+    assert lib.lnf_create(None, ctypes.byref(h)) == 1
+    assert not h.value
