@@ -34,7 +34,7 @@ __all__ = [
     "build", "lib", "Config", "stats", "otsu_threshold", "sigma_band", "okada_td_default",
     "log2_fixed", "entropy_weights", "entropy_te_default", "derive_params", "filter_volume",
     "filter_points", "image_entropy", "histogram", "MEAN", "SIGMA", "ENTROPY", "OKADA", "OURS",
-    "FILTER_NAMES", "LOG2_FRAC_BITS", "ENTROPY_W_BITS",
+    "FILTER_NAMES", "LOG2_FRAC_BITS", "ENTROPY_W_BITS", "spacing_radii",
 ]
 
 MEAN, SIGMA, ENTROPY, OKADA, OURS = 0, 1, 2, 3, 4
@@ -81,6 +81,9 @@ class _Params(ctypes.Structure):
         ("entropy_te", ctypes.c_int64),
         ("entropy_w", ctypes.POINTER(ctypes.c_uint32)),
         ("sigma_k", ctypes.c_int32),
+        ("aniso", ctypes.c_int32),
+        ("rad", ctypes.c_int32 * 3),
+        ("off", ctypes.c_int32 * 3),
     ]
 
 
@@ -273,8 +276,33 @@ class Config:
         self.offset = offset
 
 
+def _axes(v):
+    """An isotropic radius / offset r as (r, r, r); a per-axis (x, y, z) triple as itself."""
+    if isinstance(v, (tuple, list, np.ndarray)):
+        t = tuple(int(a) for a in v)
+        if len(t) != 3:
+            raise ValueError("per-axis values are (x, y, z) triples")
+        return t
+    return (int(v),) * 3
+
+
+def spacing_radii(extent, spacing):
+    """Per-axis radii (in voxels) of a physical extent on a grid of voxel
+    spacing (sx, sy, sz): floor(extent / s_a + 1/2), rounded half up in IEEE
+    double (a reading: the paper's volumes are isotropic)."""
+    out = []
+    for s in spacing:
+        s = float(s)
+        if not (s > 0 and math.isfinite(s)):
+            raise ValueError("spacing must be positive and finite")
+        out.append(int(math.floor(float(extent) / s + 0.5)))
+    return tuple(out)
+
+
 def derive_params(st, radius, cfg=None):
-    """All scalar parameters of the five filters for a volume with stats `st`."""
+    """All scalar parameters of the five filters for a volume with stats `st`.
+    `radius` is r, or a per-axis (rx, ry, rz) for anisotropic voxel spacing
+    (the entropy threshold's kernel then has (2rx+1)(2ry+1)(2rz+1) voxels)."""
     cfg = cfg or Config()
     if cfg.threshold_mode == "otsu":
         T = otsu_threshold(st.hist)
@@ -284,11 +312,12 @@ def derive_params(st, radius, cfg=None):
         T = 0
     else:
         raise ValueError(cfg.threshold_mode)
-    M = 2 * radius + 1
+    rx, ry, rz = _axes(radius)
+    m = (2 * rx + 1) * (2 * ry + 1) * (2 * rz + 1)
     delta = sigma_band(st.N, st.S, st.Q, cfg.sigma_k)
     td = okada_td_default(st.N, st.S, st.Q) if cfg.okada_td is None else int(cfg.okada_td)
     w = entropy_weights(st.hist)
-    te = entropy_te_default(st.hist, w, M ** 3) if cfg.entropy_te is None else int(cfg.entropy_te)
+    te = entropy_te_default(st.hist, w, m) if cfg.entropy_te is None else int(cfg.entropy_te)
     return {"T": T, "delta": delta, "td": td, "w": w, "te": te, "offset": cfg.offset,
             "radius": radius, "k": int(cfg.sigma_k)}
 
@@ -296,8 +325,16 @@ def derive_params(st, radius, cfg=None):
 def _cparams(filter_id, prm):
     p = _Params()
     p.filter_id = filter_id
-    p.radius = prm["radius"]
-    p.offset = prm["offset"]
+    rad, off = prm["radius"], prm["offset"]
+    if isinstance(rad, (tuple, list, np.ndarray)) or isinstance(off, (tuple, list, np.ndarray)):
+        p.aniso = 1
+        p.rad[:] = list(_axes(rad))
+        p.off[:] = list(_axes(off))
+        p.radius = max(p.rad)
+        p.offset = max(p.off)
+    else:
+        p.radius = rad
+        p.offset = off
     p.threshold = prm["T"]
     p.sigma_band = min(prm["delta"], 0xFFFFFFFF)
     p.okada_td = prm["td"]
@@ -310,7 +347,9 @@ def _cparams(filter_id, prm):
 
 def filter_volume(vol, filter_id, radius, cfg=None, params=None, roi=None, st=None):
     """Filter the whole volume (or the ROI (x0, y0, z0, nx, ny, nz)); the halo
-    always comes from the full volume and the statistics from the full volume."""
+    always comes from the full volume and the statistics from the full volume.
+    `radius` (and the cluster offset in `cfg` / `params`) may be a per-axis
+    (x, y, z) triple for anisotropic voxel spacing."""
     vol = np.ascontiguousarray(vol)
     nx, ny, nz = _dims(vol)
     if params is None:

@@ -34,6 +34,12 @@ typedef struct oracle_params {
     int64_t entropy_te;    /* T_e (fixed point): keep P0 iff E > T_e (Eq. 7) */
     const uint32_t *entropy_w; /* w[v] = fixed-point -p_v log2 p_v, one entry per grey level */
     int32_t sigma_k;       /* k of the local sigma filter: |P_i - P0| <= k sigma_local */
+    /* anisotropic voxel spacing: when `aniso` is set, radius and cluster offset
+     * are taken per axis (x, y, z) from rad[] and off[] instead of radius and
+     * offset; M_a = 2 rad[a] + 1 voxels along axis a */
+    int32_t aniso;
+    int32_t rad[3];
+    int32_t off[3];
 } oracle_params;
 
 typedef struct vol_view {
@@ -59,29 +65,39 @@ static uint32_t sample(const vol_view *v, int64_t x, int64_t y, int64_t z)
     return ((const uint16_t *)v->data)[idx];
 }
 
+/* The per-axis radii r[a] and cluster offsets d[a] (a = x, y, z) of a filter;
+ * the isotropic filters of the paper have r[a] = radius and d[a] = offset. */
+static void axis_extents(const oracle_params *p, int r[3], int d[3])
+{
+    for (int a = 0; a < 3; ++a) {
+        r[a] = p->aniso ? p->rad[a] : p->radius;
+        d[a] = p->aniso ? p->off[a] : p->offset;
+    }
+}
+
 /* round-half-up of a/b, b > 0 */
 static uint32_t round_div(uint64_t a, uint64_t b)
 {
     return (uint32_t)((2 * a + b) / (2 * b));
 }
 
-/* Eq. 2 without its 1/(3M) factor: the x-, y- and z-line sums of M voxels
- * through the cluster centre c, with offsets Delta_i = i - (M-1)/2 (Eq. 3).
- * The centre voxel therefore enters three times. */
-static uint64_t cluster_line_sum(const vol_view *v, int r, int64_t cx, int64_t cy, int64_t cz)
+/* Eq. 2 without its 1/(3M) factor: the x-, y- and z-line sums through the
+ * cluster centre c, of M_a = 2 r[a] + 1 voxels along axis a, with offsets
+ * Delta_i = i - (M_a - 1)/2 (Eq. 3).  The centre voxel therefore enters three
+ * times.  (Isotropic: M voxels per line, 3M in all.) */
+static uint64_t cluster_line_sum(const vol_view *v, const int r[3], int64_t cx, int64_t cy, int64_t cz)
 {
-    int M = 2 * r + 1;
     uint64_t s = 0;
-    for (int i = 0; i < M; ++i) {
-        int64_t di = i - (M - 1) / 2;
+    for (int i = 0; i < 2 * r[0] + 1; ++i) {
+        int64_t di = i - r[0];
         s += sample(v, cx + di, cy, cz);
     }
-    for (int i = 0; i < M; ++i) {
-        int64_t di = i - (M - 1) / 2;
+    for (int i = 0; i < 2 * r[1] + 1; ++i) {
+        int64_t di = i - r[1];
         s += sample(v, cx, cy + di, cz);
     }
-    for (int i = 0; i < M; ++i) {
-        int64_t di = i - (M - 1) / 2;
+    for (int i = 0; i < 2 * r[2] + 1; ++i) {
+        int64_t di = i - r[2];
         s += sample(v, cx, cy, cz + di);
     }
     return s;
@@ -89,33 +105,37 @@ static uint64_t cluster_line_sum(const vol_view *v, int r, int64_t cx, int64_t c
 
 /* The paper's filter (section "Our Method"): the average cluster S_0 at the
  * voxel and eight more S_1..S_8 centred at the diagonal offsets (+-d,+-d,+-d);
- * the voxel is replaced by the mean of the nine cluster averages. */
+ * the voxel is replaced by the mean of the nine cluster averages.  Each S_k is
+ * its line sum over the 3M voxels of its three lines (Mx + My + Mz with
+ * per-axis radii), so A = U / (9 * 3M). */
 static uint32_t filter_ours(const vol_view *v, const oracle_params *p, int64_t x, int64_t y, int64_t z)
 {
-    int r = p->radius, d = p->offset, M = 2 * r + 1;
+    int r[3], d[3];
+    axis_extents(p, r, d);
     uint64_t U = cluster_line_sum(v, r, x, y, z);           /* S_0 */
     for (int sz = -1; sz <= 1; sz += 2)
         for (int sy = -1; sy <= 1; sy += 2)
             for (int sx = -1; sx <= 1; sx += 2)
-                U += cluster_line_sum(v, r, x + sx * d, y + sy * d, z + sz * d); /* S_1..S_8 */
-    /* mean of nine averages S_k = L_k / (3M): A = U / (27 M) */
-    uint64_t den = 27ull * (uint64_t)M;
+                U += cluster_line_sum(v, r, x + sx * d[0], y + sy * d[1], z + sz * d[2]); /* S_1..S_8 */
+    uint64_t den = 9ull * (uint64_t)(2 * r[0] + 1 + 2 * r[1] + 1 + 2 * r[2] + 1);
     uint32_t P0 = sample(v, x, y, z);
     if (P0 < p->threshold || U < den * (uint64_t)p->threshold)
         return 0;
     return round_div(U, den);
 }
 
-/* Mean (low-pass) filter, Eq. 4: average over the M^3 cube. */
+/* Mean (low-pass) filter, Eq. 4: average over the M^3 cube (Mx x My x Mz). */
 static uint32_t filter_mean(const vol_view *v, const oracle_params *p, int64_t x, int64_t y, int64_t z)
 {
-    int r = p->radius, M = 2 * r + 1;
-    uint64_t B = 0;
-    for (int k = 0; k < M; ++k)
-        for (int j = 0; j < M; ++j)
-            for (int i = 0; i < M; ++i)
-                B += sample(v, x + i - r, y + j - r, z + k - r);
-    uint64_t n = (uint64_t)M * M * M;
+    int r[3], d[3];
+    axis_extents(p, r, d);
+    uint64_t B = 0, n = 0;
+    for (int k = -r[2]; k <= r[2]; ++k)
+        for (int j = -r[1]; j <= r[1]; ++j)
+            for (int i = -r[0]; i <= r[0]; ++i) {
+                B += sample(v, x + i, y + j, z + k);
+                n += 1;
+            }
     uint32_t P0 = sample(v, x, y, z);
     if (P0 < p->threshold || B < n * (uint64_t)p->threshold)
         return 0;
@@ -126,13 +146,14 @@ static uint32_t filter_mean(const vol_view *v, const oracle_params *p, int64_t x
  * |P_i - P0| <= delta, over the M^3 cube; P0 always qualifies). */
 static uint32_t filter_sigma(const vol_view *v, const oracle_params *p, int64_t x, int64_t y, int64_t z)
 {
-    int r = p->radius, M = 2 * r + 1;
+    int r[3], d[3];
+    axis_extents(p, r, d);
     uint32_t P0 = sample(v, x, y, z);
     uint64_t s = 0, n = 0;
-    for (int k = 0; k < M; ++k)
-        for (int j = 0; j < M; ++j)
-            for (int i = 0; i < M; ++i) {
-                uint32_t Pi = sample(v, x + i - r, y + j - r, z + k - r);
+    for (int k = -r[2]; k <= r[2]; ++k)
+        for (int j = -r[1]; j <= r[1]; ++j)
+            for (int i = -r[0]; i <= r[0]; ++i) {
+                uint32_t Pi = sample(v, x + i, y + j, z + k);
                 int64_t diff = (int64_t)Pi - (int64_t)P0;
                 if (diff < 0)
                     diff = -diff;
@@ -154,13 +175,14 @@ static uint32_t filter_sigma(const vol_view *v, const oracle_params *p, int64_t 
  * compared exactly in integers; then as filter_sigma (mean of the band, gate). */
 static uint32_t filter_sigma_local(const vol_view *v, const oracle_params *p, int64_t x, int64_t y, int64_t z)
 {
-    const int r = p->radius, M = 2 * r + 1;
+    int r[3], dd[3];
+    axis_extents(p, r, dd);
     const uint32_t P0 = sample(v, x, y, z);
-    const unsigned __int128 m = (unsigned __int128)M * M * M;
+    const unsigned __int128 m = (unsigned __int128)(2 * r[0] + 1) * (2 * r[1] + 1) * (2 * r[2] + 1);
     unsigned __int128 S1 = 0, S2 = 0;
-    for (int k = -r; k <= r; ++k)
-        for (int j = -r; j <= r; ++j)
-            for (int i = -r; i <= r; ++i) {
+    for (int k = -r[2]; k <= r[2]; ++k)
+        for (int j = -r[1]; j <= r[1]; ++j)
+            for (int i = -r[0]; i <= r[0]; ++i) {
                 const uint64_t Pi = sample(v, x + i, y + j, z + k);
                 S1 += Pi;
                 S2 += (unsigned __int128)Pi * Pi;
@@ -168,9 +190,9 @@ static uint32_t filter_sigma_local(const vol_view *v, const oracle_params *p, in
     const unsigned __int128 kk = (unsigned __int128)p->sigma_k * p->sigma_k;
     const unsigned __int128 rhs = kk * (m * S2 - S1 * S1);
     uint64_t s = 0, n = 0;
-    for (int k = -r; k <= r; ++k)
-        for (int j = -r; j <= r; ++j)
-            for (int i = -r; i <= r; ++i) {
+    for (int k = -r[2]; k <= r[2]; ++k)
+        for (int j = -r[1]; j <= r[1]; ++j)
+            for (int i = -r[0]; i <= r[0]; ++i) {
                 const uint32_t Pi = sample(v, x + i, y + j, z + k);
                 const unsigned __int128 d = Pi > P0 ? Pi - P0 : P0 - Pi;
                 if (m * m * d * d <= rhs) {
@@ -188,11 +210,13 @@ static uint32_t filter_sigma_local(const vol_view *v, const oracle_params *p, in
  * 0 when nothing qualifies). */
 static uint32_t filter_okada(const vol_view *v, const oracle_params *p, int64_t x, int64_t y, int64_t z)
 {
-    int r = p->radius;
+    int r[3], d[3];
+    axis_extents(p, r, d);
     uint32_t P0 = sample(v, x, y, z);
     uint64_t s = 0, n = 0;
     for (int axis = -1; axis < 3; ++axis) {
-        for (int t = -r; t <= r; ++t) {
+        const int arm = axis < 0 ? 0 : r[axis];
+        for (int t = -arm; t <= arm; ++t) {
             int64_t ox = 0, oy = 0, oz = 0;
             if (axis == -1) {            /* the centre itself, once */
                 if (t != 0)
@@ -226,12 +250,13 @@ static uint32_t filter_okada(const vol_view *v, const oracle_params *p, int64_t 
  * M^3 cube voxels and is evaluated in the fixed point of the weight table). */
 static uint32_t filter_entropy(const vol_view *v, const oracle_params *p, int64_t x, int64_t y, int64_t z)
 {
-    int r = p->radius, M = 2 * r + 1;
+    int r[3], d[3];
+    axis_extents(p, r, d);
     uint64_t E = 0;
-    for (int k = 0; k < M; ++k)
-        for (int j = 0; j < M; ++j)
-            for (int i = 0; i < M; ++i)
-                E += p->entropy_w[sample(v, x + i - r, y + j - r, z + k - r)];
+    for (int k = -r[2]; k <= r[2]; ++k)
+        for (int j = -r[1]; j <= r[1]; ++j)
+            for (int i = -r[0]; i <= r[0]; ++i)
+                E += p->entropy_w[sample(v, x + i, y + j, z + k)];
     uint32_t P0 = sample(v, x, y, z);
     if (P0 < p->threshold)
         return 0;
@@ -251,27 +276,31 @@ static uint32_t filter_entropy(const vol_view *v, const oracle_params *p, int64_
  * filter_ours. */
 static uint32_t filter_ours_variant(const vol_view *v, const oracle_params *p, int64_t x, int64_t y, int64_t z)
 {
-    const int r = p->radius;
-    const int64_t d = p->offset;
-    const uint64_t M = 2 * (uint64_t)r + 1;
-    const uint64_t per = p->filter_id == 5 ? 6 * (uint64_t)r + 1 : M * M * M;   /* voxels per cluster */
+    int r[3], d[3];
+    axis_extents(p, r, d);
+    /* voxels per cluster: the centre and its arms, or the whole box */
+    const uint64_t per = p->filter_id == 5 ? 1 + 2 * (uint64_t)(r[0] + r[1] + r[2])
+                                           : (uint64_t)(2 * r[0] + 1) * (2 * r[1] + 1) * (2 * r[2] + 1);
     uint64_t U = 0;
     for (int c = 0; c < 9; ++c) {
         int64_t cx = x, cy = y, cz = z;
         if (c > 0) {
-            cx += ((c - 1) & 1) ? d : -d;
-            cy += ((c - 1) & 2) ? d : -d;
-            cz += ((c - 1) & 4) ? d : -d;
+            cx += ((c - 1) & 1) ? d[0] : -d[0];
+            cy += ((c - 1) & 2) ? d[1] : -d[1];
+            cz += ((c - 1) & 4) ? d[2] : -d[2];
         }
         if (p->filter_id == 5) {
             U += sample(v, cx, cy, cz);
-            for (int t = 1; t <= r; ++t)
-                U += sample(v, cx - t, cy, cz) + sample(v, cx + t, cy, cz) + sample(v, cx, cy - t, cz) +
-                     sample(v, cx, cy + t, cz) + sample(v, cx, cy, cz - t) + sample(v, cx, cy, cz + t);
+            for (int t = 1; t <= r[0]; ++t)
+                U += sample(v, cx - t, cy, cz) + sample(v, cx + t, cy, cz);
+            for (int t = 1; t <= r[1]; ++t)
+                U += sample(v, cx, cy - t, cz) + sample(v, cx, cy + t, cz);
+            for (int t = 1; t <= r[2]; ++t)
+                U += sample(v, cx, cy, cz - t) + sample(v, cx, cy, cz + t);
         } else {
-            for (int k = -r; k <= r; ++k)
-                for (int j = -r; j <= r; ++j)
-                    for (int i = -r; i <= r; ++i)
+            for (int k = -r[2]; k <= r[2]; ++k)
+                for (int j = -r[1]; j <= r[1]; ++j)
+                    for (int i = -r[0]; i <= r[0]; ++i)
                         U += sample(v, cx + i, cy + j, cz + k);
         }
     }
@@ -309,6 +338,10 @@ int oracle_filter_box(const void *vol, int64_t nx, int64_t ny, int64_t nz, int d
         return -1;
     if (p->filter_id < 0 || p->filter_id > 7 || p->radius < 0)
         return -1;
+    if (p->aniso)
+        for (int a = 0; a < 3; ++a)
+            if (p->rad[a] < 0 || p->off[a] < 0)
+                return -1;
     vol_view v = {vol, nx, ny, nz, dtype};
     int64_t bx = x1 - x0, by = y1 - y0;
     for (int64_t z = z0; z < z1; ++z)
@@ -463,6 +496,10 @@ int oracle_render(const void *vol, int64_t nx, int64_t ny, int64_t nz, int dtype
         return -1;
     if (p->filter_id < 0 || p->filter_id > 7 || p->radius < 0)
         return -1;
+    if (p->aniso)
+        for (int a = 0; a < 3; ++a)
+            if (p->rad[a] < 0 || p->off[a] < 0)
+                return -1;
     int64_t W, H, len;
     if (render_extent(view, nx, ny, nz, &W, &H, &len) != 0)
         return -1;

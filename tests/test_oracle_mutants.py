@@ -1,5 +1,5 @@
 """Plant plausible slips in a copy of the C oracle and check that the pin
-suite (test_oracle_pins.py) rejects every one of them.  The mistakes are planted
+suites (test_oracle_pins.py, test_oracle_aniso.py) reject every one of them.  The mistakes are planted
 on the CPU, in a temporary copy; the oracle in the repository is untouched."""
 import os
 import subprocess
@@ -12,7 +12,7 @@ SRC = os.path.join(ROOT, "oracle", "lnf_oracle.c")
 
 MUTANTS = {
     "drop_z_line": ("s += sample(v, cx, cy, cz + di);", ""),
-    "corner_axis_slip": ("z + sz * d", "z + sy * d"),
+    "corner_axis_slip": ("z + sz * d[2]", "z + sy * d[2]"),
     "truncating_round": ("(2 * a + b) / (2 * b)", "a / b"),
     "gate_strict": ("U < den * (uint64_t)p->threshold", "U <= den * (uint64_t)p->threshold"),
     "sigma_open_band": ("diff <= (int64_t)p->sigma_band", "diff < (int64_t)p->sigma_band"),
@@ -21,9 +21,17 @@ MUTANTS = {
     "clamp_wrong_extent": ("z = clampi(z, 0, v->nz - 1);", "z = clampi(z, 0, v->ny - 1);"),
     "index_transposed": ("(z * v->ny + y) * v->nx + x", "(z * v->nx + y) * v->ny + x"),
     "entropy_ge": ("(int64_t)E > p->entropy_te", "(int64_t)E >= p->entropy_te"),
-    "mean_shifted_cube": ("B += sample(v, x + i - r, y + j - r, z + k - r);",
-                          "B += sample(v, x + i - r, y + j - r, z + k - r + (k == 0));"),
-    "cluster_offset_doubled": ("x + sx * d, y + sy * d", "x + sx * 2 * d, y + sy * d"),
+    "mean_shifted_cube": ("B += sample(v, x + i, y + j, z + k);",
+                          "B += sample(v, x + i, y + j, z + k + (k == 0));"),
+    "cluster_offset_doubled": ("x + sx * d[0], y + sy * d[1]", "x + sx * 2 * d[0], y + sy * d[1]"),
+    # anisotropic forms
+    "axis_radii_rotated": ("r[a] = p->aniso ? p->rad[a] : p->radius;",
+                           "r[a] = p->aniso ? p->rad[(a + 1) % 3] : p->radius;"),
+    "aniso_ours_isotropic_denominator": ("9ull * (uint64_t)(2 * r[0] + 1 + 2 * r[1] + 1 + 2 * r[2] + 1)",
+                                         "27ull * (uint64_t)(2 * r[0] + 1)"),
+    "okada_arm_of_x": ("const int arm = axis < 0 ? 0 : r[axis];", "const int arm = axis < 0 ? 0 : r[0];"),
+    "cross_cluster_y_arm_from_x": ("for (int t = 1; t <= r[1]; ++t)\n                U += sample(v, cx, cy - t, cz)",
+                                   "for (int t = 1; t <= r[0]; ++t)\n                U += sample(v, cx, cy - t, cz)"),
     "sum_of_squares_slip": ("q += (unsigned __int128)P * P;", "q += (unsigned __int128)P * P + (P > 200);"),
     "mean_gate_dropped": ("if (P0 < p->threshold || B < n * (uint64_t)p->threshold)",
                           "if (B < n * (uint64_t)p->threshold)"),
@@ -43,6 +51,7 @@ def test_pins_reject_planted_slip(name, tmp_path):
                            "-o", str(so), str(c)])
     env = dict(os.environ, LNF_ORACLE_SO=str(so))
     res = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
-                          os.path.join(ROOT, "tests", "test_oracle_pins.py")],
+                          os.path.join(ROOT, "tests", "test_oracle_pins.py"),
+                          os.path.join(ROOT, "tests", "test_oracle_aniso.py")],
                          cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
     assert res.returncode != 0, f"planted slip {name} survived the pins:\n{res.stdout[-2000:]}"
