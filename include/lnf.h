@@ -186,6 +186,52 @@ lnf_status lnf_filter_roi(lnf_ctx *ctx, int filter_id, int radius, const void *i
                           int dtype, const int64_t roi_origin[3], const int64_t roi_dims[3], void *out);
 
 /*
+ * Anisotropic voxel spacing.  The paper's volumes are isotropic; for a grid
+ * whose spacing differs per axis every filter takes a radius and a cluster
+ * offset per axis (x, y, z): the cube of M^3 voxels (mean Eq. 4, sigma Eq. 5,
+ * entropy Eq. 7, local sigma) becomes the box of Mx*My*Mz voxels, M_a = 2 r_a + 1;
+ * the Okada cross (Eq. 6) has arm r_a along axis a; a cluster of the paper's
+ * filter (Eq. 2-3) averages its x-, y- and z-lines of Mx, My and Mz voxels (so
+ * A = U / (9 (Mx + My + Mz))) and the diagonal clusters sit at (+-dx, +-dy, +-dz);
+ * the entropy threshold's default kernel has Mx*My*Mz voxels.  Equal axes give
+ * exactly lnf_filter_volume.
+ *
+ * radius: 3 radii in 0..LNF_MAX_RADIUS (host array).  offset: 3 cluster offsets
+ * in 0..8 (host array), or NULL for the context's cluster_offset on every axis.
+ * Other arguments, layout, ownership and errors as lnf_filter_volume.  Jobs
+ * with unequal axes run in the generic kernel.
+ */
+lnf_status lnf_filter_volume_aniso(lnf_ctx *ctx, int filter_id, const int radius[3], const int offset[3],
+                                   const void *in, void *out, const int64_t dims[3], int dtype);
+
+/*
+ * Per-axis radii, in voxels, of a physical extent on a grid of voxel spacing
+ * spacing[3] (x, y, z; same unit as extent): radius[a] = floor(extent /
+ * spacing[a] + 1/2) in IEEE double (round half up).  Host only; no context.
+ * Errors: LNF_EINVAL for a null pointer, extent < 0 or not finite, a spacing
+ * <= 0 or not finite, or a radius above LNF_MAX_RADIUS.
+ */
+lnf_status lnf_spacing_radii(double extent, const double spacing[3], int radius[3]);
+
+/*
+ * float32 volumes.  The paper filters grey levels; a float32 volume is filtered
+ * on 65536 levels spanning its own range, in IEEE single precision with
+ * round-to-nearest at every step (no fused operations):
+ *   lo = min, hi = max over the volume, d = hi - lo;
+ *   level q = floor((v - lo) * (65535 / d) + 1/2)   (every q = 0 when d = 0);
+ *   the 16-bit pipeline (statistics, Otsu T, the filter) runs on the levels;
+ *   out = lo + q * (d / 65535), so a gated voxel becomes lo.
+ * in/out: device float32 buffers of nx*ny*nz values, x-fastest.  radius and
+ * offset as lnf_filter_volume_aniso (equal radii: the paper's isotropic
+ * filter).  Synchronises the stream once (the range is checked on the host).
+ * Errors: LNF_EINVAL for a non-finite value, a range wider than float32 holds,
+ * and as lnf_filter_volume_aniso; LNF_ENOMEM for the level buffers (4 bytes per
+ * voxel, kept by the context); LNF_ECUDA.
+ */
+lnf_status lnf_filter_volume_f32(lnf_ctx *ctx, int filter_id, const int radius[3], const int offset[3],
+                                 const float *in, float *out, const int64_t dims[3]);
+
+/*
  * Image entropy (the paper's Fig. 4 measure) of a volume:
  * H = -sum_v (c_v/N) log2(c_v/N) over its grey-level histogram, accumulated in
  * FP64.  vol is a device buffer; *H is a HOST double.  Synchronises the stream.

@@ -34,7 +34,8 @@ __all__ = [
     "build", "lib", "Config", "stats", "otsu_threshold", "sigma_band", "okada_td_default",
     "log2_fixed", "entropy_weights", "entropy_te_default", "derive_params", "filter_volume",
     "filter_points", "image_entropy", "histogram", "MEAN", "SIGMA", "ENTROPY", "OKADA", "OURS",
-    "FILTER_NAMES", "LOG2_FRAC_BITS", "ENTROPY_W_BITS", "spacing_radii",
+    "FILTER_NAMES", "LOG2_FRAC_BITS", "ENTROPY_W_BITS", "spacing_radii", "quantize_f32", "dequantize_f32",
+    "filter_volume_f32",
 ]
 
 MEAN, SIGMA, ENTROPY, OKADA, OURS = 0, 1, 2, 3, 4
@@ -382,6 +383,49 @@ def filter_points(vol, filter_id, radius, pts, params):
     if rc != 0:
         raise ValueError("oracle_filter_points rejected its arguments")
     return vals
+
+
+# --------------------------------------------------------------------------- float32 volumes
+
+def quantize_f32(vol):
+    """The 65536 grey levels of a float32 volume (a reading: the paper filters
+    grey levels): with lo / hi the volume's min / max and d = hi - lo, level
+    q = floor((v - lo) * (65535 / d) + 1/2), every q = 0 when d = 0.  Each step
+    is one IEEE float32 operation rounded to nearest, in this order.
+    Returns (levels uint16, lo, hi)."""
+    vol = np.ascontiguousarray(vol, dtype=np.float32)
+    if not np.isfinite(vol).all():
+        raise ValueError("float32 volumes must hold finite values")
+    lo, hi = np.float32(vol.min()), np.float32(vol.max())
+    d = np.float32(hi - lo)
+    if not np.isfinite(d):
+        raise ValueError("the range is wider than float32 holds")
+    if d == 0:
+        return np.zeros(vol.shape, np.uint16), lo, hi
+    sc = np.float32(np.float32(65535.0) / d)
+    t = (vol - lo) * sc + np.float32(0.5)
+    assert t.dtype == np.float32
+    return np.minimum(np.floor(t), np.float32(65535.0)).astype(np.uint16), lo, hi
+
+
+def dequantize_f32(q, lo, hi):
+    """value(q) = lo + q * (d / 65535) in float32 (one rounding per operation)."""
+    lo, hi = np.float32(lo), np.float32(hi)
+    step = np.float32(np.float32(hi - lo) / np.float32(65535.0))
+    out = lo + q.astype(np.float32) * step
+    assert out.dtype == np.float32
+    return out
+
+
+def filter_volume_f32(vol, filter_id, radius, cfg=None, offset=None):
+    """A float32 volume: quantised to levels, filtered by the 16-bit oracle
+    (statistics and parameters of the levels), mapped back to float32."""
+    q, lo, hi = quantize_f32(vol)
+    st = stats(q)
+    prm = derive_params(st, radius, cfg)
+    if offset is not None:
+        prm = dict(prm, offset=offset)
+    return dequantize_f32(filter_volume(q, filter_id, radius, params=prm), lo, hi)
 
 
 def render_extent(shape, view):

@@ -17,7 +17,7 @@ import threading
 __all__ = [
     "MEAN", "SIGMA", "ENTROPY", "OKADA", "OURS", "OURS_CROSS7", "OURS_CUBE", "FILTERS", "THRESH_OTSU", "THRESH_FIXED", "THRESH_NONE",
     "TD_AUTO", "TE_AUTO", "TE_PASS_ALL", "LnfError", "load", "build", "Context", "Config", "Job", "Request",
-    "Result", "Params",
+    "Result", "Params", "spacing_radii",
 ]
 
 MEAN, SIGMA, ENTROPY, OKADA, OURS = 0, 1, 2, 3, 4
@@ -139,6 +139,14 @@ _SIGS = {
                                              ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                              ctypes.POINTER(ctypes.c_void_p),
                                              ctypes.POINTER(ctypes.c_double)]),
+    "lnf_filter_volume_aniso": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                               ctypes.POINTER(ctypes.c_int), ctypes.c_void_p, ctypes.c_void_p,
+                                               _i64p, ctypes.c_int]),
+    "lnf_filter_volume_f32": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                             ctypes.POINTER(ctypes.c_int), ctypes.c_void_p, ctypes.c_void_p,
+                                             _i64p]),
+    "lnf_spacing_radii": (ctypes.c_int, [ctypes.c_double, ctypes.POINTER(ctypes.c_double),
+                                         ctypes.POINTER(ctypes.c_int)]),
     "lnf_filter_roi": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p, _i64p,
                                       ctypes.c_int, _i64p, _i64p, ctypes.c_void_p]),
     "lnf_render": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p, _i64p, ctypes.c_int,
@@ -188,6 +196,18 @@ def load(path=None):
                 fn.argtypes = args
             _lib = L
     return _lib
+
+
+def spacing_radii(extent, spacing):
+    """Per-axis radii (x, y, z), in voxels, of a physical extent on a grid of
+    voxel spacing (sx, sy, sz): floor(extent / s_a + 1/2) (lnf_spacing_radii)."""
+    L = load()
+    out = (ctypes.c_int * 3)()
+    sp = (ctypes.c_double * 3)(*[float(v) for v in spacing])
+    rc = L.lnf_spacing_radii(float(extent), sp, out)
+    if rc != OK:
+        raise LnfError(rc, "lnf_spacing_radii: bad extent or spacing, or a radius above the maximum")
+    return tuple(out)
 
 
 def _dims_of(t):
@@ -289,6 +309,37 @@ class Context:
         self._sync_stream()
         self._check(self.lib.lnf_filter_volume(self.h, filter_id, radius, vol.data_ptr(), out.data_ptr(),
                                                _dims_of(vol), _dtype_of(vol)))
+        return out
+
+    def filter_volume_aniso(self, vol, filter_id, radius, offset=None, out=None):
+        """Anisotropic voxel spacing: `radius` and `offset` (None: the context's
+        cluster offset) are per-axis (x, y, z) triples."""
+        import torch
+        _check_dev(vol)
+        if out is None:
+            out = torch.empty_like(vol)
+        rad = (ctypes.c_int * 3)(*[int(r) for r in radius])
+        off = (ctypes.c_int * 3)(*[int(d) for d in offset]) if offset is not None else None
+        self._sync_stream()
+        self._check(self.lib.lnf_filter_volume_aniso(self.h, filter_id, rad, off, vol.data_ptr(), out.data_ptr(),
+                                                     _dims_of(vol), _dtype_of(vol)))
+        return out
+
+    def filter_volume_f32(self, vol, filter_id, radius, offset=None, out=None):
+        """A float32 volume, filtered on 65536 levels spanning its range
+        (lnf_filter_volume_f32); `radius` is r or a per-axis (x, y, z) triple."""
+        import torch
+        _check_dev(vol)
+        if vol.dtype != torch.float32:
+            raise TypeError("filter_volume_f32 takes a float32 volume")
+        if out is None:
+            out = torch.empty_like(vol)
+        r3 = tuple(radius) if isinstance(radius, (tuple, list)) else (radius,) * 3
+        rad = (ctypes.c_int * 3)(*[int(r) for r in r3])
+        off = (ctypes.c_int * 3)(*[int(d) for d in offset]) if offset is not None else None
+        self._sync_stream()
+        self._check(self.lib.lnf_filter_volume_f32(self.h, filter_id, rad, off, vol.data_ptr(), out.data_ptr(),
+                                                   _dims_of(vol)))
         return out
 
     def filter_multi(self, vol, filter_ids, radius, outs=None, entropy=True, H=None):

@@ -8,6 +8,7 @@
 #include "lnf_ctx.h"
 
 #include <algorithm>
+#include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstdlib>
@@ -228,7 +229,8 @@ extern "C" lnf_status lnf_create(const lnf_config *cfg_in, lnf_ctx **out)
             cudaMalloc(&ctx->d_err, sizeof(u32)) != cudaSuccess ||
             cudaMalloc(&ctx->d_counter, sizeof(u32) * 16) != cudaSuccess ||
             cudaMalloc(&ctx->d_ent_part, sizeof(double) * LNF_ENT_SPLIT * LNF_MAX_ENT) != cudaSuccess ||
-            cudaMalloc(&ctx->d_ent_done, sizeof(u32) * LNF_MAX_ENT) != cudaSuccess) {
+            cudaMalloc(&ctx->d_ent_done, sizeof(u32) * LNF_MAX_ENT) != cudaSuccess ||
+            cudaMalloc(&ctx->d_range, sizeof(u32) * 4) != cudaSuccess) {
             s = LNF_ENOMEM;
             break;
         }
@@ -275,6 +277,8 @@ extern "C" void lnf_destroy(lnf_ctx *ctx)
     cudaFree(ctx->d_err);
     cudaFree(ctx->d_counter);
     cudaFree(ctx->pitched);
+    cudaFree(ctx->f32_lv);
+    cudaFree(ctx->d_range);
     for (cudaEvent_t e : ctx->filter_done)
         cudaEventDestroy(e);
     if (ctx->copy_stream)
@@ -422,10 +426,21 @@ lnf_status lnf_analyze(lnf_ctx *ctx, const void *in, const int64_t dims[3], int 
 // Fill job `idx` of the pack; encodes a TMA map when the volume allows it.
 lnf_status lnf_make_job(lnf_ctx *ctx, FilterPack &pk, int idx, int filter, int radius, const void *in, void *out,
                         const int64_t dims[3], int dtype, const int64_t *roi_o, const int64_t *roi_d,
-                        const VolScratch &vs, u64 *out_hist, int64_t pitch)
+                        const VolScratch &vs, u64 *out_hist, int64_t pitch, const int *rad3, const int *off3)
 {
     FilterJob &j = pk.jobs[idx];
     std::memset(&j, 0, sizeof j);
+    int offset = ctx->cfg.cluster_offset;
+    for (int a = 0; a < 3; ++a) {
+        j.rad[a] = rad3 ? rad3[a] : radius;
+        j.off[a] = off3 ? off3[a] : offset;
+    }
+    if (rad3 || off3) {
+        // the halo (and the TMA box) cover the largest reach of any axis
+        j.aniso = 1;
+        radius = std::max(j.rad[0], std::max(j.rad[1], j.rad[2]));
+        offset = std::max(j.off[0], std::max(j.off[1], j.off[2]));
+    }
     j.in = in;
     j.out = out;
     j.nx = (int)dims[0];
@@ -447,7 +462,7 @@ lnf_status lnf_make_job(lnf_ctx *ctx, FilterPack &pk, int idx, int filter, int r
     j.dtype = dtype;
     j.filter = filter;
     j.radius = radius;
-    j.offset = ctx->cfg.cluster_offset;
+    j.offset = offset;
     j.prm = vs.prm;
     j.lut = vs.lut;
     j.out_hist = out_hist;
@@ -456,7 +471,7 @@ lnf_status lnf_make_job(lnf_ctx *ctx, FilterPack &pk, int idx, int filter, int r
     const size_t es = esize(dtype);
     if (ctx->encode && !ctx->no_tma && (reinterpret_cast<uintptr_t>(in) & 15) == 0 && ((size_t)j.pitch * es) % 16 == 0) {
         unsigned bw = 0, bh = 0;
-        lnf_filter_box(filter, radius, ctx->cfg.cluster_offset, dtype, &bw, &bh);
+        lnf_filter_box(filter, radius, offset, dtype, &bw, &bh);
         if (bw <= 256 && bh <= 256) {
             cuuint64_t gdim[3] = {(cuuint64_t)dims[0], (cuuint64_t)dims[1], (cuuint64_t)dims[2]};
             cuuint64_t gstr[2] = {(cuuint64_t)((size_t)j.pitch * es), (cuuint64_t)((size_t)j.pitch * dims[1] * es)};
@@ -571,12 +586,12 @@ static lnf_status stage_input(lnf_ctx *ctx, const void *in, const int64_t dims[3
 // Run one filter job on an analysed volume, through the fastest kernel that covers it.
 lnf_status lnf_run_one(lnf_ctx *ctx, int filter, int radius, const void *in, void *out, const int64_t dims[3],
                        int dtype, const int64_t *roi_o, const int64_t *roi_d, const VolScratch &vs,
-                       u64 *out_hist, cudaStream_t stream, int64_t pitch)
+                       u64 *out_hist, cudaStream_t stream, int64_t pitch, const int *rad3, const int *off3)
 {
     FilterPack &pk = ctx->pack;
     pk.n_jobs = 1;
-    lnf_status s =
-        lnf_make_job(ctx, pk, 0, filter, radius, in, out, dims, dtype, roi_o, roi_d, vs, out_hist, pitch);
+    lnf_status s = lnf_make_job(ctx, pk, 0, filter, radius, in, out, dims, dtype, roi_o, roi_d, vs, out_hist,
+                                pitch, rad3, off3);
     if (s != LNF_OK)
         return s;
     if (lnf_fault(ctx, FAULT_LAUNCH))
@@ -650,6 +665,64 @@ extern "C" lnf_status lnf_filter_roi(lnf_ctx *ctx, int filter_id, int radius, co
         return s;
     return lnf_run_one(ctx, filter_id, radius, in, out, dims, dtype, roi_origin, roi_dims, ctx->vs, nullptr,
                        ctx->stream);
+}
+
+extern "C" lnf_status lnf_filter_volume_aniso(lnf_ctx *ctx, int filter_id, const int radius[3],
+                                              const int offset[3], const void *in, void *out,
+                                              const int64_t dims[3], int dtype)
+{
+    LNF_RANGE("lnf_filter_volume_aniso");
+    if (!ctx)
+        return LNF_EINVAL;
+    if (!radius)
+        return lnf_fail(ctx, LNF_EINVAL, "null radius array");
+    int rad[3], off[3];
+    for (int a = 0; a < 3; ++a) {
+        rad[a] = radius[a];
+        off[a] = offset ? offset[a] : ctx->cfg.cluster_offset;
+        if (rad[a] < 0 || rad[a] > LNF_MAX_RADIUS)
+            return lnf_fail(ctx, LNF_EINVAL, "radius[%d] = %d not in 0..%d", a, rad[a], LNF_MAX_RADIUS);
+        if (off[a] < 0 || off[a] > 8)
+            return lnf_fail(ctx, LNF_EINVAL, "offset[%d] = %d not in 0..8", a, off[a]);
+    }
+    const bool iso = rad[0] == rad[1] && rad[1] == rad[2] && off[0] == ctx->cfg.cluster_offset &&
+                     off[1] == off[0] && off[2] == off[0];
+    if (iso)
+        return lnf_filter_volume(ctx, filter_id, rad[0], in, out, dims, dtype);
+    lnf_status s;
+    if ((s = check_filter(ctx, filter_id, rad[0])) != LNF_OK)
+        return s;
+    if ((s = lnf_check_volume(ctx, in, dims, dtype)) != LNF_OK)
+        return s;
+    if (!out)
+        return lnf_fail(ctx, LNF_EINVAL, "null output pointer");
+    const size_t bytes = nvox(dims) * esize(dtype);
+    if (overlaps(in, bytes, out, bytes))
+        return lnf_fail(ctx, LNF_EINVAL, "input and output overlap");
+    if ((s = lnf_analyze(ctx, in, dims, dtype, ctx->vs, ctx->stream)) != LNF_OK)
+        return s;
+    const int rmax = std::max(rad[0], std::max(rad[1], rad[2]));
+    return lnf_run_one(ctx, filter_id, rmax, in, out, dims, dtype, nullptr, nullptr, ctx->vs, nullptr,
+                       ctx->stream, 0, rad, off);
+}
+
+extern "C" lnf_status lnf_spacing_radii(double extent, const double spacing[3], int radius[3])
+{
+    if (!spacing || !radius || !(extent >= 0.0) || !std::isfinite(extent))
+        return LNF_EINVAL;
+    int out[3];
+    for (int a = 0; a < 3; ++a) {
+        const double s = spacing[a];
+        if (!(s > 0.0) || !std::isfinite(s))
+            return LNF_EINVAL;
+        const double q = std::floor(extent / s + 0.5);
+        if (!(q <= (double)LNF_MAX_RADIUS))
+            return LNF_EINVAL;
+        out[a] = (int)q;
+    }
+    for (int a = 0; a < 3; ++a)
+        radius[a] = out[a];
+    return LNF_OK;
 }
 
 // lnf_filter_multi, recording `after[i]` on the context stream once filter i
@@ -863,5 +936,51 @@ extern "C" lnf_status lnf_get_params(lnf_ctx *ctx, lnf_params *out, uint32_t *we
     u32 err = 0;
     if (cudaMemcpy(&err, ctx->d_err, sizeof err, cudaMemcpyDeviceToHost) == cudaSuccess && err)
         return lnf_fail(ctx, LNF_ETIMEOUT, "a bounded device wait gave up (code %u)", err);
+    return LNF_OK;
+}
+
+extern "C" lnf_status lnf_filter_volume_f32(lnf_ctx *ctx, int filter_id, const int radius[3], const int offset[3],
+                                           const float *in, float *out, const int64_t dims[3])
+{
+    LNF_RANGE("lnf_filter_volume_f32");
+    if (!ctx)
+        return LNF_EINVAL;
+    lnf_status s;
+    if (!radius)
+        return lnf_fail(ctx, LNF_EINVAL, "null radius array");
+    if ((s = check_filter(ctx, filter_id, 0)) != LNF_OK)
+        return s;
+    if ((s = lnf_check_volume(ctx, in, dims, LNF_U16)) != LNF_OK)
+        return s;
+    if (!out)
+        return lnf_fail(ctx, LNF_EINVAL, "null output pointer");
+    const u64 n = nvox(dims);
+    if (overlaps(in, n * 4, out, n * 4))
+        return lnf_fail(ctx, LNF_EINVAL, "input and output overlap");
+    cudaStream_t st = ctx->stream;
+    // the range, checked on the host: every value finite, the span finite
+    CK(lnf_launch_f32_range(in, n, ctx->d_range, ctx->num_sms, st));
+    u32 rg[4];
+    CK(cudaMemcpyAsync(rg, ctx->d_range, sizeof rg, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (rg[2] != 0)
+        return lnf_fail(ctx, LNF_EINVAL, "the volume holds %u non-finite values", rg[2]);
+    auto unkey = [](u32 k) {
+        const u32 b = (k & 0x80000000u) ? (k & 0x7FFFFFFFu) : ~k;
+        float f;
+        std::memcpy(&f, &b, sizeof f);
+        return f;
+    };
+    const float lo = unkey(rg[0]), hi = unkey(rg[1]);
+    const float span = hi - lo;
+    if (!std::isfinite(span))
+        return lnf_fail(ctx, LNF_EINVAL, "the volume's range [%g, %g] is wider than float32 can hold", lo, hi);
+    if ((s = ensure_stage(ctx, &ctx->f32_lv, &ctx->f32_lv_cap, (size_t)n * 4)) != LNF_OK)
+        return s;
+    uint16_t *lv_in = static_cast<uint16_t *>(ctx->f32_lv), *lv_out = lv_in + n;
+    CK(lnf_launch_f32_quantize(in, n, ctx->d_range, lv_in, ctx->num_sms, st));
+    if ((s = lnf_filter_volume_aniso(ctx, filter_id, radius, offset, lv_in, lv_out, dims, LNF_U16)) != LNF_OK)
+        return s;
+    CK(lnf_launch_f32_dequantize(lv_out, n, ctx->d_range, out, ctx->num_sms, st));
     return LNF_OK;
 }

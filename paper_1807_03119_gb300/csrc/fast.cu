@@ -781,7 +781,7 @@ lnf_status lnf_fast_dispatch(lnf_ctx *ctx, const FilterJob &job, const CUtensorM
                              int *handled, u32 *counter)
 {
     *handled = 0;
-    if (!tmap || !lnf_fast_covers(job.filter, job.radius, job.offset))
+    if (!tmap || job.aniso || !lnf_fast_covers(job.filter, job.radius, job.offset))
         return LNF_OK;
     if (job.filter != LNF_OURS)
         return lnf_fast2_dispatch(ctx, job, tmap, stream, handled, counter);

@@ -48,8 +48,13 @@ __host__ __device__ inline Geo make_geo(int h, int esize)
     return g;
 }
 
-// the paper's filter and its cluster-layout variants reach r past the cluster centres at offset d
-__host__ __device__ inline int job_halo(int filter, int r, int d) { return filter >= 4 ? r + d : r; }
+// the paper's filter and its cluster-layout variants reach r past the cluster
+// centres at offset d (anisotropic jobs: the largest radius and offset, a bound
+// on the reach along every axis)
+__host__ __device__ inline int job_halo(int filter, int r, int d)
+{
+    return (filter >= 4 && filter <= 6) ? r + d : r;
+}
 
 __device__ __forceinline__ int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
 
@@ -194,7 +199,8 @@ __device__ void process_item(const FilterJob &J, const CUtensorMap *tmap, int it
 
     // parameters of this job
     const DevParams &P = *J.prm;
-    const StepParams sp = make_step_params(P, J.radius, J.offset, J.lut);
+    const StepParams sp = J.aniso ? make_step_params3(P, J.rad, J.off, J.lut)
+                                  : make_step_params(P, J.radius, J.offset, J.lut);
     // stage loader for plain loads
     auto load_plane_plain = [&](int p, T *dst) {
         const int z = clampi(z0 - h + p, 0, J.nz - 1);

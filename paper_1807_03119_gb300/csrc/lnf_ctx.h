@@ -96,6 +96,10 @@ struct lnf_ctx {
     // plain calls: a copy of an input TMA cannot address, rows padded to 16 bytes
     void *pitched = nullptr;
     size_t pitched_cap = 0;
+    // float32 volumes: the level volumes (input and output, 16-bit) and the range word
+    void *f32_lv = nullptr;
+    size_t f32_lv_cap = 0;
+    u32 *d_range = nullptr;
     // batched graph cache
     std::vector<BatchEntry *> batches;   // owned; freed by lnf_batch_cache_clear
     // autotuner choice for batched launches (0 = not tuned yet)
@@ -133,10 +137,13 @@ ParamCfg lnf_param_cfg(const lnf_config &c);
 lnf_status lnf_scratch_pool(lnf_ctx *ctx, size_t n);
 lnf_status lnf_analyze(lnf_ctx *ctx, const void *in, const int64_t dims[3], int dtype, VolScratch &vs,
                        cudaStream_t stream);
-// `pitch`: the input's row stride in elements (0: dense rows, = dims[0])
+// `pitch`: the input's row stride in elements (0: dense rows, = dims[0]);
+// `rad3` / `off3`: per-axis radii and cluster offsets (x, y, z) of an
+// anisotropic job (null: `radius` and the context's offset on every axis)
 lnf_status lnf_make_job(lnf_ctx *ctx, FilterPack &pk, int idx, int filter, int radius, const void *in, void *out,
                         const int64_t dims[3], int dtype, const int64_t *roi_o, const int64_t *roi_d,
-                        const VolScratch &vs, u64 *out_hist, int64_t pitch = 0);
+                        const VolScratch &vs, u64 *out_hist, int64_t pitch = 0, const int *rad3 = nullptr,
+                        const int *off3 = nullptr);
 // 3D TMA map of a volume with row stride `pitch` elements, box {box_w, box_h, 1};
 // false when the volume does not meet TMA's alignment rules or encoding fails
 bool lnf_encode_box(lnf_ctx *ctx, const void *in, int nx, int ny, int nz, int pitch, int dtype, unsigned box_w,
@@ -145,7 +152,8 @@ lnf_status lnf_run_pack(lnf_ctx *ctx, FilterPack &pk, int persistent, cudaStream
 lnf_status lnf_run_pack_counter(lnf_ctx *ctx, FilterPack &pk, int persistent, cudaStream_t stream, u32 *counter);
 lnf_status lnf_run_one(lnf_ctx *ctx, int filter, int radius, const void *in, void *out, const int64_t dims[3],
                        int dtype, const int64_t *roi_o, const int64_t *roi_d, const VolScratch &vs,
-                       u64 *out_hist, cudaStream_t stream, int64_t pitch = 0);
+                       u64 *out_hist, cudaStream_t stream, int64_t pitch = 0, const int *rad3 = nullptr,
+                       const int *off3 = nullptr);
 // Row length in bytes of the padded copy of an input TMA cannot address (0: the
 // input itself is addressable: 16-byte-aligned base and row length)
 size_t lnf_pitched_row(const void *in, const int64_t dims[3], int dtype);
@@ -170,6 +178,12 @@ lnf_status lnf_fast2_box(lnf_ctx *ctx, const FilterJob &job, cudaStream_t stream
 cudaError_t lnf_launch_render(const void *vol, const int64_t dims[3], int64_t pitch, int dtype, int view,
                               int filter, int radius, int offset, const DevParams *prm, const u32 *lut,
                               unsigned char *image, int *depth, u32 *value, cudaStream_t st);
+// f32.cu: range (min key, max key, non-finite count), quantisation to and from 65536 levels
+cudaError_t lnf_launch_f32_range(const float *in, u64 n, u32 *range, int num_sms, cudaStream_t st);
+cudaError_t lnf_launch_f32_quantize(const float *in, u64 n, const u32 *range, uint16_t *q, int num_sms,
+                                    cudaStream_t st);
+cudaError_t lnf_launch_f32_dequantize(const uint16_t *q, u64 n, const u32 *range, float *out, int num_sms,
+                                      cudaStream_t st);
 // batch.cu
 void lnf_batch_cache_clear(lnf_ctx *ctx);
 // serve.cu

@@ -59,8 +59,11 @@ struct FilterJob {
     int bx, by, bz;             // ROI dims (= output dims)
     int dtype;                  // 0 u8, 1 u16
     int filter;                 // lnf_filter_id
-    int radius;
-    int offset;                 // cluster offset d
+    int radius;                 // r (anisotropic jobs: the largest of rad[])
+    int offset;                 // cluster offset d (anisotropic jobs: the largest of off[])
+    int aniso;                  // 1: per-axis radii rad[] and offsets off[] (x, y, z)
+    int rad[3];
+    int off[3];
     const DevParams *prm;
     const u32 *lut;             // entropy weights, levels entries
     u64 *out_hist;              // output histogram (levels entries) or null

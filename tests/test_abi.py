@@ -74,3 +74,29 @@ def test_fault_spec_is_checked_before_any_device_call(libpath, monkeypatch, spec
     h = ctypes.c_void_p()
     assert lib.lnf_create(None, ctypes.byref(h)) == 1
     assert not h.value
+
+
+def test_spacing_radii_match_the_oracle(libpath):
+    """lnf_spacing_radii (host code of the library, no device call) against the
+    oracle's own rounding of extent / spacing, on random and half-way cases."""
+    import ctypes
+    import random
+    import oracle
+    try:
+        lib = ctypes.CDLL(libpath)
+    except OSError as e:
+        pytest.skip(f"cannot dlopen: {e}")
+    lib.lnf_spacing_radii.argtypes = [ctypes.c_double, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)]
+    rng = random.Random(5)
+    cases = [(1.5, (1.0, 3.0, 0.5)), (2.5, (1.0, 1.0, 1.0)), (0.0, (1.0, 2.0, 3.0))]
+    cases += [(rng.uniform(0, 6), tuple(rng.uniform(0.3, 4.0) for _ in range(3))) for _ in range(500)]
+    for extent, spacing in cases:
+        out = (ctypes.c_int * 3)()
+        rc = lib.lnf_spacing_radii(extent, (ctypes.c_double * 3)(*spacing), out)
+        want = oracle.spacing_radii(extent, spacing)
+        if max(want) > 8:
+            assert rc == 1
+        else:
+            assert rc == 0 and tuple(out) == want, (extent, spacing)
+    for bad in ((1.0, (0.0, 1.0, 1.0)), (-1.0, (1.0, 1.0, 1.0)), (float("inf"), (1.0, 1.0, 1.0))):
+        assert lib.lnf_spacing_radii(bad[0], (ctypes.c_double * 3)(*bad[1]), (ctypes.c_int * 3)()) == 1
