@@ -285,7 +285,8 @@ def main():
     ap.add_argument("--impl", default="lnf", choices=["lnf", "reference"])
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--mode", default="plain", choices=["plain", "batched", "served", "render", "variants"],
+    ap.add_argument("--mode", default="plain",
+                    choices=["plain", "batched", "served", "render", "variants", "spacing"],
                     help="plain: the 512^3 five-filter step (default); batched / served: the delivery forms")
     ap.add_argument("--duration", type=float, default=10.0, help="served: seconds of Poisson arrivals")
     ap.add_argument("--rate", type=float, default=200.0, help="served: requests per second")
@@ -319,6 +320,8 @@ def main():
         return run_render(args)
     if args.mode == "variants":
         return run_variants(args)
+    if args.mode == "spacing":
+        return run_spacing(args)
 
     import numpy as np
     import torch
@@ -712,6 +715,94 @@ def run_variants(args):
             "value": res["ours_cube"]["gvox_s"], "unit": UNIT, "higher_is_better": True, "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "dtype": "u16", "data": "synthetic",
             "config": {"workload": WORKLOAD, "radius": RADIUS}, "filters": res}
+    print(json.dumps(line))
+    ctx.close()
+
+
+def run_spacing(args):
+    """Anisotropic voxel spacing and float32 volumes on the 512^3 phantom.
+    (a) The uint16 phantom read as a grid of spacing (1, 1, 2) (slices twice as
+    thick as the in-plane pixels): each filter at the radii of a 2-voxel extent,
+    (2, 2, 1), through lnf_filter_volume_aniso.  (b) The phantom as float32
+    values (v / 4 - 1000, exact in float32): the paper's filter at r = 2 through
+    lnf_filter_volume_f32.  Device ms per call (events around the whole call:
+    statistics, parameters, every kernel) and per kernel (the library's
+    profile), GVoxel/s and HBM fractions; the oracle timed beside each on a
+    bounded sample (2 of the 512 planes, scaled; float32: its whole-volume
+    quantisation, statistics and parameters plus the sampled filter)."""
+    import numpy as np
+    import torch
+    import oracle
+    import phantoms
+    import paper_1807_03119_gb300 as lnf
+    from paper_1807_03119_gb300 import builder
+    builder.build()
+    lnf.load()
+    vol = phantoms.P2()
+    t = torch.from_numpy(vol).cuda()
+    out = torch.empty_like(t)
+    ctx = lnf.Context()
+    hbm = peaks()["hbm_gbs"]
+    radii = lnf.spacing_radii(2.0, (1.0, 1.0, 2.0))
+    sample = 2
+    st = oracle.stats(vol)
+
+    def timed(call):
+        for _ in range(args.warmup):
+            call()
+        torch.cuda.synchronize()
+        ctx.profile(True)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.steps):
+            call()
+        e1.record()
+        torch.cuda.synchronize()
+        kern, _ = ctx.profile_read()
+        ctx.profile(False)
+        return e0.elapsed_time(e1) / args.steps, {k: v[1] / v[0] for k, v in kern.items()}
+
+    aniso = {}
+    for name in FILTER_NAMES:
+        f = lnf.FILTERS[name]
+        ms, kern = timed(lambda: ctx.filter_volume_aniso(t, f, radii, out=out))
+        kms = kern["filter:" + name]
+        prm = oracle.derive_params(st, radii)
+        c0 = time.perf_counter()
+        oracle.filter_volume(vol, f, radii, params=prm, roi=(0, 0, 0, DIMS[0], DIMS[1], sample))
+        cpu_ms = (time.perf_counter() - c0) * 1e3 * DIMS[2] / sample
+        aniso[name] = {"ms_per_call": ms, "filter_kernel_ms": kms, "gvox_s": N_VOX / (ms / 1e3) / 1e9,
+                       "filter_hbm_frac": N_VOX * ES * 2 / (kms / 1e3) / 1e9 / hbm,
+                       "oracle_ms": cpu_ms}
+    vf = (vol.astype(np.float32) / np.float32(4.0) - np.float32(1000.0)).astype(np.float32)
+    tf = torch.from_numpy(vf).cuda()
+    of = torch.empty_like(tf)
+    ms, kern = timed(lambda: ctx.filter_volume_f32(tf, lnf.OURS, RADIUS, out=of))
+    per_kernel = {}
+    for k, b in (("f32_range", 4), ("f32_quantize", 6), ("f32_dequantize", 6), ("filter:ours", 4)):
+        if k in kern:
+            per_kernel[k] = {"ms": kern[k], "gb_s": N_VOX * b / (kern[k] / 1e3) / 1e9,
+                             "hbm_frac": N_VOX * b / (kern[k] / 1e3) / 1e9 / hbm, "bytes_per_voxel": b}
+    c0 = time.perf_counter()
+    q, lo, hi = oracle.quantize_f32(vf)
+    prm = oracle.derive_params(oracle.stats(q), RADIUS)
+    lv = oracle.filter_volume(q, oracle.OURS, RADIUS, params=prm, roi=(0, 0, 0, DIMS[0], DIMS[1], sample))
+    oracle.dequantize_f32(lv, lo, hi)
+    c1 = time.perf_counter()
+    oracle.filter_volume(q, oracle.OURS, RADIUS, params=prm, roi=(0, 0, 0, DIMS[0], DIMS[1], sample))
+    filt_s = time.perf_counter() - c1
+    cpu_ms = ((c1 - c0) - filt_s + filt_s * DIMS[2] / sample) * 1e3
+    f32 = {"ms_per_call": ms, "gvox_s": N_VOX / (ms / 1e3) / 1e9,
+           "ideal_bytes_per_voxel": 8, "ideal_hbm_frac": N_VOX * 8 / (ms / 1e3) / 1e9 / hbm,
+           "kernels": per_kernel, "oracle_ms": cpu_ms}
+    line = {"metric": "anisotropic spacing (5 filters) and float32 (paper's filter), 512^3, GVoxel/s",
+            "mode": "spacing", "value": f32["gvox_s"], "unit": UNIT, "higher_is_better": True, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "dtype": "u16 / f32", "data": "synthetic",
+            "config": {"workload": "512x512x512 insect-like phantom: uint16 on a (1, 1, 2) grid at the radii "
+                                   "of a 2-voxel extent; float32 copy v / 4 - 1000, paper's filter r = 2",
+                       "radii": list(radii), "oracle_sample": f"{sample} of {DIMS[2]} planes, scaled, 1 host thread"},
+            "aniso": aniso, "f32": f32}
     print(json.dumps(line))
     ctx.close()
 

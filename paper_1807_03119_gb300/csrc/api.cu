@@ -959,7 +959,9 @@ extern "C" lnf_status lnf_filter_volume_f32(lnf_ctx *ctx, int filter_id, const i
         return lnf_fail(ctx, LNF_EINVAL, "input and output overlap");
     cudaStream_t st = ctx->stream;
     // the range, checked on the host: every value finite, the span finite
+    int rec = lnf_prof_begin(ctx, st);
     CK(lnf_launch_f32_range(in, n, ctx->d_range, ctx->num_sms, st));
+    lnf_prof_end(ctx, rec, "f32_range", st, 2);
     u32 rg[4];
     CK(cudaMemcpyAsync(rg, ctx->d_range, sizeof rg, cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
@@ -978,9 +980,13 @@ extern "C" lnf_status lnf_filter_volume_f32(lnf_ctx *ctx, int filter_id, const i
     if ((s = ensure_stage(ctx, &ctx->f32_lv, &ctx->f32_lv_cap, (size_t)n * 4)) != LNF_OK)
         return s;
     uint16_t *lv_in = static_cast<uint16_t *>(ctx->f32_lv), *lv_out = lv_in + n;
+    rec = lnf_prof_begin(ctx, st);
     CK(lnf_launch_f32_quantize(in, n, ctx->d_range, lv_in, ctx->num_sms, st));
+    lnf_prof_end(ctx, rec, "f32_quantize", st, 1);
     if ((s = lnf_filter_volume_aniso(ctx, filter_id, radius, offset, lv_in, lv_out, dims, LNF_U16)) != LNF_OK)
         return s;
+    rec = lnf_prof_begin(ctx, st);
     CK(lnf_launch_f32_dequantize(lv_out, n, ctx->d_range, out, ctx->num_sms, st));
+    lnf_prof_end(ctx, rec, "f32_dequantize", st, 1);
     return LNF_OK;
 }
