@@ -70,17 +70,23 @@ def alu_peak_tops(sm_mhz):
 
 
 # algorithmic work per launch of each kernel kind on this workload
-def algorithmic(kind):
+def algorithmic(kind, n_pass, hbm_gbs, alu_tops):
+    """(bound, work) of one launch: HBM bytes, or integer ALU operations where
+    those take longer at peak.  Sigma and Okada test every tap of a voxel whose
+    own value passes the gate (P0 >= T) -- four operations per tap: subtract,
+    compare, add value, add count -- and nothing for the others, whose output is
+    0 whatever their band: their ALU work is 4 x taps x n_pass."""
     M3 = (2 * RADIUS + 1) ** 3
     if kind == "stats":
         return "hbm", N_VOX * ES
     if kind.startswith("filter:"):
         f = kind.split(":")[1]
-        if f == "sigma":   # per tap: subtract, compare, add value, add count
-            return "alu", N_VOX * 4 * M3
-        if f == "okada":   # per tap of the 6r+1 cross: same four operations
-            return "alu", N_VOX * 4 * (6 * RADIUS + 1)
-        return "hbm", N_VOX * ES * 2   # read the input once, write the output once
+        hbm = N_VOX * ES * 2   # read the input once, write the output once
+        if f in ("sigma", "okada"):
+            alu = 4 * (M3 if f == "sigma" else 6 * RADIUS + 1) * n_pass
+            if alu / (alu_tops * 1e12) > hbm / (hbm_gbs * 1e9):
+                return "alu", alu
+        return "hbm", hbm
     return None, None
 
 
@@ -411,9 +417,12 @@ def main():
 
     pk = peaks()
     sm_mhz = pk["sm_max_mhz"]
+    # voxels whose own value passes the gate: the ones sigma and Okada evaluate
+    T = ctx.params()["threshold"]
+    n_pass = int(np.count_nonzero(vol >= T))
     rooflines = {}
     for kind, (n, tot) in kern.items():
-        bound, work = algorithmic(kind)
+        bound, work = algorithmic(kind, n_pass, pk["hbm_gbs"], alu_peak_tops(sm_mhz))
         if bound is None or n == 0:
             continue
         avg_s = tot / n / 1e3
@@ -428,6 +437,8 @@ def main():
             rooflines[kind] = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "Tops/s",
                                "frac": ach / peak, "avg_ms": tot / n, "traffic": recorded_traffic(kind),
                                "hbm_gbs": N_VOX * ES * 2 / avg_s / 1e9}
+        if kind in ("filter:sigma", "filter:okada"):
+            rooflines[kind]["gated_voxels"] = n_pass
     dom = max((k for k in rooflines), key=lambda k: kern[k][1]) if rooflines else None
     roof = dict(rooflines[dom], kernel=dom) if dom else None
     if roof:

@@ -210,10 +210,21 @@ constexpr int kBoxWin = 2048;        // box kernel (entropy): histogram / weight
 template <typename T, int R, bool ENT, bool MASK>
 __device__ void box_items(const Args2 &a, const CUtensorMap *tmap, unsigned char *smem, int *s_item, int *s_abort,
                           Hist2 &hist, const u32 *lut_sh, u32 lut_base);
-// tap kernel body (fast2_tap.cu): sigma and Okada
+// tap kernel (fast2_tap.cu): the taps of one voxel, and the most voxels with
+// P0 >= T a block lists per step (beyond it every warp takes the dense form,
+// which tests every tap of all its voxels while reusing each loaded row)
+template <int R, int FILTER>
+struct TapCoop {
+    static constexpr int TAPS = FILTER == LNF_SIGMA ? (2 * R + 1) * (2 * R + 1) * (2 * R + 1) : 6 * R + 1;
+    static constexpr int PER_LANE = (TAPS + 31) / 32;
+    static constexpr int CAP = 1024;
+    static constexpr int BYTES = CAP * 2 + 64;   // the list and the warps' counts
+};
+// tap kernel body (fast2_tap.cu): sigma and Okada; `wl`: the block's candidate
+// list (TapCoop::CAP 16-bit entries) followed by one 32-bit count per warp
 template <typename T, int R, int FILTER, bool MASK>
 __device__ void tap_items(const Args2 &a, const CUtensorMap *tmap, unsigned char *smem, int *s_item, int *s_abort,
-                          Hist2 &hist, const u32 *recip);
+                          Hist2 &hist, const u32 *recip, uint16_t *wl);
 
 // ------------------------------------------------------------------ kernels
 
@@ -227,7 +238,8 @@ struct K2Smem {
     static constexpr int NTAB = (2 * R + 1) * (2 * R + 1) * (2 * R + 1) + 1;   // counts 0 .. M^3
     static constexpr int LUTB = FILTER == LNF_ENTROPY ? LWIN * 4 : (BOX ? 0 : ((NTAB * 4 + 15) / 16) * 16);
     static constexpr int MAIN = G::RING + (BOX ? G::BZ : 0) + G::NP * 8;
-    static constexpr int TOTAL = 128 + MAIN + 64 + HISTB + LUTB;
+    static constexpr int COOPB = BOX ? 0 : TapCoop<R, FILTER>::BYTES;
+    static constexpr int TOTAL = 128 + MAIN + 64 + HISTB + LUTB + COOPB;
 };
 
 // MASK: masked per-voxel stores (a region of interest, an odd width), else dense
@@ -242,6 +254,7 @@ __global__ void __launch_bounds__(kThreads, (K2Smem<T, R, FILTER>::BOX && R > 2)
     __shared__ int s_item, s_abort;
     u32 *hsh = reinterpret_cast<u32 *>(smem + S::MAIN + 64);
     u32 *lut_sh = reinterpret_cast<u32 *>(smem + S::MAIN + 64 + S::HISTB);
+    uint16_t *wl = reinterpret_cast<uint16_t *>(smem + S::MAIN + 64 + S::HISTB + S::LUTB);
     const u32 bins = (u32)S::HWIN;
     Hist2 h;
     h.sh = hsh;
@@ -271,7 +284,7 @@ __global__ void __launch_bounds__(kThreads, (K2Smem<T, R, FILTER>::BOX && R > 2)
     else if constexpr (FILTER == LNF_ENTROPY)
         box_items<T, R, true, MASK>(a, &tmap, smem, &s_item, &s_abort, h, lut_sh, lut_base);
     else
-        tap_items<T, R, FILTER, MASK>(a, &tmap, smem, &s_item, &s_abort, h, lut_sh);
+        tap_items<T, R, FILTER, MASK>(a, &tmap, smem, &s_item, &s_abort, h, lut_sh, wl);
     if (a.out_hist) {
         __syncthreads();
         for (int i = threadIdx.x; i < (int)bins; i += blockDim.x)
@@ -319,6 +332,10 @@ lnf_status launch2(lnf_ctx *ctx, const FilterJob &j, cudaStream_t st, u32 *count
     a.tiles_x = (a.xend - a.xs + kTX - 1) / kTX;
     a.tiles_y = (j.by + kTY - 1) / kTY;
     a.zlen = ctx->fast_zlen > 0 ? ctx->fast_zlen : 16;
+    // the tap kernels' work is concentrated where voxels pass the gate: shorter
+    // z chunks (twice the work items) keep one heavy item from setting the end
+    if (!S::BOX)
+        a.zlen = std::max(1, a.zlen / 2);
     a.total_items = a.tiles_x * a.tiles_y * ((j.bz + a.zlen - 1) / a.zlen);
     a.filter = FILTER;
     a.prm = j.prm;

@@ -45,7 +45,7 @@ __device__ __forceinline__ void ld4p(const unsigned char *row, int col, u32 pv[4
 
 template <typename T, int R, int FILTER, bool MASK>
 __device__ void tap_items(const Args2 &a, const CUtensorMap *tmap, unsigned char *smem, int *s_item, int *s_abort,
-                          Hist2 &hist, const u32 *recip)
+                          Hist2 &hist, const u32 *recip, uint16_t *wl)
 {
     using namespace lnfdev;
     typedef Geo2<T, R> G;
@@ -124,22 +124,188 @@ __device__ void tap_items(const Args2 &a, const CUtensorMap *tmap, unsigned char
                 for (int p = pfirst; p <= s + 2 * R; ++p)
                     fixup2<T, R>(ring + (p % G::NP) * G::PBYTES, px0, py0, a.nx, a.ny);
             const unsigned char *pc = ring + ((s + R) % G::NP) * G::PBYTES;   // plane z
-            u32 p0[kRows][4], lo[kRows][4], wd[kRows][4];
+            u32 p0[kRows][4];
 #pragma unroll
-            for (int i = 0; i < kRows; ++i) {
+            for (int i = 0; i < kRows; ++i)
                 ld4<T>(pc + (r0 + i) * G::ROWB, c0, p0[i]);
+            // the band of a centre value as (v - lo) <= width: sigma [P0 - delta, P0 + delta],
+            // Okada |P0 - v| < td (td >= 1)
+            auto band = [&](u32 c, u32 &blo, u32 &bwd) {
+                const u32 h = FILTER == LNF_SIGMA ? dl : (td > 65536 ? 65535u : (u32)(td - 1));
+                blo = c > h ? c - h : 0u;
+                bwd = c - blo + h;
+            };
+            // round(sm / n) half up = floor((sm + floor(n/2)) / n) = (x * recip[n]) >> 32
+            // with recip[n] = ceil(2^32 / n): exact when x e < 2^32 (e = recip n - 2^32 < n);
+            // x < n 2^16 gives x e < n^2 2^16, so counts below 256 use the table
+            // and larger ones (sigma at radius >= 3) divide; then the gate
+            auto finish = [&](u32 sm, u32 n, u32 P0) -> u32 {
+                const u32 x = sm + (n >> 1);
+                constexpr bool SMALL = TapCoop<R, FILTER>::TAPS < 256;   // every count has a table entry
+                const u32 q = n == 1 ? sm : ((SMALL || n < 256) ? __umulhi(x, recip[n]) : x / n);
+                return (n && P0 >= T_ && (u64)sm >= (u64)n * T_) ? q : 0u;
+            };
+            u32 fo[kRows][4];   // this step's outputs
+            // Gate first: a voxel with P0 < T is 0 whatever its band, so only the
+            // voxels with P0 >= T need their taps.  The block lists this step's
+            // such voxels in shared memory and all eight warps share them out (the
+            // per-step barrier would otherwise hold every warp to the slowest one):
+            // with more taps than lanes a whole warp evaluates one voxel (each lane
+            // a few taps, a butterfly sum of the packed value and count), else one
+            // thread evaluates one voxel.  Beyond TapCoop::CAP voxels every warp
+            // takes the dense form below, which tests every tap of all 16 voxels of
+            // every lane.  (Okada at r >= 3, whose 6r + 1 taps per voxel are cheap,
+            // keeps the dense form: the listed one would cost it registers.)
+            typedef TapCoop<R, FILTER> TC;
+            constexpr bool COOP = FILTER == LNF_SIGMA || R <= 2;
+            u32 cm = 0, cnt = 0, incl = 0, wbase = 0, ctot = 0xFFFFFFFFu;
+            u32 *s_wt = reinterpret_cast<u32 *>(wl + TC::CAP);
+            if constexpr (COOP) {
 #pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    if (FILTER == LNF_SIGMA) {   // band [P0 - delta, P0 + delta] as (v - lo) <= width
-                        lo[i][k] = p0[i][k] > dl ? p0[i][k] - dl : 0u;
-                        wd[i][k] = p0[i][k] - lo[i][k] + dl;
-                    } else {                     // |P0 - v| < td  as (v - lo) <= width, td >= 1
-                        const u32 t1 = td > 65536 ? 65535u : (u32)(td - 1);
-                        lo[i][k] = p0[i][k] > t1 ? p0[i][k] - t1 : 0u;
-                        wd[i][k] = p0[i][k] - lo[i][k] + t1;
-                    }
+                for (int i = 0; i < kRows; ++i)
+#pragma unroll
+                    for (int k = 0; k < 4; ++k)
+                        if (p0[i][k] >= T_)
+                            cm |= 1u << (4 * i + k);
+                if (FILTER == LNF_OKADA && td <= 0)
+                    cm = 0;   // Okada selects nothing: every output is 0
+                cnt = (u32)__popc(cm);
+                incl = cnt;   // inclusive prefix of the lanes' counts
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const u32 t = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+                    if (lane >= o)
+                        incl += t;
+                }
+                if (lane == 31)
+                    s_wt[warp] = incl;
+                __syncthreads();
+                ctot = 0;
+#pragma unroll
+                for (int w = 0; w < kWarps; ++w) {
+                    const u32 v = s_wt[w];
+                    wbase += w < warp ? v : 0u;
+                    ctot += v;
                 }
             }
+            if (COOP && ctot <= (u32)TC::CAP) {
+#pragma unroll
+                for (int i = 0; i < kRows; ++i)
+#pragma unroll
+                    for (int k = 0; k < 4; ++k)
+                        fo[i][k] = 0u;
+                {
+                    u32 m = cm, pos = wbase + incl - cnt;
+                    while (m) {
+                        const int b = __ffs(m) - 1;
+                        m &= m - 1;
+                        // the voxel's byte offset in a plane (< 2^16: a plane is smaller)
+                        wl[pos++] = (uint16_t)((r0 + (b >> 2)) * G::ROWB + (c0 + (b & 3)) * (int)sizeof(T));
+                    }
+                }
+                __syncthreads();
+                static_assert(G::PBYTES <= 65536, "a plane's byte offsets fit the 16-bit list entries");
+                auto cell_of = [](u32 e) { return (int)e; };
+                auto val = [&](const unsigned char *q) {
+                    return sizeof(T) == 2 ? (u32)*reinterpret_cast<const uint16_t *>(q) : (u32)*q;
+                };
+                // the byte offsets of the ring slots of planes z - R .. z + R from plane z
+                int poff[2 * R + 1];
+#pragma unroll
+                for (int d = 0; d <= 2 * R; ++d)
+                    poff[d] = (int)(ring - pc) + ((s + d) % G::NP) * G::PBYTES;
+                // the byte offset of tap t from the centre's cell in plane z
+                auto tap_off = [&](int t) {
+                    int dx = 0, dy = 0, dz = 0;
+                    if (FILTER == LNF_SIGMA) {
+                        constexpr int M = 2 * R + 1;
+                        dz = t / (M * M) - R;
+                        dy = (t / M) % M - R;
+                        dx = t % M - R;
+                    } else if (t > 0) {   // tap 0 is the centre; then the arms
+                        const int arm = (t - 1) % 6, d = (t - 1) / 6 + 1;
+                        const int sg = (arm & 1) ? d : -d;
+                        dx = arm < 2 ? sg : 0;
+                        dy = arm == 2 || arm == 3 ? sg : 0;
+                        dz = arm >= 4 ? sg : 0;
+                    }
+                    return poff[dz + R] + dy * G::ROWB + dx * (int)sizeof(T);
+                };
+                if (TC::TAPS > 32) {   // a warp per voxel
+                    if (ctot > (u32)warp) {
+                        int toff[TC::PER_LANE];
+#pragma unroll
+                        for (int j = 0; j < TC::PER_LANE; ++j)
+                            toff[j] = tap_off(lane + 32 * j < TC::TAPS ? lane + 32 * j : 0);
+                        for (u32 c = warp; c < ctot; c += kWarps) {
+                            const int cell = cell_of(wl[c]);
+                            const u32 P0 = val(pc + cell);
+                            u32 blo, bwd;
+                            band(P0, blo, bwd);
+                            u32 acc = 0, nn = 0;   // packed (value << CS) + count, or value and count
+#pragma unroll
+                            for (int j = 0; j < TC::PER_LANE; ++j) {
+                                if (lane + 32 * j >= TC::TAPS)
+                                    continue;
+                                const u32 v = val(pc + cell + toff[j]);
+                                if (v - blo <= bwd) {
+                                    if (TP::PACK) {
+                                        acc += (v << TP::CS) | 1u;
+                                    } else {
+                                        acc += v;
+                                        ++nn;
+                                    }
+                                }
+                            }
+#pragma unroll
+                            for (int o = 16; o > 0; o >>= 1) {
+                                acc += __shfl_xor_sync(0xFFFFFFFFu, acc, o);
+                                if (!TP::PACK)
+                                    nn += __shfl_xor_sync(0xFFFFFFFFu, nn, o);
+                            }
+                            const u32 n = TP::PACK ? (acc & ((1u << TP::CS) - 1u)) : nn;
+                            const u32 sm = TP::PACK ? (acc >> TP::CS) : acc;
+                            if (lane == 0)
+                                wl[c] = (uint16_t)finish(sm, n, P0);   // the result replaces the entry
+                        }
+                    }
+                } else {               // a thread per voxel, dealt round the warps
+                    for (u32 c = warp + kWarps * lane; c < ctot; c += kThreads) {
+                        const int cell = cell_of(wl[c]);
+                        const u32 P0 = val(pc + cell);
+                        u32 blo, bwd;
+                        band(P0, blo, bwd);
+                        u32 sm = 0, n = 0;
+#pragma unroll
+                        for (int t = 0; t < TC::TAPS; ++t) {
+                            const u32 v = val(pc + cell + tap_off(t));
+                            if (v - blo <= bwd) {
+                                sm += v;
+                                ++n;
+                            }
+                        }
+                        wl[c] = (uint16_t)finish(sm, n, P0);
+                    }
+                }
+                __syncthreads();
+                u32 m = cm, pos = wbase + incl - cnt;
+                while (m) {
+                    const int b = __ffs(m) - 1;
+                    m &= m - 1;
+                    const u32 f = wl[pos++];
+#pragma unroll
+                    for (int i = 0; i < kRows; ++i)
+#pragma unroll
+                        for (int k = 0; k < 4; ++k)
+                            fo[i][k] = b == 4 * i + k ? f : fo[i][k];
+                }
+            } else {
+            u32 lo[kRows][4], wd[kRows][4];
+#pragma unroll
+            for (int i = 0; i < kRows; ++i)
+#pragma unroll
+                for (int k = 0; k < 4; ++k)
+                    band(p0[i][k], lo[i][k], wd[i][k]);
             u32 acc[kRows][4], cnt[kRows][4];
 #pragma unroll
             for (int i = 0; i < kRows; ++i)
@@ -270,23 +436,24 @@ __device__ void tap_items(const Args2 &a, const CUtensorMap *tmap, unsigned char
                     }
                 }
             }
-            // ---- gate, round, store, histogram
-            // round(sm / n) half up = floor((sm + floor(n/2)) / n) = (x * recip[n]) >> 32
-            // with recip[n] = ceil(2^32 / n): exact when x e < 2^32 (e = recip n - 2^32 < n);
-            // x < n 2^16 gives x e < n^2 2^16, so counts below 256 use the table
-            // and larger ones (sigma at radius >= 3) divide
+            // ---- gate and round
+#pragma unroll
+            for (int i = 0; i < kRows; ++i)
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const u32 n = TP::PACK ? (acc[i][k] & ((1u << TP::CS) - 1u)) : cnt[i][k];
+                    const u32 sm = TP::PACK ? (acc[i][k] >> TP::CS) : acc[i][k];
+                    fo[i][k] = finish(sm, n, p0[i][k]);
+                }
+            }   // dense
+            // ---- store, histogram
             const int z = z0 + s;
 #pragma unroll
             for (int i = 0; i < kRows; ++i) {
                 u32 f[4];
 #pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    const u32 n = TP::PACK ? (acc[i][k] & ((1u << TP::CS) - 1u)) : cnt[i][k];
-                    const u32 sm = TP::PACK ? (acc[i][k] >> TP::CS) : acc[i][k];
-                    const u32 x = sm + (n >> 1);
-                    const u32 q = n == 1 ? sm : (n < 256 ? __umulhi(x, recip[n]) : x / n);
-                    f[k] = (n && p0[i][k] >= T_ && (u64)sm >= (u64)n * T_) ? q : 0u;
-                }
+                for (int k = 0; k < 4; ++k)
+                    f[k] = fo[i][k];
                 const int y = y0 + kRows * warp + i, x = x0 + 4 * lane;
                 if (MASK) {
                     store_roi<T>(a, hist, z, y, x, f);

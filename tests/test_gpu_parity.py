@@ -399,3 +399,27 @@ def test_fast_ours_matches_oracle(ctx, dims, dt, kind):
         assert_same(host(outs[0]), want, f"fast ours r={r} {dims} {dt} {kind}")
         hw = oracle.image_entropy(oracle.histogram(want))
         assert abs(float(host(H)[1]) - hw) <= H_TOL * max(1.0, hw)
+
+
+@pytest.mark.parametrize("dt", ["u8", "u16"])
+def test_tap_kernels_sparse_and_dense_warps(ctx, dt):
+    # sigma and Okada evaluate only the voxels with P0 >= T when every lane of a
+    # warp holds few of them, and every voxel otherwise: one volume whose upper
+    # half is a phantom (mostly below T: sparse warps, with isolated salt) and
+    # whose lower half is uniform noise (dense warps) exercises both forms and
+    # the warps at their boundary
+    dims = (136, 70, 23)
+    if dt == "u16":
+        vol = phantoms.insect_phantom(dims, 91, dt)
+    else:
+        vol = phantoms.ellipsoid_phantom(dims, 91, dt)
+    noise = phantoms.random_volume(dims, 92, dt, p_extreme=0.1)
+    vol[:, 35:, :] = noise[:, 35:, :]
+    vol[:, 20:23, 40:44] = np.iinfo(vol.dtype).max   # a dense clump inside the sparse half
+    st = oracle.stats(vol)
+    t = dev(vol)
+    for r in (1, 2, 3, 4):
+        prm = oracle.derive_params(st, r)
+        for f in (oracle.SIGMA, oracle.OKADA):
+            got = host(ctx.filter_volume(t, f, r))
+            assert_same(got, oracle.filter_volume(vol, f, r, params=prm), f"tap filter {f} r={r} {dt}")
