@@ -722,10 +722,43 @@ def run_variants(args):
         ms = tot / n
         res[name] = {"ms_per_launch": ms, "gvox_s": N_VOX / (ms / 1e3) / 1e9,
                      "hbm_frac": N_VOX * ES * 2 / (ms / 1e3) / 1e9 / peaks()["hbm_gbs"]}
+    # the gather kernels against the plane-ring kernels on a sparse volume: 12-bit
+    # background noise (400, sigma 30) with 0.1% salt, so about 0.1% of the voxels
+    # pass the gate; the ring context never pairs the gather kernels
+    import numpy as np
+    rng = np.random.default_rng(9)
+    sv = np.clip(np.rint(rng.normal(400.0, 30.0, vol.shape).astype(np.float32)), 0, 4095).astype(np.uint16)
+    sv.reshape(-1)[rng.integers(0, sv.size, sv.size // 1000)] = 4095
+    ts = torch.from_numpy(sv).cuda()
+    os.environ["LNF_NO_GATHER"] = "1"
+    ring_ctx = lnf.Context()
+    del os.environ["LNF_NO_GATHER"]
+    sparse = {}
+    for name in FILTER_NAMES:
+        f = lnf.FILTERS[name]
+        row = {}
+        for label, c in (("gather", ctx), ("ring", ring_ctx)):
+            for _ in range(args.warmup):
+                c.filter_volume(ts, f, RADIUS, out=out)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(args.steps):
+                c.filter_volume(ts, f, RADIUS, out=out)
+            e1.record()
+            torch.cuda.synchronize()
+            row[label + "_ms_per_call"] = e0.elapsed_time(e1) / args.steps
+        sparse[name] = row
+    sparse["passing_fraction"] = float(np.count_nonzero(sv >= ctx.params()["threshold"]) / sv.size)
+    del sv
+    ring_ctx.close()
     line = {"metric": "filter variants (cluster layouts, local sigma), 512^3 uint16, r=2", "mode": "variants",
             "value": res["ours_cube"]["gvox_s"], "unit": UNIT, "higher_is_better": True, "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "dtype": "u16", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "radius": RADIUS}, "filters": res}
+            "config": {"workload": WORKLOAD, "radius": RADIUS,
+                       "sparse_workload": "512^3 uint16, noise 400 +- 30 with 0.1% salt at 4095"},
+            "filters": res, "sparse_gather_vs_ring": sparse}
     print(json.dumps(line))
     ctx.close()
 

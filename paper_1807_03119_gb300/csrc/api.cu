@@ -243,11 +243,13 @@ extern "C" lnf_status lnf_create(const lnf_config *cfg_in, lnf_ctx **out)
                 cudaSuccess &&
             q == cudaDriverEntryPointSuccess)
             ctx->encode = reinterpret_cast<PFN_encodeTiled>(fn);
-        // test hooks: force the plain-load path / the generic kernel
+        // test hooks: force the plain-load path / the generic kernel / the ring kernels alone
         const char *ev = getenv("LNF_FORCE_PLAIN");
         ctx->no_tma = ev && ev[0] == '1';
         ev = getenv("LNF_FORCE_GENERIC");
         ctx->no_fast = ev && ev[0] == '1';
+        ev = getenv("LNF_NO_GATHER");
+        ctx->no_gather = ev && ev[0] == '1';
         if (cudaDeviceSynchronize() != cudaSuccess)
             s = LNF_ECUDA;
     } while (0);

@@ -236,6 +236,7 @@ struct FastArgs {
     u64 *out_hist;
     u32 *counter;
     u32 *err;
+    int paired;                           // 1: launched beside the gather kernel, which may take the job
 };
 
 // the ring-column cell (tile column -1 or kTX, tile row -1 .. kTY) a lane
@@ -667,6 +668,8 @@ template <typename T, int R, bool MASK>
 __global__ void __launch_bounds__(kThreads, 2) k_ours_fast(const __grid_constant__ CUtensorMap tmap, const FastArgs a)
 {
     typedef FGeo<T, R> G;
+    if (a.paired && lnf_gather_mode(*a.prm, LNF_OURS))
+        return;   // few voxels pass the gate: the gather kernel does the work
     extern __shared__ __align__(128) unsigned char smem_raw[];
     unsigned char *smem = smem_raw + ((128 - (lnfdev::smem_u32(smem_raw) & 127)) & 127);
     __shared__ int s_item, s_abort;
@@ -705,7 +708,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_ours_fast(const __grid_constant
 }
 
 template <typename T, int R>
-lnf_status launch(lnf_ctx *ctx, const FilterJob &j, cudaStream_t st, u64 *out_hist, u32 *counter, int *handled)
+lnf_status launch(lnf_ctx *ctx, const FilterJob &j, cudaStream_t st, u64 *out_hist, u32 *counter, int *handled,
+                  int paired)
 {
     typedef FGeo<T, R> G;
     // this kernel's own descriptor: box = its tile + halo
@@ -744,6 +748,7 @@ lnf_status launch(lnf_ctx *ctx, const FilterJob &j, cudaStream_t st, u64 *out_hi
     a.out_hist = out_hist;
     a.counter = counter ? counter : ctx->d_counter + 8;
     a.err = ctx->d_err;
+    a.paired = paired;
     void (*kern)(const CUtensorMap, const FastArgs) = a.roi ? k_ours_fast<T, R, true> : k_ours_fast<T, R, false>;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, G::SMEM) != cudaSuccess)
         return lnf_fail(ctx, LNF_ECUDA, "fast kernel: shared memory attribute");
@@ -783,24 +788,33 @@ lnf_status lnf_fast_dispatch(lnf_ctx *ctx, const FilterJob &job, const CUtensorM
     *handled = 0;
     if (!tmap || job.aniso || !lnf_fast_covers(job.filter, job.radius, job.offset))
         return LNF_OK;
-    if (job.filter != LNF_OURS)
-        return lnf_fast2_dispatch(ctx, job, tmap, stream, handled, counter);
+    // whole volumes at radius 1..2 also get the gather kernel, which takes the
+    // job when few voxels pass the gate (decided on the device); it is launched
+    // only once the ring kernel has taken the job, so that no other kernel
+    // writes the output (or its histogram) a second time
+    const int pair = !ctx->no_gather && lnf_gather_covers(job);
     lnf_status s = LNF_OK;
-    u64 *oh = job.out_hist;
-    if (job.dtype == LNF_U8) {
-        switch (job.radius) {
-        case 1: s = launch<uint8_t, 1>(ctx, job, stream, oh, counter, handled); break;
-        case 2: s = launch<uint8_t, 2>(ctx, job, stream, oh, counter, handled); break;
-        case 3: s = launch<uint8_t, 3>(ctx, job, stream, oh, counter, handled); break;
-        default: s = launch<uint8_t, 4>(ctx, job, stream, oh, counter, handled); break;
-        }
+    if (job.filter != LNF_OURS) {
+        s = lnf_fast2_dispatch(ctx, job, tmap, stream, handled, counter, pair);
     } else {
-        switch (job.radius) {
-        case 1: s = launch<uint16_t, 1>(ctx, job, stream, oh, counter, handled); break;
-        case 2: s = launch<uint16_t, 2>(ctx, job, stream, oh, counter, handled); break;
-        case 3: s = launch<uint16_t, 3>(ctx, job, stream, oh, counter, handled); break;
-        default: s = launch<uint16_t, 4>(ctx, job, stream, oh, counter, handled); break;
+        u64 *oh = job.out_hist;
+        if (job.dtype == LNF_U8) {
+            switch (job.radius) {
+            case 1: s = launch<uint8_t, 1>(ctx, job, stream, oh, counter, handled, pair); break;
+            case 2: s = launch<uint8_t, 2>(ctx, job, stream, oh, counter, handled, pair); break;
+            case 3: s = launch<uint8_t, 3>(ctx, job, stream, oh, counter, handled, pair); break;
+            default: s = launch<uint8_t, 4>(ctx, job, stream, oh, counter, handled, pair); break;
+            }
+        } else {
+            switch (job.radius) {
+            case 1: s = launch<uint16_t, 1>(ctx, job, stream, oh, counter, handled, pair); break;
+            case 2: s = launch<uint16_t, 2>(ctx, job, stream, oh, counter, handled, pair); break;
+            case 3: s = launch<uint16_t, 3>(ctx, job, stream, oh, counter, handled, pair); break;
+            default: s = launch<uint16_t, 4>(ctx, job, stream, oh, counter, handled, pair); break;
+            }
         }
     }
+    if (s == LNF_OK && *handled && pair)
+        s = lnf_gather_launch(ctx, job, stream);
     return s;
 }

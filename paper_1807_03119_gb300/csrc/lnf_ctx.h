@@ -74,6 +74,7 @@ struct lnf_ctx {
     int fast_zlen = 16;         // z chunk length of a work item (specialised kernels)
     bool no_tma = false;        // testing: force plain loads
     bool no_fast = false;       // testing: force the generic kernel
+    bool no_gather = false;     // testing: never pair the gather kernel with the ring kernels
     VolScratch vs;              // scratch of plain calls
     std::vector<VolScratch> pool;   // scratch of batched / resident volumes
     u64 *out_hist = nullptr;    // LNF_MAX_PACK output histograms of 65536 bins
@@ -170,10 +171,17 @@ bool lnf_fast_covers(int filter, int radius, int offset);
 // `counter` is the launch's work counter (null: the context's own, for its stream)
 lnf_status lnf_fast_dispatch(lnf_ctx *ctx, const FilterJob &job, const CUtensorMap *tmap, cudaStream_t stream,
                              int *handled, u32 *counter = nullptr);
+// `paired`: the gather kernel is launched beside (the ring kernel returns at once
+// when that one does the work)
 lnf_status lnf_fast2_dispatch(lnf_ctx *ctx, const FilterJob &job, const CUtensorMap *tmap, cudaStream_t stream,
-                              int *handled, u32 *counter = nullptr);
+                              int *handled, u32 *counter = nullptr, int paired = 0);
 // fast2_box.cu: the mean / entropy-filter job through its box kernel
-lnf_status lnf_fast2_box(lnf_ctx *ctx, const FilterJob &job, cudaStream_t stream, u32 *counter, int *handled);
+lnf_status lnf_fast2_box(lnf_ctx *ctx, const FilterJob &job, cudaStream_t stream, u32 *counter, int *handled,
+                         int paired);
+// sparse.cu: whether the gather kernel covers the job (whole volume, dense aligned
+// rows, radius 1..2, filters 0..4), and its launch
+bool lnf_gather_covers(const FilterJob &j);
+lnf_status lnf_gather_launch(lnf_ctx *ctx, const FilterJob &j, cudaStream_t st);
 // render.cu: one ray per pixel (see lnf_render)
 cudaError_t lnf_launch_render(const void *vol, const int64_t dims[3], int64_t pitch, int dtype, int view,
                               int filter, int radius, int offset, const DevParams *prm, const u32 *lut,

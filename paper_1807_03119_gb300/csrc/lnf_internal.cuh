@@ -47,7 +47,22 @@ struct DevParams {
     double H_in;                // image entropy of the input
     u32 sigma_k;                // k of the sigma bands (global: in delta; local: applied per cube)
     u32 pad;
+    u64 n_pass;                 // voxels whose own value passes the gate (P0 >= T)
 };
+
+// Which of a filter's two whole-volume kernels works: the gather kernel
+// (sparse.cu), which evaluates only the voxels that pass the gate (every other
+// output is 0 by the gate's definition), while very few do; the plane-ring
+// kernel (fast.cu, fast2_*.cu), which evaluates every voxel, otherwise.  Both
+// are launched and both read this, so exactly one of them writes the output.
+// The switch points follow the two kernels' measured costs (a fixed streaming
+// cost plus one per passing voxel for the gather kernel): sigma 1/128 of the
+// voxels passing, every other filter 1/256.
+__host__ __device__ inline bool lnf_gather_mode(const DevParams &P, int filter)
+{
+    const u64 k = filter == 1 ? 128ull : 256ull;
+    return P.n_pass * k <= P.N;
+}
 
 // One unit of filter work: a volume (or ROI of it) with a filter and radius.
 struct FilterJob {

@@ -511,12 +511,35 @@ __device__ void chunk_params(const u64 *hist, const DevStats *st, const ParamCfg
             __syncthreads();
         }
     }
+    // the gate threshold, and how many voxels pass it: the chunks above T's
+    // chunk whole, then the levels of T's own chunk from T up
+    const u32 t_best = sm.t[0];
+    const u64 hws = sm.hw[0];
+    const double Hs = sm.d[0];
+    const u32 T_gate = cfg.threshold_mode == 0 ? (t_best ? t_best : st->minv)
+                                               : (cfg.threshold_mode == 1 ? cfg.threshold_value : 0u);
+    {
+        const int cT = (int)(T_gate / kChunk);
+        u64 np = 0;
+        for (int cc = tid; cc < nc; cc += blockDim.x)
+            if (cc > cT)
+                np += __ldcg(&ps->tot_n[cc]);
+        for (u32 v = (u32)cT * kChunk + tid; v < min((u32)(cT + 1) * kChunk, L); v += blockDim.x)
+            if (v >= T_gate)
+                np += hist[v];
+        __syncthreads();
+        sm.hw[tid] = np;
+        __syncthreads();
+        for (int off = kPThreads / 2; off > 0; off >>= 1) {
+            if (tid < off)
+                sm.hw[tid] += sm.hw[tid + off];
+            __syncthreads();
+        }
+    }
     if (tid != 0)
         return;
     OtsuJ b;
-    b.t = sm.t[0];
-    const u64 hws = sm.hw[0];
-    const double Hs = sm.d[0];
+    b.t = t_best;
     ps->done = 0;
     const u32 t_otsu = b.t ? b.t : st->minv;   // single level: T = that level
     const u128 var_num = (u128)N * Q - (u128)S * S;   // N^2 sigma^2
@@ -540,6 +563,7 @@ __device__ void chunk_params(const u64 *hist, const DevStats *st, const ParamCfg
     p.H_in = Hs;
     p.sigma_k = (u32)cfg.sigma_k;
     p.pad = 0;
+    p.n_pass = sm.hw[0];
     *prm = p;
 }
 
