@@ -96,11 +96,11 @@ KIND_SOURCES = {
     "stats": ["stats.cu"],
     "params": ["stats.cu"],
     "entropy": ["stats.cu"],
-    "filter:ours": ["fast.cu"],
-    "filter:mean": ["fast2.cuh", "fast2_box.cu"],
-    "filter:entropy": ["fast2.cuh", "fast2_box.cu"],
-    "filter:sigma": ["fast2.cuh", "fast2_tap.cu"],
-    "filter:okada": ["fast2.cuh", "fast2_tap.cu"],
+    "filter:ours": ["fast.cu", "sparse.cu"],
+    "filter:mean": ["fast2.cuh", "fast2_box.cu", "sparse.cu"],
+    "filter:entropy": ["fast2.cuh", "fast2_box.cu", "sparse.cu"],
+    "filter:sigma": ["fast2.cuh", "fast2_tap.cu", "sparse.cu"],
+    "filter:okada": ["fast2.cuh", "fast2_tap.cu", "sparse.cu"],
 }
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "dram_traffic_512cubed_u16_r2.txt")
 
@@ -129,7 +129,9 @@ def recorded_traffic(kind):
 
 
 def kind_of_kernel(name):
-    """Bench kind of an ncu kernel name (None for launches that are not ours)."""
+    """Bench kind of an ncu kernel name (None for launches that are not ours, and
+    for the gather kernels, whose launch beside a ring kernel reads nothing when the
+    ring kernel does the work)."""
     import re
     m = re.search(r"k_fast2<[^,]+, \d+, (\d+)", name)
     if m:

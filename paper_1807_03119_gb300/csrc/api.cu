@@ -604,7 +604,7 @@ lnf_status lnf_run_one(lnf_ctx *ctx, int filter, int radius, const void *in, voi
         int handled = 0;
         s = lnf_fast_dispatch(ctx, pk.jobs[0], pk.jobs[0].tmap_idx >= 0 ? &pk.tmaps[0] : nullptr, stream, &handled);
         if (s != LNF_OK || handled) {
-            lnf_prof_end(ctx, rec, filter_name(filter), stream, 1);
+            lnf_prof_end(ctx, rec, filter_name(filter), stream, handled ? handled : 1);
             return s;
         }
     }

@@ -814,7 +814,9 @@ lnf_status lnf_fast_dispatch(lnf_ctx *ctx, const FilterJob &job, const CUtensorM
             }
         }
     }
-    if (s == LNF_OK && *handled && pair)
+    if (s == LNF_OK && *handled && pair) {
         s = lnf_gather_launch(ctx, job, stream);
+        *handled = 2;   // two kernels launched
+    }
     return s;
 }

@@ -167,7 +167,8 @@ void lnf_prof_end(lnf_ctx *ctx, int rec, const char *name, cudaStream_t st, int 
 // fast.cu: whether a specialised kernel covers this filter, radius and cluster
 // offset (on an input TMA can address)
 bool lnf_fast_covers(int filter, int radius, int offset);
-// fast.cu: run the job through a specialised kernel if one covers it (*handled = 1);
+// fast.cu: run the job through a specialised kernel if one covers it (*handled = the
+// number of kernels launched: 1, or 2 with the gather kernel beside, else 0);
 // `counter` is the launch's work counter (null: the context's own, for its stream)
 lnf_status lnf_fast_dispatch(lnf_ctx *ctx, const FilterJob &job, const CUtensorMap *tmap, cudaStream_t stream,
                              int *handled, u32 *counter = nullptr);
