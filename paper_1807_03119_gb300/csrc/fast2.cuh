@@ -205,7 +205,9 @@ __device__ __forceinline__ void store_roi(const Args2 &a, Hist2 &h, int z, int y
 // ------------------------------------------------------------------ the two kernel bodies
 
 constexpr int kBoxPF = 1;            // box kernel: one plane prefetched (two CTAs per SM fit)
-constexpr int kBoxWin = 2048;        // box kernel (entropy): histogram / weight windows
+constexpr int kLutWin16 = 4096;      // box kernel (entropy): window of the weight table in shared
+                                     // memory (16-bit data: all 12-bit levels from the minimum)
+constexpr int kEntHist16 = 1024;     // ... and of its output histogram (the rest goes to global atomics)
 
 // box kernel body (fast2_box.cu): mean (ENT = false) and entropy filter (ENT = true)
 template <typename T, int R, bool ENT, bool MASK>
@@ -219,10 +221,13 @@ struct TapCoop {
     static constexpr int TAPS = FILTER == LNF_SIGMA ? (2 * R + 1) * (2 * R + 1) * (2 * R + 1) : 6 * R + 1;
     static constexpr int PER_LANE = (TAPS + 31) / 32;
     static constexpr int CAP = 1024;
-    static constexpr int BYTES = CAP * 2 + 64;   // the list and the warps' counts
+    // the list (cells and destinations, 16 bits each), the warps' counts, and one
+    // 16-bit output per voxel of the block step
+    static constexpr int BYTES = CAP * 4 + 64 + kWarps * 32 * 16 * 2;
 };
 // tap kernel body (fast2_tap.cu): sigma and Okada; `wl`: the block's candidate
-// list (TapCoop::CAP 16-bit entries) followed by one 32-bit count per warp
+// area (TapCoop::BYTES): CAP cells, CAP destinations, one 32-bit count per warp,
+// then the outputs of the step (16 per lane)
 template <typename T, int R, int FILTER, bool MASK>
 __device__ void tap_items(const Args2 &a, const CUtensorMap *tmap, unsigned char *smem, int *s_item, int *s_abort,
                           Hist2 &hist, const u32 *recip, uint16_t *wl);
@@ -233,8 +238,8 @@ template <typename T, int R, int FILTER>
 struct K2Smem {
     static constexpr bool BOX = FILTER == LNF_MEAN || FILTER == LNF_ENTROPY;
     typedef Geo2<T, R, BOX ? kBoxPF : kPF> G;
-    static constexpr int HWIN = sizeof(T) == 1 ? 256 : (FILTER == LNF_ENTROPY ? kBoxWin : kHistWin);
-    static constexpr int LWIN = sizeof(T) == 1 ? 256 : kBoxWin;
+    static constexpr int HWIN = sizeof(T) == 1 ? 256 : (FILTER == LNF_ENTROPY ? kEntHist16 : kHistWin);
+    static constexpr int LWIN = sizeof(T) == 1 ? 256 : kLutWin16;
     static constexpr int HISTB = HWIN * 4;
     static constexpr int NTAB = (2 * R + 1) * (2 * R + 1) * (2 * R + 1) + 1;   // counts 0 .. M^3
     static constexpr int LUTB = FILTER == LNF_ENTROPY ? LWIN * 4 : (BOX ? 0 : ((NTAB * 4 + 15) / 16) * 16);
@@ -336,9 +341,9 @@ lnf_status launch2(lnf_ctx *ctx, const FilterJob &j, cudaStream_t st, u32 *count
     a.tiles_y = (j.by + kTY - 1) / kTY;
     a.zlen = ctx->fast_zlen > 0 ? ctx->fast_zlen : 16;
     // the tap kernels' work is concentrated where voxels pass the gate: shorter
-    // z chunks (twice the work items) keep one heavy item from setting the end
+    // z chunks (four times the work items) keep one heavy item from setting the end
     if (!S::BOX)
-        a.zlen = std::max(1, a.zlen / 2);
+        a.zlen = std::max(1, a.zlen / 4);
     a.total_items = a.tiles_x * a.tiles_y * ((j.bz + a.zlen - 1) / a.zlen);
     a.filter = FILTER;
     a.prm = j.prm;

@@ -19,7 +19,7 @@ struct BoxBody {
         if (!ENT)
             return v;
         const u32 o = v - lut_base;
-        return o < (u32)kBoxWin ? lut_sh[o] : __ldg(lut_g + v);
+        return o < (u32)(sizeof(T) == 1 ? 256 : kLutWin16) ? lut_sh[o] : __ldg(lut_g + v);
     }
 };
 

@@ -66,6 +66,17 @@ __device__ void tap_items(const Args2 &a, const CUtensorMap *tmap, unsigned char
         fence_mbar_init();
     }
     __syncthreads();
+    // sigma, a warp per listed voxel: lane's taps t = lane + 32 j of the M^3 cube,
+    // as a plane index (0 .. 2R, plane z - R + index) and an in-plane byte offset
+    constexpr int TPL = (FILTER == LNF_SIGMA && TapCoop<R, FILTER>::TAPS > 32) ? TapCoop<R, FILTER>::PER_LANE : 1;
+    int tdz[TPL], tin[TPL];
+#pragma unroll
+    for (int j = 0; j < TPL; ++j) {
+        constexpr int M = 2 * R + 1;
+        const int t = lane + 32 * j < TapCoop<R, FILTER>::TAPS ? lane + 32 * j : 0;
+        tdz[j] = t / (M * M);
+        tin[j] = ((t / M) % M - R) * G::ROWB + (t % M - R) * (int)sizeof(T);
+    }
 
     for (;;) {
         if (threadIdx.x == 0)
@@ -159,7 +170,9 @@ __device__ void tap_items(const Args2 &a, const CUtensorMap *tmap, unsigned char
             typedef TapCoop<R, FILTER> TC;
             constexpr bool COOP = FILTER == LNF_SIGMA || R <= 2;
             u32 cm = 0, cnt = 0, incl = 0, wbase = 0, ctot = 0xFFFFFFFFu;
-            u32 *s_wt = reinterpret_cast<u32 *>(wl + TC::CAP);
+            uint16_t *wdst = wl + TC::CAP;                                   // destinations
+            u32 *s_wt = reinterpret_cast<u32 *>(wl + 2 * TC::CAP);          // the warps' counts
+            uint16_t *wres = wl + 2 * TC::CAP + 32;                         // outputs, 16 per lane
             if constexpr (COOP) {
 #pragma unroll
                 for (int i = 0; i < kRows; ++i)
@@ -199,8 +212,11 @@ __device__ void tap_items(const Args2 &a, const CUtensorMap *tmap, unsigned char
                     while (m) {
                         const int b = __ffs(m) - 1;
                         m &= m - 1;
-                        // the voxel's byte offset in a plane (< 2^16: a plane is smaller)
-                        wl[pos++] = (uint16_t)((r0 + (b >> 2)) * G::ROWB + (c0 + (b & 3)) * (int)sizeof(T));
+                        // the voxel's byte offset in a plane (< 2^16: a plane is smaller),
+                        // and where its output goes
+                        wl[pos] = (uint16_t)((r0 + (b >> 2)) * G::ROWB + (c0 + (b & 3)) * (int)sizeof(T));
+                        wdst[pos] = (uint16_t)((warp * 32 + lane) * 16 + b);
+                        ++pos;
                     }
                 }
                 __syncthreads();
@@ -233,10 +249,17 @@ __device__ void tap_items(const Args2 &a, const CUtensorMap *tmap, unsigned char
                 };
                 if (TC::TAPS > 32) {   // a warp per voxel
                     if (ctot > (u32)warp) {
+                        // this lane's taps: the in-plane part of the offset is fixed, the
+                        // plane's slot is picked from this step's (no division per tap)
                         int toff[TC::PER_LANE];
 #pragma unroll
-                        for (int j = 0; j < TC::PER_LANE; ++j)
-                            toff[j] = tap_off(lane + 32 * j < TC::TAPS ? lane + 32 * j : 0);
+                        for (int j = 0; j < TC::PER_LANE; ++j) {
+                            int sel = poff[0];
+#pragma unroll
+                            for (int d = 1; d <= 2 * R; ++d)
+                                sel = tdz[j] == d ? poff[d] : sel;
+                            toff[j] = sel + tin[j];
+                        }
                         for (u32 c = warp; c < ctot; c += kWarps) {
                             const int cell = cell_of(wl[c]);
                             const u32 P0 = val(pc + cell);
@@ -266,7 +289,7 @@ __device__ void tap_items(const Args2 &a, const CUtensorMap *tmap, unsigned char
                             const u32 n = TP::PACK ? (acc & ((1u << TP::CS) - 1u)) : nn;
                             const u32 sm = TP::PACK ? (acc >> TP::CS) : acc;
                             if (lane == 0)
-                                wl[c] = (uint16_t)finish(sm, n, P0);   // the result replaces the entry
+                                wres[wdst[c]] = (uint16_t)finish(sm, n, P0);
                         }
                     }
                 } else {               // a thread per voxel, dealt round the warps
@@ -284,20 +307,22 @@ __device__ void tap_items(const Args2 &a, const CUtensorMap *tmap, unsigned char
                                 ++n;
                             }
                         }
-                        wl[c] = (uint16_t)finish(sm, n, P0);
+                        wres[wdst[c]] = (uint16_t)finish(sm, n, P0);
                     }
                 }
                 __syncthreads();
-                u32 m = cm, pos = wbase + incl - cnt;
-                while (m) {
-                    const int b = __ffs(m) - 1;
-                    m &= m - 1;
-                    const u32 f = wl[pos++];
+                if (cm) {   // this lane's 16 outputs, two 16-byte loads; listed voxels only
+                    const uint4 *rp = reinterpret_cast<const uint4 *>(wres + (warp * 32 + lane) * 16);
+                    const uint4 q0 = rp[0], q1 = rp[1];
+                    const u32 w[8] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, q1.z, q1.w};
 #pragma unroll
                     for (int i = 0; i < kRows; ++i)
 #pragma unroll
-                        for (int k = 0; k < 4; ++k)
-                            fo[i][k] = b == 4 * i + k ? f : fo[i][k];
+                        for (int k = 0; k < 4; ++k) {
+                            const int b = 4 * i + k;
+                            const u32 f = (w[b >> 1] >> (16 * (b & 1))) & 0xFFFFu;
+                            fo[i][k] = (cm >> b) & 1u ? f : 0u;
+                        }
                 }
             } else {
             u32 lo[kRows][4], wd[kRows][4];
