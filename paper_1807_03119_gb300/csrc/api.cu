@@ -243,13 +243,16 @@ extern "C" lnf_status lnf_create(const lnf_config *cfg_in, lnf_ctx **out)
                 cudaSuccess &&
             q == cudaDriverEntryPointSuccess)
             ctx->encode = reinterpret_cast<PFN_encodeTiled>(fn);
-        // test hooks: force the plain-load path / the generic kernel / the ring kernels alone
+        // test hooks: force the plain-load path / the generic kernel / the ring kernels
+        // alone / no fused kernel
         const char *ev = getenv("LNF_FORCE_PLAIN");
         ctx->no_tma = ev && ev[0] == '1';
         ev = getenv("LNF_FORCE_GENERIC");
         ctx->no_fast = ev && ev[0] == '1';
         ev = getenv("LNF_NO_GATHER");
         ctx->no_gather = ev && ev[0] == '1';
+        ev = getenv("LNF_NO_FUSED");
+        ctx->no_fused = ev && ev[0] == '1';
         if (cudaDeviceSynchronize() != cudaSuccess)
             s = LNF_ECUDA;
     } while (0);
@@ -773,15 +776,59 @@ static lnf_status multi_impl(lnf_ctx *ctx, int radius, const void *in, const int
     int64_t pitch = 0;
     if (any_fast && (s = stage_input(ctx, in, dims, dtype, st, &src, &pitch)) != LNF_OK)
         return s;
-    for (int i = 0; i < n; ++i) {
+    // mean, sigma, entropy filter and Okada, each asked for once, in one pass of the
+    // fused kernel while few voxels pass the gate (decided on the device; their
+    // ring kernels, launched after it, return at once then).  The other filters run
+    // first, so that copies of their outputs (`after`) overlap the fused pass.
+    int slot4[4] = {-1, -1, -1, -1};
+    bool once = true;
+    for (int i = 0; i < n; ++i)
+        if (filter_ids[i] >= LNF_MEAN && filter_ids[i] <= LNF_OKADA) {
+            once = once && slot4[filter_ids[i]] < 0;
+            slot4[filter_ids[i]] = i;
+        }
+    const bool fuse = once && slot4[0] >= 0 && slot4[1] >= 0 && slot4[2] >= 0 && slot4[3] >= 0 && !ctx->no_fused &&
+                      !ctx->no_fast && lnf_fast_covers(LNF_SIGMA, radius, ctx->cfg.cluster_offset);
+    auto run = [&](int i) -> lnf_status {
         u64 *oh = d_entropy ? ctx->out_hist + (size_t)i * LNF_LEVELS_U16 : nullptr;
         const bool f = lnf_fast_covers(filter_ids[i], radius, ctx->cfg.cluster_offset);
-        if ((s = lnf_run_one(ctx, filter_ids[i], radius, f ? src : in, outs[i], dims, dtype, nullptr, nullptr,
-                             ctx->vs, oh, st, f ? pitch : 0)) != LNF_OK)
+        lnf_status r = lnf_run_one(ctx, filter_ids[i], radius, f ? src : in, outs[i], dims, dtype, nullptr, nullptr,
+                                   ctx->vs, oh, st, f ? pitch : 0);
+        if (r == LNF_OK && after && cudaEventRecord(after[i], st) != cudaSuccess)
+            r = lnf_fail(ctx, LNF_ECUDA, "event record failed");
+        return r;
+    };
+    auto in_fused = [&](int i) { return fuse && filter_ids[i] >= LNF_MEAN && filter_ids[i] <= LNF_OKADA; };
+    ctx->fused_mask = 0;
+    for (int i = 0; i < n; ++i)
+        if (!in_fused(i) && (s = run(i)) != LNF_OK)
             return s;
-        if (after)
-            CK(cudaEventRecord(after[i], st));
+    if (fuse) {
+        FilterPack &pk = ctx->pack;
+        pk.n_jobs = 1;
+        if ((s = lnf_make_job(ctx, pk, 0, LNF_MEAN, radius, src, outs[slot4[0]], dims, dtype, nullptr, nullptr,
+                              ctx->vs, nullptr, pitch)) != LNF_OK)
+            return s;
+        void *o4[4];
+        u64 *h4[4];
+        for (int f = 0; f < 4; ++f) {
+            o4[f] = outs[slot4[f]];
+            h4[f] = d_entropy ? ctx->out_hist + (size_t)slot4[f] * LNF_LEVELS_U16 : nullptr;
+        }
+        int handled = 0;
+        const int rec = lnf_prof_begin(ctx, st);
+        s = lnf_fused_launch(ctx, pk.jobs[0], o4, h4, st, &handled);
+        lnf_prof_end(ctx, rec, "filter:fused4", st, 1);
+        if (s != LNF_OK)
+            return s;
+        ctx->fused_mask = handled ? 0xF : 0;
+        for (int i = 0; i < n; ++i)
+            if (in_fused(i) && (s = run(i)) != LNF_OK) {
+                ctx->fused_mask = 0;
+                return s;
+            }
     }
+    ctx->fused_mask = 0;
     if (d_entropy) {
         CK(cudaMemcpyAsync(d_entropy, &ctx->vs.prm->H_in, sizeof(double), cudaMemcpyDeviceToDevice, st));
         EntropyPack ep;

@@ -792,7 +792,8 @@ lnf_status lnf_fast_dispatch(lnf_ctx *ctx, const FilterJob &job, const CUtensorM
     // job when few voxels pass the gate (decided on the device); it is launched
     // only once the ring kernel has taken the job, so that no other kernel
     // writes the output (or its histogram) a second time
-    const int pair = !ctx->no_gather && lnf_gather_covers(job);
+    // (a filter the fused kernel of this multi-filter call covers is not paired)
+    const int pair = !ctx->no_gather && !((ctx->fused_mask >> job.filter) & 1) && lnf_gather_covers(job);
     lnf_status s = LNF_OK;
     if (job.filter != LNF_OURS) {
         s = lnf_fast2_dispatch(ctx, job, tmap, stream, handled, counter, pair);

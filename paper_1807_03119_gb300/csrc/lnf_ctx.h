@@ -75,6 +75,8 @@ struct lnf_ctx {
     bool no_tma = false;        // testing: force plain loads
     bool no_fast = false;       // testing: force the generic kernel
     bool no_gather = false;     // testing: never pair the gather kernel with the ring kernels
+    bool no_fused = false;      // testing: never launch the fused kernel of a multi-filter call
+    int fused_mask = 0;         // filter ids a launched fused kernel covers (during a multi-filter call)
     VolScratch vs;              // scratch of plain calls
     std::vector<VolScratch> pool;   // scratch of batched / resident volumes
     u64 *out_hist = nullptr;    // LNF_MAX_PACK output histograms of 65536 bins
@@ -82,7 +84,7 @@ struct lnf_ctx {
     u32 *d_err = nullptr;
     u32 *d_counter = nullptr;   // work counters: [0] generic, [1..4] serving streams (generic),
                                 // [8] paper's filter, [9] comparison filters, [10..13] serving
-                                // streams (specialised), [15] the self-test's status word
+                                // streams (specialised), [14] fused kernel, [15] the self-test's status word
     double *d_ent_part = nullptr;   // entropy reduction partials (LNF_ENT_SPLIT x LNF_MAX_ENT)
     u32 *d_ent_done = nullptr;      // entropy reduction tickets (LNF_MAX_ENT)
     PFN_encodeTiled encode = nullptr;
@@ -183,6 +185,10 @@ lnf_status lnf_fast2_box(lnf_ctx *ctx, const FilterJob &job, cudaStream_t stream
 // rows, radius 1..2, filters 0..4), and its launch
 bool lnf_gather_covers(const FilterJob &j);
 lnf_status lnf_gather_launch(lnf_ctx *ctx, const FilterJob &j, cudaStream_t st);
+// fused.cu: mean, sigma, entropy filter and Okada of one volume in one pass (outs /
+// hists in that order); *handled = 1 if launched
+lnf_status lnf_fused_launch(lnf_ctx *ctx, const FilterJob &j, void *const outs[4], u64 *const hists[4],
+                            cudaStream_t st, int *handled);
 // render.cu: one ray per pixel (see lnf_render)
 cudaError_t lnf_launch_render(const void *vol, const int64_t dims[3], int64_t pitch, int dtype, int view,
                               int filter, int radius, int offset, const DevParams *prm, const u32 *lut,

@@ -64,6 +64,15 @@ __host__ __device__ inline bool lnf_gather_mode(const DevParams &P, int filter)
     return P.n_pass * k <= P.N;
 }
 
+// Whether the fused kernel (fused.cu) does the work of the four cube filters
+// (mean, sigma, entropy, Okada) of a multi-filter call: it evaluates only the
+// voxels that pass the gate, so while they are at most 1/32 of the volume; the
+// four ring kernels, launched beside, return at once then.
+__host__ __device__ inline bool lnf_fused_mode(const DevParams &P)
+{
+    return P.n_pass * 32ull <= P.N;
+}
+
 // One unit of filter work: a volume (or ROI of it) with a filter and radius.
 struct FilterJob {
     const void *in;

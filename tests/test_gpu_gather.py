@@ -112,3 +112,51 @@ def test_dense_volume_leaves_the_work_to_the_ring_kernels(lnf):
         for f in FILTERS:
             got = c.filter_volume(t, f, 2).cpu().numpy()
             assert np.array_equal(got, oracle.filter_volume(vol, f, 2, params=oracle.derive_params(st, 2)))
+
+
+@pytest.mark.parametrize("dt", ["u16", "u8"])
+def test_fused_multi_filter_pass(lnf, monkeypatch, dt):
+    """The fused kernel of a multi-filter call (mean, sigma, entropy filter and
+    Okada from one pass) on a volume where few voxels pass the gate overall but a
+    bright cube packs more than a round's worth (1024) into some block steps:
+    outputs and entropies against the oracle and against the ring kernels alone.
+    The cube fills one whole 128 x 32 block tile (4096 voxels per step: four rounds)
+    at the volume's left border."""
+    rng = np.random.default_rng(721)
+    nx, ny, nz = 256, 128, 40
+    if dt == "u16":
+        vol = np.clip(np.rint(rng.normal(400, 30, (nz, ny, nx))), 0, 4095)
+        vol[10:18, 32:64, 0:128] = rng.integers(2500, 3500, (8, 32, 128))
+        vol[rng.random(vol.shape) < 0.002] = 4095
+    else:
+        vol = np.clip(np.rint(rng.normal(20, 4, (nz, ny, nx))), 0, 255)
+        vol[10:18, 32:64, 0:128] = rng.integers(150, 220, (8, 32, 128))
+        vol[rng.random(vol.shape) < 0.002] = 255
+    vol = vol.astype(np.uint16 if dt == "u16" else np.uint8)
+    st = oracle.stats(vol)
+    a = lnf.Context()
+    monkeypatch.setenv("LNF_NO_FUSED", "1")
+    try:
+        b = lnf.Context()
+    finally:
+        monkeypatch.delenv("LNF_NO_FUSED")
+    try:
+        t = torch.from_numpy(vol).cuda()
+        for r in (1, 2):
+            prm = oracle.derive_params(st, r)
+            frac = np.count_nonzero(vol >= prm["T"]) / vol.size
+            assert 1 / 256 < frac <= 1 / 32, frac   # the fused kernel's range, not the gather kernel's
+            outs, H = a.filter_multi(t, FILTERS, r)
+            outs_b, H_b = b.filter_multi(t, FILTERS, r)
+            Hh = H.cpu().numpy()
+            for i, f in enumerate(FILTERS):
+                want = oracle.filter_volume(vol, f, r, params=prm)
+                got = outs[i].cpu().numpy()
+                assert np.array_equal(got, want), (f, r, int((got != want).sum()))
+                assert np.array_equal(outs_b[i].cpu().numpy(), want), (f, r, "ring")
+                hw = oracle.image_entropy(oracle.histogram(want))
+                assert abs(Hh[i + 1] - hw) <= 1e-9 * max(1.0, hw), (f, Hh[i + 1], hw)
+            assert np.allclose(H.cpu().numpy(), H_b.cpu().numpy(), rtol=1e-12, atol=0)
+    finally:
+        a.close()
+        b.close()
