@@ -160,3 +160,25 @@ def test_fused_multi_filter_pass(lnf, monkeypatch, dt):
     finally:
         a.close()
         b.close()
+
+
+def test_fused_pass_only_for_the_four_once(lnf):
+    """The fused pass runs only when mean, sigma, entropy filter and Okada are each
+    asked for once; repeated or partial lists take the ring kernels, with the
+    same results (sparse volume: the fused pass would otherwise work)."""
+    vol = _sparse_u16((96, 40, 36), 731)
+    st = oracle.stats(vol)
+    prm = oracle.derive_params(st, 2)
+    want = {f: oracle.filter_volume(vol, f, 2, params=prm) for f in FILTERS}
+    t = torch.from_numpy(vol).cuda()
+    with lnf.Context() as c:
+        for ids in ([oracle.MEAN, oracle.MEAN, oracle.SIGMA, oracle.ENTROPY, oracle.OKADA],
+                    [oracle.SIGMA, oracle.OKADA], [oracle.OURS, oracle.OKADA, oracle.MEAN],
+                    [oracle.OKADA, oracle.ENTROPY, oracle.SIGMA, oracle.MEAN, oracle.OURS, oracle.SIGMA]):
+            outs, H = c.filter_multi(t, ids, 2)
+            Hh = H.cpu().numpy()
+            for i, f in enumerate(ids):
+                got = outs[i].cpu().numpy()
+                assert np.array_equal(got, want[f]), (ids, i, f)
+                hw = oracle.image_entropy(oracle.histogram(want[f]))
+                assert abs(Hh[i + 1] - hw) <= 1e-9 * max(1.0, hw), (ids, i, f)
