@@ -731,9 +731,11 @@ extern "C" lnf_status lnf_spacing_radii(double extent, const double spacing[3], 
 }
 
 // lnf_filter_multi, recording `after[i]` on the context stream once filter i
-// has been enqueued (when `after` is not null)
+// has been enqueued (when `after` is not null) and listing in `order` the filter
+// indices in the order their events were recorded (when `order` is not null)
 static lnf_status multi_impl(lnf_ctx *ctx, int radius, const void *in, const int64_t dims[3], int dtype, int n,
-                             const int *filter_ids, void *const *outs, double *d_entropy, cudaEvent_t *after);
+                             const int *filter_ids, void *const *outs, double *d_entropy, cudaEvent_t *after,
+                             int *order = nullptr);
 
 extern "C" lnf_status lnf_filter_multi(lnf_ctx *ctx, int radius, const void *in, const int64_t dims[3], int dtype,
                                        int n, const int *filter_ids, void *const *outs, double *d_entropy)
@@ -743,7 +745,8 @@ extern "C" lnf_status lnf_filter_multi(lnf_ctx *ctx, int radius, const void *in,
 }
 
 static lnf_status multi_impl(lnf_ctx *ctx, int radius, const void *in, const int64_t dims[3], int dtype, int n,
-                             const int *filter_ids, void *const *outs, double *d_entropy, cudaEvent_t *after)
+                             const int *filter_ids, void *const *outs, double *d_entropy, cudaEvent_t *after,
+                             int *order)
 {
     if (!ctx)
         return LNF_EINVAL;
@@ -789,6 +792,7 @@ static lnf_status multi_impl(lnf_ctx *ctx, int radius, const void *in, const int
         }
     const bool fuse = once && slot4[0] >= 0 && slot4[1] >= 0 && slot4[2] >= 0 && slot4[3] >= 0 && !ctx->no_fused &&
                       !ctx->no_fast && lnf_fast_covers(LNF_SIGMA, radius, ctx->cfg.cluster_offset);
+    int done = 0;
     auto run = [&](int i) -> lnf_status {
         u64 *oh = d_entropy ? ctx->out_hist + (size_t)i * LNF_LEVELS_U16 : nullptr;
         const bool f = lnf_fast_covers(filter_ids[i], radius, ctx->cfg.cluster_offset);
@@ -796,6 +800,8 @@ static lnf_status multi_impl(lnf_ctx *ctx, int radius, const void *in, const int
                                    ctx->vs, oh, st, f ? pitch : 0);
         if (r == LNF_OK && after && cudaEventRecord(after[i], st) != cudaSuccess)
             r = lnf_fail(ctx, LNF_ECUDA, "event record failed");
+        if (r == LNF_OK && order)
+            order[done++] = i;
         return r;
     };
     auto in_fused = [&](int i) { return fuse && filter_ids[i] >= LNF_MEAN && filter_ids[i] <= LNF_OKADA; };
@@ -896,12 +902,16 @@ extern "C" lnf_status lnf_filter_multi_host(lnf_ctx *ctx, int radius, const void
     }
     cudaStream_t st = ctx->stream, cs = ctx->copy_stream;
     CK(cudaMemcpyAsync(ctx->st_in, in, bytes, cudaMemcpyHostToDevice, st));
+    int order[LNF_MAX_PACK];
     if ((s = multi_impl(ctx, radius, ctx->st_in, dims, dtype, n, filter_ids, ctx->st_out.data(), ctx->d_H,
-                        ctx->filter_done.data())) != LNF_OK) {
+                        ctx->filter_done.data(), order)) != LNF_OK) {
         cudaStreamSynchronize(st);
         return s;
     }
-    for (int i = 0; i < n; ++i) {
+    // in the order the outputs become ready (the fused pass finishes four at once, after
+    // the filters that run before it)
+    for (int k = 0; k < n; ++k) {
+        const int i = order[k];
         CK(cudaStreamWaitEvent(cs, ctx->filter_done[i], 0));
         CK(cudaMemcpyAsync(outs[i], ctx->st_out[i], bytes, cudaMemcpyDeviceToHost, cs));
     }
