@@ -45,8 +45,6 @@ constexpr int kThreads = kWarps * 32;
 constexpr int kRows = 4;                  // rows per lane
 constexpr int kTX = 128;                  // 32 lanes x 4 columns
 constexpr int kTY = kWarps * kRows;       // 32
-constexpr int kPF = 2;                    // planes prefetched beyond the ones in use
-constexpr int kHistWin = 4096;
 
 __device__ __forceinline__ int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
 
