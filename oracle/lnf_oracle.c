@@ -25,7 +25,7 @@
 #include <stddef.h>
 
 typedef struct oracle_params {
-    int32_t filter_id;     /* 0..4 */
+    int32_t filter_id;     /* 0..4 the paper's five (Fig. 5 order), 5..7 the variants below */
     int32_t radius;        /* r >= 0, kernel size M = 2r+1 (Eq. 3 needs M odd) */
     int32_t offset;        /* d: diagonal cluster offset, (+-d,+-d,+-d); d=1 is distance sqrt(3) */
     uint32_t threshold;    /* T: Otsu (Eq. 1) or fixed; 0 disables the gate */
