@@ -163,7 +163,9 @@ lnf_status lnf_filter_volume(lnf_ctx *ctx, int filter_id, int radius, const void
  * statistics once: outs[i] = filter_ids[i](in).  If d_entropy is not NULL it is
  * a DEVICE array of n+1 doubles that receives the image entropy (Fig. 4) of the
  * input and of each output, in that order; the output histograms are fused
- * into the filter kernels.  Enqueued; no host synchronisation.
+ * into the filter kernels.  Enqueued; no host synchronisation.  The outputs must
+ * not overlap the input or one another (LNF_EINVAL): mean, sigma, entropy filter
+ * and Okada may be computed together in one pass.
  */
 lnf_status lnf_filter_multi(lnf_ctx *ctx, int radius, const void *in, const int64_t dims[3], int dtype,
                             int n, const int *filter_ids, void *const *outs, double *d_entropy);

@@ -761,6 +761,10 @@ static lnf_status multi_impl(lnf_ctx *ctx, int radius, const void *in, const int
             return s;
         if (!outs[i] || overlaps(in, bytes, outs[i], bytes))
             return lnf_fail(ctx, LNF_EINVAL, "output %d is null or overlaps the input", i);
+        // (one launch may write several outputs at once: they must be distinct)
+        for (int k = 0; k < i; ++k)
+            if (overlaps(outs[k], bytes, outs[i], bytes))
+                return lnf_fail(ctx, LNF_EINVAL, "outputs %d and %d overlap", k, i);
     }
     cudaStream_t st = ctx->stream;
     if ((s = lnf_analyze(ctx, in, dims, dtype, ctx->vs, st)) != LNF_OK)
