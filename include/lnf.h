@@ -300,11 +300,16 @@ lnf_status lnf_selftest_wait(lnf_ctx *ctx, double limit_ms, double *elapsed_ms);
  * Scratch: one file-scope device array of 65536 uint32 counters (256 KiB),
  * present on every GPU that loads the library until the process exits.  The
  * first call on a device (with that device current) looks up the array's
- * address; make it before any stream capture.  Every call zeroes and reuses
+ * address and has CUDA load all of this entry point's kernels (under lazy
+ * module loading a kernel is otherwise loaded, possibly allocating, at its
+ * first launch); make that first call before any stream capture.  The looked-up
+ * address does not survive cudaDeviceReset.  Every call zeroes and reuses
  * the same array, so calls that overlap on the GPU race: order them on one
  * stream.  Returns LNF_EINVAL for null pointers, a bad dtype, dims < 1 or more
- * than 2^32 - 1 voxels (the counters are 32-bit), LNF_ECUDA if a launch fails.
- * Asynchronous: read *d_entropy after synchronising the stream.
+ * than 2^32 - 1 voxels (the counters are 32-bit), LNF_ECUDA if a launch fails
+ * or if a CUDA error was already pending from earlier work (that error is
+ * left set for the caller).  Asynchronous: read *d_entropy after
+ * synchronising the stream.
  */
 lnf_status lnf_entropy_noalloc(const void *vol, const int64_t dims[3], int dtype, double *d_entropy,
                                void *stream);

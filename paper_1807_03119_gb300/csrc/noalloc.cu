@@ -11,8 +11,17 @@
 //
 // Set-up: the first call on each device, with that device current, looks up
 // the array's device address with cudaGetSymbolAddress (host code cannot use
-// the array's name as a device address) and caches it.  Make that first call
-// before any stream capture.
+// the array's name as a device address) and caches it, and makes CUDA load
+// all four kernels of this file (cudaFuncGetAttributes on each).  With lazy
+// module loading, CUDA's default, a kernel is otherwise loaded -- which can
+// allocate device memory -- the first time it is launched, so a later first
+// call with the other dtype could still load code.  Make that first call
+// before any stream capture.  The cached address does not survive a
+// cudaDeviceReset of that device (the process would need to restart).
+//
+// A CUDA error left pending by the caller's earlier work is reported as
+// LNF_ECUDA before anything is enqueued and is left in place (not cleared), so
+// that it is not mistaken for a failure of this call's own launches.
 //
 // Every call reuses the same array and zeroes it first; two calls whose work
 // overlaps on the GPU (different streams, or different host threads) race on
@@ -102,6 +111,9 @@ extern "C" lnf_status lnf_entropy_noalloc(const void *vol, const int64_t dims[3]
     if (n128 > 0xFFFFFFFFull)
         return LNF_EINVAL;
     const u64 n = (u64)n128;
+    // an error pending from earlier work is the caller's: report it, leave it set
+    if (cudaPeekAtLastError() != cudaSuccess)
+        return LNF_ECUDA;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices)
         return LNF_ECUDA;
@@ -116,6 +128,13 @@ extern "C" lnf_status lnf_entropy_noalloc(const void *vol, const int64_t dims[3]
             int s = 0;
             if (cudaDeviceGetAttribute(&s, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || s < 1)
                 s = 1;
+            // load every kernel now, so that no later call loads code
+            cudaFuncAttributes fa;
+            if (cudaFuncGetAttributes(&fa, k_clear) != cudaSuccess ||
+                cudaFuncGetAttributes(&fa, k_count<uint8_t>) != cudaSuccess ||
+                cudaFuncGetAttributes(&fa, k_count<uint16_t>) != cudaSuccess ||
+                cudaFuncGetAttributes(&fa, k_reduce) != cudaSuccess)
+                return LNF_ECUDA;
             g_sms[dev] = s;
             g_addr[dev] = static_cast<u32 *>(p);
         }

@@ -1,13 +1,15 @@
 """lnf_entropy_noalloc, the entry point for callers that cannot allocate
-device memory (no context, no cudaMalloc): its result must equal the ordinary
-lnf_entropy call's, on two calls in a row (the shared scratch array keeps the
-previous call's counts and must be cleared each time).  This file is collected
-last on purpose."""
+device memory (no context, no cudaMalloc): its result must equal the oracle's
+image entropy and the ordinary lnf_entropy call's, on two calls in a row (the
+shared scratch array keeps the previous call's counts and must be cleared each
+time), with the dtype changing between calls.  This file is collected last on
+purpose."""
 import ctypes
 
 import numpy as np
 import pytest
 
+import oracle
 import phantoms
 
 pytestmark = pytest.mark.gpu
@@ -33,15 +35,18 @@ def _dims(vol):
     return (ctypes.c_int64 * 3)(nx, ny, nz)
 
 
-def test_noalloc_entropy_matches_lnf_entropy(lib):
+def test_noalloc_entropy_matches_oracle_and_lnf_entropy(lib):
     L, fn = lib
-    vols = [phantoms.P1(), phantoms.insect_phantom((72, 40, 33), 5, "u16"),
-            phantoms.random_volume((31, 17, 9), 6, "u16")]
+    # the dtype changes from call to call (u16 first, then u8, then u16 again)
+    vols = [phantoms.insect_phantom((72, 40, 33), 5, "u16"), phantoms.P1(),
+            phantoms.random_volume((31, 17, 9), 6, "u16"), phantoms.random_volume((5, 3, 2), 7, "u8")]
     stream = torch.cuda.current_stream()
     with L.Context() as ctx:
         for vol in vols:
+            want = oracle.image_entropy(oracle.histogram(vol))   # the definition, on the host
             t = torch.from_numpy(vol).cuda()
             ref = ctx.entropy(t)           # the existing entry point
+            assert abs(ref - want) <= 1e-9 * max(1.0, abs(want)), (ref, want)
             dH = torch.full((1,), -1.0, dtype=torch.float64, device="cuda")
             for call in range(2):          # two calls in a row reuse the scratch array
                 rc = fn(t.data_ptr(), _dims(vol), 0 if vol.dtype == np.uint8 else 1, dH.data_ptr(),
@@ -49,6 +54,7 @@ def test_noalloc_entropy_matches_lnf_entropy(lib):
                 assert rc == 0
                 torch.cuda.synchronize()
                 got = float(dH.item())
+                assert abs(got - want) <= 1e-9 * max(1.0, abs(want)), (call, got, want)
                 assert abs(got - ref) <= 1e-9 * max(1.0, abs(ref)), (call, got, ref)
 
 
