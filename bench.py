@@ -79,8 +79,10 @@ def algorithmic(kind, n_pass, hbm_gbs, alu_tops):
     M3 = (2 * RADIUS + 1) ** 3
     if kind == "stats":
         return "hbm", N_VOX * ES
-    if kind == "filter:fused4":   # mean, sigma, entropy filter, Okada: read once, four outputs written
-        return "hbm", N_VOX * ES * 5
+    if kind == "filter:gate":     # the five filters: read once, five outputs written
+        return "hbm", N_VOX * ES * 6
+    if kind.startswith("gate:"):      # one filter through the gate-first kernel: read once, write once
+        return "hbm", N_VOX * ES * 2
     if kind.startswith("filter:"):
         f = kind.split(":")[1]
         hbm = N_VOX * ES * 2   # read the input once, write the output once
@@ -98,12 +100,15 @@ KIND_SOURCES = {
     "stats": ["stats.cu"],
     "params": ["stats.cu"],
     "entropy": ["stats.cu"],
-    "filter:ours": ["fast.cu", "sparse.cu"],
-    "filter:mean": ["fast2.cuh", "fast2_box.cu", "sparse.cu"],
-    "filter:entropy": ["fast2.cuh", "fast2_box.cu", "sparse.cu"],
-    "filter:sigma": ["fast2.cuh", "fast2_tap.cu", "sparse.cu"],
-    "filter:okada": ["fast2.cuh", "fast2_tap.cu", "sparse.cu"],
-    "filter:fused4": ["fast2.cuh", "fused.cu"],
+    "filter:ours": ["fast.cu"],
+    "filter:mean": ["fast2.cuh", "fast2_box.cu"],
+    "filter:entropy": ["fast2.cuh", "fast2_box.cu"],
+    "filter:sigma": ["fast2.cuh", "fast2_tap.cu"],
+    "filter:okada": ["fast2.cuh", "fast2_tap.cu"],
+    "filter:gate": ["gate.cuh", "gate_u16.cu"],
+    "gate:ours": ["gate.cuh", "gate_u16.cu"],
+    "gate:scan": ["gate.cuh", "gate_u16.cu"],
+    "gate:eval": ["gate.cuh", "gate_u16.cu"],
 }
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "dram_traffic_512cubed_u16_r2.txt")
 
@@ -139,8 +144,11 @@ def kind_of_kernel(name):
     m = re.search(r"k_fast2<[^,]+, \d+, (\d+)", name)
     if m:
         return "filter:" + {0: "mean", 1: "sigma", 2: "entropy", 3: "okada"}[int(m.group(1))]
-    if "k_fused4" in name:
-        return "filter:fused4"
+    m = re.search(r"k_eval<[^,]+, \d+, (\d+)>", name)
+    if m:   # the filter set: 3 all five (a multi-filter call), 1 the paper's filter alone, 2 comparison filters
+        return {3: "gate:eval", 1: "gate:eval_ours", 2: "gate:eval_cube"}[int(m.group(1))]
+    if "gatek::k_scan" in name:
+        return "gate:scan"
     if "k_ours_fast" in name:
         return "filter:ours"
     for k, kind in (("k_stats_batched", None), ("k_stats<", "stats"), ("k_params", "params"),
@@ -430,12 +438,12 @@ def main():
     T = ctx.params()["threshold"]
     n_pass = int(np.count_nonzero(vol >= T))
     rooflines = {}
-    # while the fused kernel does the four cube filters, their ring kernels return at once
-    cube = ("filter:mean", "filter:sigma", "filter:entropy", "filter:okada")
-    fused_worked = "filter:fused4" in kern and all(k not in kern or kern[k][1] < 0.1 * kern["filter:fused4"][1]
-                                                   for k in cube)
+    # while the gate-first kernel does the five filters, their ring kernels return at once
+    five = ("filter:mean", "filter:sigma", "filter:entropy", "filter:okada", "filter:ours")
+    gate_worked = "filter:gate" in kern and all(k not in kern or kern[k][1] < 0.1 * kern["filter:gate"][1]
+                                                for k in five)
     for kind, (n, tot) in kern.items():
-        if fused_worked and kind in cube:
+        if gate_worked and kind in five:
             continue
         bound, work = algorithmic(kind, n_pass, pk["hbm_gbs"], alu_peak_tops(sm_mhz))
         if bound is None or n == 0:

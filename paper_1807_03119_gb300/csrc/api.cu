@@ -243,16 +243,15 @@ extern "C" lnf_status lnf_create(const lnf_config *cfg_in, lnf_ctx **out)
                 cudaSuccess &&
             q == cudaDriverEntryPointSuccess)
             ctx->encode = reinterpret_cast<PFN_encodeTiled>(fn);
-        // test hooks: force the plain-load path / the generic kernel / the ring kernels
-        // alone / no fused kernel
+        // test hooks: force the plain-load path / the generic kernel / the ring
+        // kernels alone (no gate-first kernels)
         const char *ev = getenv("LNF_FORCE_PLAIN");
         ctx->no_tma = ev && ev[0] == '1';
         ev = getenv("LNF_FORCE_GENERIC");
         ctx->no_fast = ev && ev[0] == '1';
-        ev = getenv("LNF_NO_GATHER");
-        ctx->no_gather = ev && ev[0] == '1';
-        ev = getenv("LNF_NO_FUSED");
-        ctx->no_fused = ev && ev[0] == '1';
+        ev = getenv("LNF_NO_GATE");
+        ctx->no_gate = ev && ev[0] == '1';
+
         if (cudaDeviceSynchronize() != cudaSuccess)
             s = LNF_ECUDA;
     } while (0);
@@ -282,6 +281,7 @@ extern "C" void lnf_destroy(lnf_ctx *ctx)
     cudaFree(ctx->d_err);
     cudaFree(ctx->d_counter);
     cudaFree(ctx->pitched);
+    cudaFree(ctx->gate_mask_buf);
     cudaFree(ctx->f32_lv);
     cudaFree(ctx->d_range);
     for (cudaEvent_t e : ctx->filter_done)
@@ -591,7 +591,8 @@ static lnf_status stage_input(lnf_ctx *ctx, const void *in, const int64_t dims[3
 // Run one filter job on an analysed volume, through the fastest kernel that covers it.
 lnf_status lnf_run_one(lnf_ctx *ctx, int filter, int radius, const void *in, void *out, const int64_t dims[3],
                        int dtype, const int64_t *roi_o, const int64_t *roi_d, const VolScratch &vs,
-                       u64 *out_hist, cudaStream_t stream, int64_t pitch, const int *rad3, const int *off3)
+                       u64 *out_hist, cudaStream_t stream, int64_t pitch, const int *rad3, const int *off3,
+                       const void *orig)
 {
     FilterPack &pk = ctx->pack;
     pk.n_jobs = 1;
@@ -605,7 +606,9 @@ lnf_status lnf_run_one(lnf_ctx *ctx, int filter, int radius, const void *in, voi
     const int rec = lnf_prof_begin(ctx, stream);
     if (!ctx->no_fast) {
         int handled = 0;
-        s = lnf_fast_dispatch(ctx, pk.jobs[0], pk.jobs[0].tmap_idx >= 0 ? &pk.tmaps[0] : nullptr, stream, &handled);
+        pk.jobs[0].orig = orig;
+        s = lnf_fast_dispatch(ctx, pk.jobs[0], pk.jobs[0].tmap_idx >= 0 ? &pk.tmaps[0] : nullptr, stream, &handled,
+                              nullptr, 1);
         if (s != LNF_OK || handled) {
             lnf_prof_end(ctx, rec, filter_name(filter), stream, handled ? handled : 1);
             return s;
@@ -642,7 +645,7 @@ extern "C" lnf_status lnf_filter_volume(lnf_ctx *ctx, int filter_id, int radius,
         (s = stage_input(ctx, in, dims, dtype, ctx->stream, &src, &pitch)) != LNF_OK)
         return s;
     return lnf_run_one(ctx, filter_id, radius, src, out, dims, dtype, nullptr, nullptr, ctx->vs, nullptr,
-                       ctx->stream, pitch);
+                       ctx->stream, pitch, nullptr, nullptr, in);
 }
 
 extern "C" lnf_status lnf_filter_roi(lnf_ctx *ctx, int filter_id, int radius, const void *in,
@@ -783,62 +786,60 @@ static lnf_status multi_impl(lnf_ctx *ctx, int radius, const void *in, const int
     int64_t pitch = 0;
     if (any_fast && (s = stage_input(ctx, in, dims, dtype, st, &src, &pitch)) != LNF_OK)
         return s;
-    // mean, sigma, entropy filter and Okada, each asked for once, in one pass of the
-    // fused kernel while few voxels pass the gate (decided on the device; their
-    // ring kernels, launched after it, return at once then).  The other filters run
-    // first, so that copies of their outputs (`after`) overlap the fused pass.
-    int slot4[4] = {-1, -1, -1, -1};
+    // The filters of this call the gate-first kernel covers, each asked for once,
+    // in one launch (one read of the volume, one write per output) while few
+    // voxels pass the gate (decided on the device; their ring kernels, launched
+    // after it, return at once then).
+    int slot5[5] = {-1, -1, -1, -1, -1};
     bool once = true;
     for (int i = 0; i < n; ++i)
-        if (filter_ids[i] >= LNF_MEAN && filter_ids[i] <= LNF_OKADA) {
-            once = once && slot4[filter_ids[i]] < 0;
-            slot4[filter_ids[i]] = i;
+        if (filter_ids[i] >= LNF_MEAN && filter_ids[i] <= LNF_OURS) {
+            once = once && slot5[filter_ids[i]] < 0;
+            slot5[filter_ids[i]] = i;
         }
-    const bool fuse = once && slot4[0] >= 0 && slot4[1] >= 0 && slot4[2] >= 0 && slot4[3] >= 0 && !ctx->no_fused &&
-                      !ctx->no_fast && lnf_fast_covers(LNF_SIGMA, radius, ctx->cfg.cluster_offset);
-    int done = 0;
-    auto run = [&](int i) -> lnf_status {
-        u64 *oh = d_entropy ? ctx->out_hist + (size_t)i * LNF_LEVELS_U16 : nullptr;
-        const bool f = lnf_fast_covers(filter_ids[i], radius, ctx->cfg.cluster_offset);
-        lnf_status r = lnf_run_one(ctx, filter_ids[i], radius, f ? src : in, outs[i], dims, dtype, nullptr, nullptr,
-                                   ctx->vs, oh, st, f ? pitch : 0);
-        if (r == LNF_OK && after && cudaEventRecord(after[i], st) != cudaSuccess)
-            r = lnf_fail(ctx, LNF_ECUDA, "event record failed");
-        if (r == LNF_OK && order)
-            order[done++] = i;
-        return r;
-    };
-    auto in_fused = [&](int i) { return fuse && filter_ids[i] >= LNF_MEAN && filter_ids[i] <= LNF_OKADA; };
-    ctx->fused_mask = 0;
-    for (int i = 0; i < n; ++i)
-        if (!in_fused(i) && (s = run(i)) != LNF_OK)
-            return s;
-    if (fuse) {
+    ctx->gate_mask = 0;
+    if (once && !ctx->no_gate && !ctx->no_fast && n > 0) {
         FilterPack &pk = ctx->pack;
         pk.n_jobs = 1;
-        if ((s = lnf_make_job(ctx, pk, 0, LNF_MEAN, radius, src, outs[slot4[0]], dims, dtype, nullptr, nullptr,
+        if ((s = lnf_make_job(ctx, pk, 0, filter_ids[0], radius, src, outs[0], dims, dtype, nullptr, nullptr,
                               ctx->vs, nullptr, pitch)) != LNF_OK)
             return s;
-        void *o4[4];
-        u64 *h4[4];
-        for (int f = 0; f < 4; ++f) {
-            o4[f] = outs[slot4[f]];
-            h4[f] = d_entropy ? ctx->out_hist + (size_t)slot4[f] * LNF_LEVELS_U16 : nullptr;
-        }
-        int handled = 0;
-        const int rec = lnf_prof_begin(ctx, st);
-        s = lnf_fused_launch(ctx, pk.jobs[0], o4, h4, st, &handled);
-        lnf_prof_end(ctx, rec, "filter:fused4", st, 1);
-        if (s != LNF_OK)
-            return s;
-        ctx->fused_mask = handled ? 0xF : 0;
-        for (int i = 0; i < n; ++i)
-            if (in_fused(i) && (s = run(i)) != LNF_OK) {
-                ctx->fused_mask = 0;
-                return s;
+        pk.jobs[0].orig = in;
+        void *o5[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+        u64 *h5[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+        int mask = 0;
+        for (int f = 0; f < 5; ++f)
+            if (slot5[f] >= 0 && lnf_gate_covers(pk.jobs[0], f)) {
+                o5[f] = outs[slot5[f]];
+                h5[f] = d_entropy ? ctx->out_hist + (size_t)slot5[f] * LNF_LEVELS_U16 : nullptr;
+                mask |= 1 << f;
             }
+        if (mask) {
+            int handled = 0;
+            const int rec = lnf_prof_begin(ctx, st);
+            s = lnf_gate_launch(ctx, pk.jobs[0], o5, h5, st, &handled);
+            lnf_prof_end(ctx, rec, "filter:gate", st, 2);   // the scan and the evaluation
+            if (s != LNF_OK)
+                return s;
+            ctx->gate_mask = handled ? mask : 0;
+        }
     }
-    ctx->fused_mask = 0;
+    int done = 0;
+    for (int i = 0; i < n; ++i) {
+        u64 *oh = d_entropy ? ctx->out_hist + (size_t)i * LNF_LEVELS_U16 : nullptr;
+        const bool f = lnf_fast_covers(filter_ids[i], radius, ctx->cfg.cluster_offset);
+        s = lnf_run_one(ctx, filter_ids[i], radius, f ? src : in, outs[i], dims, dtype, nullptr, nullptr, ctx->vs,
+                        oh, st, f ? pitch : 0, nullptr, nullptr, in);
+        if (s == LNF_OK && after && cudaEventRecord(after[i], st) != cudaSuccess)
+            s = lnf_fail(ctx, LNF_ECUDA, "event record failed");
+        if (s != LNF_OK) {
+            ctx->gate_mask = 0;
+            return s;
+        }
+        if (order)
+            order[done++] = i;
+    }
+    ctx->gate_mask = 0;
     if (d_entropy) {
         CK(cudaMemcpyAsync(d_entropy, &ctx->vs.prm->H_in, sizeof(double), cudaMemcpyDeviceToDevice, st));
         EntropyPack ep;

@@ -234,7 +234,7 @@ struct FastArgs {
     u64 *out_hist;
     u32 *counter;
     u32 *err;
-    int paired;                           // 1: launched beside the gather kernel, which may take the job
+    int gated;                            // 1: launched beside the gate-first kernel, which may take the job
 };
 
 // the ring-column cell (tile column -1 or kTX, tile row -1 .. kTY) a lane
@@ -666,8 +666,8 @@ template <typename T, int R, bool MASK>
 __global__ void __launch_bounds__(kThreads, 2) k_ours_fast(const __grid_constant__ CUtensorMap tmap, const FastArgs a)
 {
     typedef FGeo<T, R> G;
-    if (a.paired && lnf_gather_mode(*a.prm, LNF_OURS))
-        return;   // few voxels pass the gate: the gather kernel does the work
+    if (a.gated && lnf_gate_mode(*a.prm))
+        return;   // few voxels pass the gate: the gate-first kernel does the work
     extern __shared__ __align__(128) unsigned char smem_raw[];
     unsigned char *smem = smem_raw + ((128 - (lnfdev::smem_u32(smem_raw) & 127)) & 127);
     __shared__ int s_item, s_abort;
@@ -707,7 +707,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_ours_fast(const __grid_constant
 
 template <typename T, int R>
 lnf_status launch(lnf_ctx *ctx, const FilterJob &j, cudaStream_t st, u64 *out_hist, u32 *counter, int *handled,
-                  int paired)
+                  int gated)
 {
     typedef FGeo<T, R> G;
     // this kernel's own descriptor: box = its tile + halo
@@ -746,7 +746,7 @@ lnf_status launch(lnf_ctx *ctx, const FilterJob &j, cudaStream_t st, u64 *out_hi
     a.out_hist = out_hist;
     a.counter = counter ? counter : ctx->d_counter + 8;
     a.err = ctx->d_err;
-    a.paired = paired;
+    a.gated = gated;
     void (*kern)(const CUtensorMap, const FastArgs) = a.roi ? k_ours_fast<T, R, true> : k_ours_fast<T, R, false>;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, G::SMEM) != cudaSuccess)
         return lnf_fail(ctx, LNF_ECUDA, "fast kernel: shared memory attribute");
@@ -781,41 +781,64 @@ bool lnf_fast_covers(int filter, int radius, int offset)
 }
 
 lnf_status lnf_fast_dispatch(lnf_ctx *ctx, const FilterJob &job, const CUtensorMap *tmap, cudaStream_t stream,
-                             int *handled, u32 *counter)
+                             int *handled, u32 *counter, int allow_gate)
 {
     *handled = 0;
     if (!tmap || job.aniso || !lnf_fast_covers(job.filter, job.radius, job.offset))
         return LNF_OK;
-    // whole volumes at radius 1..2 also get the gather kernel, which takes the
-    // job when few voxels pass the gate (decided on the device); it is launched
-    // only once the ring kernel has taken the job, so that no other kernel
-    // writes the output (or its histogram) a second time
-    // (a filter the fused kernel of this multi-filter call covers is not paired)
-    const int pair = !ctx->no_gather && !((ctx->fused_mask >> job.filter) & 1) && lnf_gather_covers(job);
+    // Whole volumes also get the gate-first kernels, which take the job when few
+    // voxels pass the gate (decided on the device); the ring kernel then returns
+    // at once.  A multi-filter call may have launched them for this filter
+    // already.  A single comparison filter stays on its ring kernel: the
+    // gate-first evaluation computes the four cube filters together, which for
+    // one filter alone is slower.
+    const bool in_multi = (ctx->gate_mask >> job.filter) & 1;
+    const bool own_gate = allow_gate && !in_multi && !ctx->no_gate && job.filter == LNF_OURS &&
+                          lnf_gate_covers(job, job.filter);
     lnf_status s = LNF_OK;
+    // the gate-first kernels first: whether they could be launched decides whether
+    // the ring kernel may leave the job to them
+    int own = 0;
+    if (own_gate) {
+        static const char *names[5] = {"gate:mean", "gate:sigma", "gate:entropy", "gate:okada", "gate:ours"};
+        void *outs[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+        u64 *hists[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+        outs[job.filter] = job.out;
+        hists[job.filter] = job.out_hist;
+        const int rec = lnf_prof_begin(ctx, stream);   // the gate kernels alone (counted by the caller)
+        s = lnf_gate_launch(ctx, job, outs, hists, stream, &own);
+        lnf_prof_end(ctx, rec, names[job.filter], stream, 0);
+        if (s != LNF_OK)
+            return s;
+    }
+    const int gated = in_multi || own ? 1 : 0;
     if (job.filter != LNF_OURS) {
-        s = lnf_fast2_dispatch(ctx, job, tmap, stream, handled, counter, pair);
+        s = lnf_fast2_dispatch(ctx, job, tmap, stream, handled, counter, gated);
     } else {
         u64 *oh = job.out_hist;
         if (job.dtype == LNF_U8) {
             switch (job.radius) {
-            case 1: s = launch<uint8_t, 1>(ctx, job, stream, oh, counter, handled, pair); break;
-            case 2: s = launch<uint8_t, 2>(ctx, job, stream, oh, counter, handled, pair); break;
-            case 3: s = launch<uint8_t, 3>(ctx, job, stream, oh, counter, handled, pair); break;
-            default: s = launch<uint8_t, 4>(ctx, job, stream, oh, counter, handled, pair); break;
+            case 1: s = launch<uint8_t, 1>(ctx, job, stream, oh, counter, handled, gated); break;
+            case 2: s = launch<uint8_t, 2>(ctx, job, stream, oh, counter, handled, gated); break;
+            case 3: s = launch<uint8_t, 3>(ctx, job, stream, oh, counter, handled, gated); break;
+            default: s = launch<uint8_t, 4>(ctx, job, stream, oh, counter, handled, gated); break;
             }
         } else {
             switch (job.radius) {
-            case 1: s = launch<uint16_t, 1>(ctx, job, stream, oh, counter, handled, pair); break;
-            case 2: s = launch<uint16_t, 2>(ctx, job, stream, oh, counter, handled, pair); break;
-            case 3: s = launch<uint16_t, 3>(ctx, job, stream, oh, counter, handled, pair); break;
-            default: s = launch<uint16_t, 4>(ctx, job, stream, oh, counter, handled, pair); break;
+            case 1: s = launch<uint16_t, 1>(ctx, job, stream, oh, counter, handled, gated); break;
+            case 2: s = launch<uint16_t, 2>(ctx, job, stream, oh, counter, handled, gated); break;
+            case 3: s = launch<uint16_t, 3>(ctx, job, stream, oh, counter, handled, gated); break;
+            default: s = launch<uint16_t, 4>(ctx, job, stream, oh, counter, handled, gated); break;
             }
         }
     }
-    if (s == LNF_OK && *handled && pair) {
-        s = lnf_gather_launch(ctx, job, stream);
-        *handled = 2;   // two kernels launched
-    }
+    if (s != LNF_OK)
+        return s;
+    // where the gate kernels may write this output, the ring kernel must be there
+    // to take the dense case: no other kernel may write it
+    if (gated && !*handled)
+        return lnf_fail(ctx, LNF_ECUDA, "ring kernel not launchable beside the gate-first kernels");
+    if (own)
+        *handled = 3;   // the two gate kernels and the ring kernel
     return s;
 }

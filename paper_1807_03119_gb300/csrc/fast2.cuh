@@ -133,8 +133,7 @@ struct Args2 {
     u32 *err;
     u32 one;        // always 1; a multiplier the compiler cannot fold, so that adds
                     // written as multiply-adds issue on the FMA pipe (see tap_items)
-    int paired;     // 1: launched beside the gather kernel, which may take the job (lnf_gather_mode)
-    int fused;      // 1: launched beside the fused kernel of a multi-filter call (lnf_fused_mode)
+    int gated;      // 1: launched beside the gate-first kernel, which may take the job (lnf_gate_mode)
 };
 
 // shared histogram of nonzero outputs (window [hbase, hbase + bins)), zero count by difference
@@ -256,8 +255,8 @@ __global__ void __launch_bounds__(kThreads, (K2Smem<T, R, FILTER>::BOX && R > 2)
     k_fast2(const __grid_constant__ CUtensorMap tmap, const Args2 a)
 {
     typedef K2Smem<T, R, FILTER> S;
-    if ((a.paired && lnf_gather_mode(*a.prm, FILTER)) || (a.fused && lnf_fused_mode(*a.prm)))
-        return;   // few voxels pass the gate: the gather or the fused kernel does the work
+    if (a.gated && lnf_gate_mode(*a.prm))
+        return;   // few voxels pass the gate: the gate-first kernel does the work
     extern __shared__ __align__(128) unsigned char smem_raw[];
     unsigned char *smem = smem_raw + ((128 - (lnfdev::smem_u32(smem_raw) & 127)) & 127);
     __shared__ int s_item, s_abort;
@@ -308,8 +307,7 @@ __global__ void __launch_bounds__(kThreads, (K2Smem<T, R, FILTER>::BOX && R > 2)
 }
 
 template <typename T, int R, int FILTER>
-lnf_status launch2(lnf_ctx *ctx, const FilterJob &j, cudaStream_t st, u32 *counter, int *handled, int paired,
-                   int fused)
+lnf_status launch2(lnf_ctx *ctx, const FilterJob &j, cudaStream_t st, u32 *counter, int *handled, int gated)
 {
     typedef K2Smem<T, R, FILTER> S;
     typedef typename S::G G;
@@ -354,8 +352,7 @@ lnf_status launch2(lnf_ctx *ctx, const FilterJob &j, cudaStream_t st, u32 *count
     a.counter = counter ? counter : ctx->d_counter + 9;
     a.err = ctx->d_err;
     a.one = 1u;
-    a.paired = paired;
-    a.fused = fused;
+    a.gated = gated;
     void (*kern)(const CUtensorMap, const Args2) = a.roi ? k_fast2<T, R, FILTER, true> : k_fast2<T, R, FILTER, false>;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, S::TOTAL) !=
         cudaSuccess)
@@ -375,14 +372,13 @@ lnf_status launch2(lnf_ctx *ctx, const FilterJob &j, cudaStream_t st, u32 *count
 }
 
 template <typename T, int FILTER>
-lnf_status by_radius(lnf_ctx *ctx, const FilterJob &j, cudaStream_t st, u32 *counter, int *handled, int paired)
+lnf_status by_radius(lnf_ctx *ctx, const FilterJob &j, cudaStream_t st, u32 *counter, int *handled, int gated)
 {
-    const int fused = (ctx->fused_mask >> j.filter) & 1;
     switch (j.radius) {
-    case 1: return launch2<T, 1, FILTER>(ctx, j, st, counter, handled, paired, fused);
-    case 2: return launch2<T, 2, FILTER>(ctx, j, st, counter, handled, paired, fused);
-    case 3: return launch2<T, 3, FILTER>(ctx, j, st, counter, handled, paired, fused);
-    default: return launch2<T, 4, FILTER>(ctx, j, st, counter, handled, paired, fused);
+    case 1: return launch2<T, 1, FILTER>(ctx, j, st, counter, handled, gated);
+    case 2: return launch2<T, 2, FILTER>(ctx, j, st, counter, handled, gated);
+    case 3: return launch2<T, 3, FILTER>(ctx, j, st, counter, handled, gated);
+    default: return launch2<T, 4, FILTER>(ctx, j, st, counter, handled, gated);
     }
 }
 

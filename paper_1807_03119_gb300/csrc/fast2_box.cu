@@ -349,12 +349,12 @@ __device__ void box_items(const Args2 &a, const CUtensorMap *tmap, unsigned char
 }  // namespace
 
 lnf_status lnf_fast2_box(lnf_ctx *ctx, const FilterJob &job, cudaStream_t stream, u32 *counter, int *handled,
-                         int paired)
+                         int gated)
 {
     const bool u8 = job.dtype == LNF_U8;
     if (job.filter == LNF_MEAN)
-        return u8 ? by_radius<uint8_t, LNF_MEAN>(ctx, job, stream, counter, handled, paired)
-                  : by_radius<uint16_t, LNF_MEAN>(ctx, job, stream, counter, handled, paired);
-    return u8 ? by_radius<uint8_t, LNF_ENTROPY>(ctx, job, stream, counter, handled, paired)
-              : by_radius<uint16_t, LNF_ENTROPY>(ctx, job, stream, counter, handled, paired);
+        return u8 ? by_radius<uint8_t, LNF_MEAN>(ctx, job, stream, counter, handled, gated)
+                  : by_radius<uint16_t, LNF_MEAN>(ctx, job, stream, counter, handled, gated);
+    return u8 ? by_radius<uint8_t, LNF_ENTROPY>(ctx, job, stream, counter, handled, gated)
+              : by_radius<uint16_t, LNF_ENTROPY>(ctx, job, stream, counter, handled, gated);
 }

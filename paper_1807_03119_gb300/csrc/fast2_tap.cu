@@ -514,7 +514,7 @@ __device__ void tap_items(const Args2 &a, const CUtensorMap *tmap, unsigned char
 // Route mean / sigma / entropy / Okada jobs on TMA-able volumes (whole or a
 // region of interest) at radius 1..4 (sigma 1..2) to the specialised kernels.
 lnf_status lnf_fast2_dispatch(lnf_ctx *ctx, const FilterJob &job, const CUtensorMap *tmap, cudaStream_t stream,
-                              int *handled, u32 *counter, int paired)
+                              int *handled, u32 *counter, int gated)
 {
     *handled = 0;
     if (!tmap || job.aniso || job.filter == LNF_OURS || !lnf_fast_covers(job.filter, job.radius, job.offset))
@@ -522,11 +522,11 @@ lnf_status lnf_fast2_dispatch(lnf_ctx *ctx, const FilterJob &job, const CUtensor
     const bool u8 = job.dtype == LNF_U8;
     switch (job.filter) {
     case LNF_MEAN:
-    case LNF_ENTROPY: return lnf_fast2_box(ctx, job, stream, counter, handled, paired);
-    case LNF_SIGMA: return u8 ? by_radius<uint8_t, LNF_SIGMA>(ctx, job, stream, counter, handled, paired)
-                              : by_radius<uint16_t, LNF_SIGMA>(ctx, job, stream, counter, handled, paired);
-    case LNF_OKADA: return u8 ? by_radius<uint8_t, LNF_OKADA>(ctx, job, stream, counter, handled, paired)
-                              : by_radius<uint16_t, LNF_OKADA>(ctx, job, stream, counter, handled, paired);
+    case LNF_ENTROPY: return lnf_fast2_box(ctx, job, stream, counter, handled, gated);
+    case LNF_SIGMA: return u8 ? by_radius<uint8_t, LNF_SIGMA>(ctx, job, stream, counter, handled, gated)
+                              : by_radius<uint16_t, LNF_SIGMA>(ctx, job, stream, counter, handled, gated);
+    case LNF_OKADA: return u8 ? by_radius<uint8_t, LNF_OKADA>(ctx, job, stream, counter, handled, gated)
+                              : by_radius<uint16_t, LNF_OKADA>(ctx, job, stream, counter, handled, gated);
     default: return LNF_OK;
     }
 }

@@ -74,9 +74,10 @@ struct lnf_ctx {
     int fast_zlen = 16;         // z chunk length of a work item (specialised kernels)
     bool no_tma = false;        // testing: force plain loads
     bool no_fast = false;       // testing: force the generic kernel
-    bool no_gather = false;     // testing: never pair the gather kernel with the ring kernels
-    bool no_fused = false;      // testing: never launch the fused kernel of a multi-filter call
-    int fused_mask = 0;         // filter ids a launched fused kernel covers (during a multi-filter call)
+    bool no_gate = false;       // testing: never launch the gate-first kernel (the ring kernels work)
+    int gate_mask = 0;          // filter ids a launched gate-first kernel covers (during a multi-filter call)
+    void *gate_mask_buf = nullptr;   // gate-first path: the bitmask of passing voxels (grow-only)
+    size_t gate_mask_cap = 0;
     VolScratch vs;              // scratch of plain calls
     std::vector<VolScratch> pool;   // scratch of batched / resident volumes
     u64 *out_hist = nullptr;    // LNF_MAX_PACK output histograms of 65536 bins
@@ -156,7 +157,7 @@ lnf_status lnf_run_pack_counter(lnf_ctx *ctx, FilterPack &pk, int persistent, cu
 lnf_status lnf_run_one(lnf_ctx *ctx, int filter, int radius, const void *in, void *out, const int64_t dims[3],
                        int dtype, const int64_t *roi_o, const int64_t *roi_d, const VolScratch &vs,
                        u64 *out_hist, cudaStream_t stream, int64_t pitch = 0, const int *rad3 = nullptr,
-                       const int *off3 = nullptr);
+                       const int *off3 = nullptr, const void *orig = nullptr);
 // Row length in bytes of the padded copy of an input TMA cannot address (0: the
 // input itself is addressable: 16-byte-aligned base and row length)
 size_t lnf_pitched_row(const void *in, const int64_t dims[3], int dtype);
@@ -170,25 +171,26 @@ void lnf_prof_end(lnf_ctx *ctx, int rec, const char *name, cudaStream_t st, int 
 // offset (on an input TMA can address)
 bool lnf_fast_covers(int filter, int radius, int offset);
 // fast.cu: run the job through a specialised kernel if one covers it (*handled = the
-// number of kernels launched: 1, or 2 with the gather kernel beside, else 0);
+// number of kernels launched: 1, or 2 with the gate-first kernel beside, else 0);
 // `counter` is the launch's work counter (null: the context's own, for its stream)
+// `allow_gate`: the gate-first kernels may take a whole-volume job (plain calls on
+// the context's stream only: they use the context's bitmask scratch)
 lnf_status lnf_fast_dispatch(lnf_ctx *ctx, const FilterJob &job, const CUtensorMap *tmap, cudaStream_t stream,
-                             int *handled, u32 *counter = nullptr);
-// `paired`: the gather kernel is launched beside (the ring kernel returns at once
-// when that one does the work)
+                             int *handled, u32 *counter = nullptr, int allow_gate = 0);
+// `gated`: the gate-first kernel was launched for this job (the ring kernel
+// returns at once when that one does the work)
 lnf_status lnf_fast2_dispatch(lnf_ctx *ctx, const FilterJob &job, const CUtensorMap *tmap, cudaStream_t stream,
-                              int *handled, u32 *counter = nullptr, int paired = 0);
+                              int *handled, u32 *counter = nullptr, int gated = 0);
 // fast2_box.cu: the mean / entropy-filter job through its box kernel
 lnf_status lnf_fast2_box(lnf_ctx *ctx, const FilterJob &job, cudaStream_t stream, u32 *counter, int *handled,
-                         int paired);
-// sparse.cu: whether the gather kernel covers the job (whole volume, dense aligned
-// rows, radius 1..2, filters 0..4), and its launch
-bool lnf_gather_covers(const FilterJob &j);
-lnf_status lnf_gather_launch(lnf_ctx *ctx, const FilterJob &j, cudaStream_t st);
-// fused.cu: mean, sigma, entropy filter and Okada of one volume in one pass (outs /
-// hists in that order); *handled = 1 if launched
-lnf_status lnf_fused_launch(lnf_ctx *ctx, const FilterJob &j, void *const outs[4], u64 *const hists[4],
-                            cudaStream_t st, int *handled);
+                         int gated);
+// gate.cu: whether the gate-first kernel covers `filter` on the job's volume (a
+// whole volume, isotropic radius 1..4, the paper's filter at cluster offset 1),
+// and its launch for the filters whose outputs are given (outs / hists indexed
+// by filter id 0..4, null where not requested); *handled = 1 if launched
+bool lnf_gate_covers(const FilterJob &j, int filter);
+lnf_status lnf_gate_launch(lnf_ctx *ctx, const FilterJob &j, void *const outs[5], u64 *const hists[5],
+                           cudaStream_t st, int *handled);
 // render.cu: one ray per pixel (see lnf_render)
 cudaError_t lnf_launch_render(const void *vol, const int64_t dims[3], int64_t pitch, int dtype, int view,
                               int filter, int radius, int offset, const DevParams *prm, const u32 *lut,

@@ -50,25 +50,11 @@ struct DevParams {
     u64 n_pass;                 // voxels whose own value passes the gate (P0 >= T)
 };
 
-// Which of a filter's two whole-volume kernels works: the gather kernel
-// (sparse.cu), which evaluates only the voxels that pass the gate (every other
-// output is 0 by the gate's definition), while very few do; the plane-ring
-// kernel (fast.cu, fast2_*.cu), which evaluates every voxel, otherwise.  Both
-// are launched and both read this, so exactly one of them writes the output.
-// The switch points follow the two kernels' measured costs (a fixed streaming
-// cost plus one per passing voxel for the gather kernel): sigma 1/128 of the
-// voxels passing, every other filter 1/256.
-__host__ __device__ inline bool lnf_gather_mode(const DevParams &P, int filter)
-{
-    const u64 k = filter == 1 ? 128ull : 256ull;
-    return P.n_pass * k <= P.N;
-}
-
-// Whether the fused kernel (fused.cu) does the work of the four cube filters
-// (mean, sigma, entropy, Okada) of a multi-filter call: it evaluates only the
-// voxels that pass the gate, so while they are at most 1/32 of the volume; the
-// four ring kernels, launched beside, return at once then.
-__host__ __device__ inline bool lnf_fused_mode(const DevParams &P)
+// Whether the gate-first kernel (gate.cuh) does the work of the filters it is
+// launched for: it streams the volume once and evaluates only the voxels that
+// pass the gate (every other output is 0), so while they are at most 1/32 of
+// the volume; the plane-ring kernels, launched beside, return at once then.
+__host__ __device__ inline bool lnf_gate_mode(const DevParams &P)
 {
     return P.n_pass * 32ull <= P.N;
 }
@@ -92,6 +78,7 @@ struct FilterJob {
     const u32 *lut;             // entropy weights, levels entries
     u64 *out_hist;              // output histogram (levels entries) or null
     int tmap_idx;               // index of the job's TMA map in the pack, -1: plain loads
+    const void *orig;           // the caller's dense volume when `in` is a row-padded copy of it (or null)
     int tiles_x, tiles_y, zchunks;
     int item_begin;             // first flattened work item of this job
 };

@@ -14,10 +14,12 @@ HBM, ALU = 6783.5, 40.27
 
 def test_algorithmic_bytes_and_ops():
     n, es = bench.N_VOX, bench.ES
-    # a plain filter reads and writes the volume once; the fused pass writes four outputs
+    # a plain filter reads and writes the volume once; the gate-first pass of the
+    # five filters reads once and writes five outputs
     assert bench.algorithmic("filter:mean", 0, HBM, ALU) == ("hbm", n * es * 2)
     assert bench.algorithmic("filter:ours", 0, HBM, ALU) == ("hbm", n * es * 2)
-    assert bench.algorithmic("filter:fused4", 0, HBM, ALU) == ("hbm", n * es * 5)
+    assert bench.algorithmic("gate:ours", 0, HBM, ALU) == ("hbm", n * es * 2)
+    assert bench.algorithmic("filter:gate", 0, HBM, ALU) == ("hbm", n * es * 6)
     assert bench.algorithmic("stats", 0, HBM, ALU) == ("hbm", n * es)
     # sigma and Okada: ALU work of the voxels passing the gate, when it outlasts the bytes
     few = n // 100
@@ -33,18 +35,19 @@ def test_kind_of_kernel():
     k = bench.kind_of_kernel
     assert k("void <unnamed>::k_fast2<unsigned short, 2, 1, 0>(CUtensorMap_st, <unnamed>::Args2)") == "filter:sigma"
     assert k("void <unnamed>::k_fast2<unsigned char, 1, 0, 1>(CUtensorMap_st, <unnamed>::Args2)") == "filter:mean"
-    assert k("void <unnamed>::k_fused4<unsigned short, 2>(CUtensorMap_st, <unnamed>::FusedArgs)") == "filter:fused4"
+    assert k("void gatek::k_eval<unsigned short, 2, 3>(gatek::EvalArgs)") == "gate:eval"
+    assert k("void gatek::k_eval<unsigned char, 4, 1>(gatek::EvalArgs)") == "gate:eval_ours"
+    assert k("void gatek::k_scan<unsigned short>(gatek::ScanArgs)") == "gate:scan"
     assert k("void <unnamed>::k_ours_fast<unsigned short, 2, 0>(CUtensorMap_st, <unnamed>::FastArgs)") == "filter:ours"
-    assert k("void <unnamed>::k_gather<unsigned short, 2, 4>(<unnamed>::GatherArgs)") is None
     assert k("void at::native::vectorized_elementwise_kernel<4>(int)") is None
 
 
 def test_record_traffic_leaves_out_launches_that_returned(tmp_path, monkeypatch):
     rows = [
-        ("1", "void <unnamed>::k_fused4<unsigned short, 2>(X)", 150e6, 600e6),
+        ("1", "void gatek::k_eval<unsigned short, 2, 3>(X)", 150e6, 600e6),
         ("2", "void <unnamed>::k_fast2<unsigned short, 2, 1, 0>(X)", 0.0, 0.0),   # returned at once
         ("3", "void <unnamed>::k_ours_fast<unsigned short, 2, 0>(X)", 151e6, 105e6),
-        ("4", "void <unnamed>::k_fused4<unsigned short, 2>(X)", 152e6, 602e6),
+        ("4", "void gatek::k_eval<unsigned short, 2, 3>(X)", 152e6, 602e6),
     ]
     lines = ['"ID","Kernel Name","Metric Name","Metric Unit","Metric Value"']
     for i, name, rd, wr in rows:
@@ -56,6 +59,6 @@ def test_record_traffic_leaves_out_launches_that_returned(tmp_path, monkeypatch)
     monkeypatch.setattr(bench, "TRAFFIC_FILE", str(out))
     bench.record_traffic(str(csv), 2.0)
     got = {ln.split()[0]: int(ln.split()[1]) for ln in out.read_text().splitlines()}
-    assert set(got) == {"filter:fused4", "filter:ours"}
-    assert got["filter:fused4"] == round((150e6 + 600e6 + 152e6 + 602e6) / 2 * 2.0)
+    assert set(got) == {"gate:eval", "filter:ours"}
+    assert got["gate:eval"] == round((150e6 + 600e6 + 152e6 + 602e6) / 2 * 2.0)
     assert got["filter:ours"] == round((151e6 + 105e6) * 2.0)
