@@ -281,7 +281,6 @@ extern "C" void lnf_destroy(lnf_ctx *ctx)
     cudaFree(ctx->d_err);
     cudaFree(ctx->d_counter);
     cudaFree(ctx->pitched);
-    cudaFree(ctx->gate_mask_buf);
     cudaFree(ctx->f32_lv);
     cudaFree(ctx->d_range);
     for (cudaEvent_t e : ctx->filter_done)

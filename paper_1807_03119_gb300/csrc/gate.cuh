@@ -4,21 +4,22 @@
 //
 // Every one of the five outputs is 0 where the voxel's own value P0 is below
 // the noise threshold T, whatever its neighbourhood (§Our Method; the "0,
-// otherwise" of Eq. 6 and Eq. 7).  While few voxels pass (lnf_gate_mode), the
-// work splits into two kernels:
-//   k_scan -- a stream over the volume: 16-byte vector loads (8 voxels), one
-//     zero vector stored to every requested output, and one bit per voxel,
-//     P0 >= T, into a bitmask.  It moves each byte once and needs no shared
-//     memory or synchronisation, so it runs at the speed of a copy;
-//   k_eval -- persistent warps take 1024-voxel chunks of the bitmask, gather
-//     the set bits of a chunk into their own list (in-warp prefix sum) and
-//     evaluate full rounds of 32 listed voxels, one per lane, carrying the rest
-//     into the next chunk.  Each voxel's taps are read through L1 from the
-//     input (taps at compile-time plane / row / column offsets); a voxel within
-//     the filter's reach of a face takes a clamped path (clamp-to-edge
-//     sampling).  Nonzero outputs overwrite the zeros.
-// One launch pair serves any subset of the five filters: one read of the
-// volume, one write per output.
+// otherwise" of Eq. 6 and Eq. 7).  While few voxels pass (lnf_gate_mode), one
+// persistent kernel streams the volume and evaluates only the passing voxels.
+// Its warps claim 512-voxel chunks in order; per chunk a warp
+//   - loads the chunk (two 16-byte vectors of 8 voxels per lane), stores one
+//     zero vector to every requested output and keeps, per lane, the bits of
+//     its voxels with P0 >= T;
+//   - appends those voxels to its own list (in-warp prefix sum) and evaluates
+//     full rounds of 32 listed voxels, one per lane, carrying up to 31 into
+//     its next chunk (the warp zeroed them itself, so its nonzero outputs
+//     follow the zeros in program order).
+// A voxel's taps are read through L1 from the input, at compile-time plane /
+// row / column offsets; the chunks a warp's neighbours in z were given a few
+// hundred claims earlier, so those taps come from L2.  A voxel within the
+// filter's reach of a face takes a clamped path (clamp-to-edge sampling).
+// One launch serves any subset of the five filters: one read of the volume,
+// one write per output.
 //
 // Output histograms: nonzero outputs (all >= max(1, T, min)) go to a shared
 // window of 4096 16-bit bins per output (all 12-bit levels), the rest to
@@ -33,12 +34,11 @@
 
 namespace gatek {
 
-constexpr int kScanThreads = 256;
-constexpr int kScanUnroll = 4;                       // vectors a thread loads before using them
-constexpr int kEvalWarps = 8;
-constexpr int kEvalThreads = kEvalWarps * 32;
-constexpr int kChunkWords = 32;                      // bitmask words (32 voxels each) per chunk
-constexpr int kChunkVox = kChunkWords * 32;          // voxels per chunk
+constexpr int kWarpsC = 8;                           // warps per CTA
+constexpr int kThreadsC = kWarpsC * 32;
+constexpr int kVecL = 2;                             // 8-voxel vectors per lane and chunk
+constexpr int kChunkVec = 32 * kVecL;                // vectors per chunk
+constexpr int kChunkVox = kChunkVec * 8;             // voxels per chunk
 constexpr int kListCap = kChunkVox + 32;             // a warp's list: one chunk plus 31 carried over
 constexpr int kHistW = 4096;                         // shared histogram window per output (16-bit bins)
 constexpr int kLutW = 4096;                          // entropy weights kept in shared memory (16-bit data)
@@ -86,7 +86,7 @@ struct GGeo {
     static constexpr int NOUT = (OURS ? 1 : 0) + (CUBE ? 4 : 0);
     static constexpr int LUTN = CUBE ? (ES == 1 ? 256 : kLutW) : 0;
     static constexpr int HISTB = NOUT * kHistW * 2;   // two 16-bit bins per 32-bit word
-    static constexpr int LSTB = kEvalWarps * kListCap * 4;
+    static constexpr int LSTB = kWarpsC * kListCap * 4;
     static constexpr int SMEM = HISTB + LUTN * 4 + LSTB;
     // sigma: value and count packed in one word (count in the low bits) while exact
     static constexpr int SSH = ES == 1 ? 10 : 8;
@@ -103,26 +103,16 @@ __host__ __device__ constexpr int oslot(int f)
     return f == LNF_OURS ? ((SET & SET_CUBE) ? 4 : 0) : f;
 }
 
-struct ScanArgs {
+struct GateArgs {
     const void *in;
     void *out[5];                  // by filter id; null: not requested
-    u32 *mask;                     // one bit per voxel (P0 >= T), voxel i at bit i % 32 of word i / 32
-    u64 n;                         // voxels
-    u64 mask_bytes;                // bytes of the bitmask the evaluation reads (whole chunks)
-    const DevParams *prm;
-    u32 *counter;                  // the evaluation's chunk counter (reset here)
-};
-
-struct EvalArgs {
-    const void *in;
-    void *out[5];
     u64 *hist[5];                  // output histograms (null: not wanted)
-    const u32 *mask;
     int nx, ny, nz;
+    u64 n;                         // voxels
     u32 nchunks;
     const DevParams *prm;
     const u32 *lut;
-    u32 *counter;
+    u32 *counter;                  // chunk counter, 0 at launch
 };
 
 __device__ __forceinline__ int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
@@ -155,72 +145,6 @@ __device__ __forceinline__ u32 pass_bits(const uint4 &w, u32 T_)
     return bits;
 }
 
-// one bit per voxel of the bitmask, written a byte (8 voxels) at a time
-template <typename T>
-__global__ void __launch_bounds__(kScanThreads) k_scan(const ScanArgs a)
-{
-    const DevParams &P = *a.prm;
-    if (!lnf_gate_mode(P))
-        return;   // many voxels pass the gate: the plane-ring kernels do the work
-    const u32 T_ = P.T;
-    if (blockIdx.x == 0 && threadIdx.x == 0)
-        *a.counter = 0;   // the evaluation, next on the stream, claims chunks from 0
-    unsigned char *mb = reinterpret_cast<unsigned char *>(a.mask);
-    const u64 nvec = a.n / 8;
-    const u64 stride = (u64)gridDim.x * blockDim.x;
-    for (u64 v0 = blockIdx.x * (u64)blockDim.x + threadIdx.x; v0 < nvec; v0 += kScanUnroll * stride) {
-        uint4 w[kScanUnroll];
-#pragma unroll
-        for (int k = 0; k < kScanUnroll; ++k) {
-            const u64 v = v0 + k * stride;
-            w[k] = make_uint4(0u, 0u, 0u, 0u);
-            if (v < nvec) {
-                if (sizeof(T) == 2) {
-                    w[k] = __ldg(reinterpret_cast<const uint4 *>(a.in) + v);
-                } else {
-                    const uint2 h = __ldg(reinterpret_cast<const uint2 *>(a.in) + v);
-                    w[k] = make_uint4(h.x, h.y, 0u, 0u);
-                }
-            }
-        }
-#pragma unroll
-        for (int k = 0; k < kScanUnroll; ++k) {
-            const u64 v = v0 + k * stride;
-            if (v >= nvec)
-                continue;
-            const u32 bits = pass_bits<T>(w[k], T_);
-#pragma unroll
-            for (int f = 0; f < 5; ++f)
-                if (a.out[f]) {
-                    if (sizeof(T) == 2)
-                        reinterpret_cast<uint4 *>(a.out[f])[v] = make_uint4(0u, 0u, 0u, 0u);
-                    else
-                        reinterpret_cast<uint2 *>(a.out[f])[v] = make_uint2(0u, 0u);
-                }
-            mb[v] = (unsigned char)bits;
-        }
-    }
-    // the last voxels (n not a multiple of 8), and the bitmask's bytes beyond the
-    // volume up to the end of the last chunk
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        const u64 r = a.n - nvec * 8;
-        u32 bits = 0;
-        for (u64 q = 0; q < r; ++q) {
-            const u64 i = nvec * 8 + q;
-            const u32 val = sizeof(T) == 2 ? (u32) static_cast<const uint16_t *>(a.in)[i]
-                                           : (u32) static_cast<const uint8_t *>(a.in)[i];
-            bits |= (val >= T_ ? 1u : 0u) << q;
-            for (int f = 0; f < 5; ++f)
-                if (a.out[f])
-                    static_cast<T *>(a.out[f])[i] = (T)0;
-        }
-        if (r)
-            mb[nvec] = (unsigned char)bits;
-        for (u64 b = (a.n + 7) / 8; b < a.mask_bytes; ++b)
-            mb[b] = 0;
-    }
-}
-
 // ------------------------------------------------------------------ the evaluation
 
 // compile-time loop: f(std::integral_constant<int, i>) for i = 0 .. N-1
@@ -244,6 +168,9 @@ __device__ __forceinline__ u32 ldgv(const T *p)
 // One voxel's sums for the filters of the set.  CLAMP = false: every tap is at a
 // compile-time offset from the pointer of its plane and row; CLAMP = true: the
 // voxel lies within reach H of a face, and each tap is clamped into the volume.
+// The paper's filter's taps are unrolled (two instructions each); the cube's
+// are unrolled within a plane and looped over the planes, which keeps the code
+// of a voxel small enough for the instruction cache.
 template <typename T, int R, int SET, bool LUTALL, bool CLAMP>
 struct Sums {
     u32 U = 0, B = 0, S = 0, N = 0, O = 0, E = 0;
@@ -251,75 +178,95 @@ struct Sums {
     // so that the adds form four short dependency chains instead of one long one
     static constexpr int NA = R <= 2 ? 4 : 1;
 
+    __device__ __forceinline__ const T *row(const T *in, int x, int y, int z, int dy, int dz, int nx, int ny,
+                                            int nz, long long sxy) const
+    {
+        if constexpr (CLAMP)
+            return in + (clampi(z + dz, 0, nz - 1) * sxy + (long long)clampi(y + dy, 0, ny - 1) * nx);
+        else
+            return in + ((long long)(z + dz) * sxy + (long long)(y + dy) * nx + x);
+    }
+
+    template <int DX>
+    __device__ __forceinline__ u32 tap(const T *rp, int x, int nx) const
+    {
+        if constexpr (CLAMP)
+            return ldgv<T>(rp + clampi(x + DX, 0, nx - 1));
+        else
+            return ldgv<T>(rp + DX);
+    }
+
     __device__ __forceinline__ void run(const T *in, int x, int y, int z, int nx, int ny, int nz, u32 slo,
                                         u32 swd, u32 olo, u32 owd, const u32 *lut_sh, u32 lbase, const u32 *lut)
     {
         typedef GGeo<T, R, SET> G;
         const long long sxy = (long long)nx * ny;
-        u32 u[4] = {0u, 0u, 0u, 0u};
-        u32 b[4] = {0u, 0u, 0u, 0u}, sg[4] = {0u, 0u, 0u, 0u}, n[4] = {0u, 0u, 0u, 0u}, e[4] = {0u, 0u, 0u, 0u};
-        u32 o[2] = {0u, 0u};
-        // one row (plane dz, row dy) at a time: its pointer, then its taps
-        sfor<G::W * G::W>([&](auto ri) {
-            constexpr int rix = decltype(ri)::value;
-            constexpr int dy = rix % G::W - G::H, dz = rix / G::W - G::H;
-            constexpr bool row_cube = G::CUBE && dy >= -R && dy <= R && dz >= -R && dz <= R;
-            constexpr bool row_ours = G::OURS && ours_row(R, dy, dz);
-            if constexpr (row_cube || row_ours) {
-                const T *rp;
-                if constexpr (CLAMP)
-                    rp = in + (clampi(z + dz, 0, nz - 1) * sxy + (long long)clampi(y + dy, 0, ny - 1) * nx);
-                else
-                    rp = in + ((long long)(z + dz) * sxy + (long long)(y + dy) * nx + x);
-                sfor<G::W>([&](auto ci) {
-                    constexpr int dx = decltype(ci)::value - G::H;
-                    constexpr int t = rix * G::W + decltype(ci)::value;
-                    constexpr int w = G::OURS ? ours_weight(R, dx, dy, dz) : 0;
-                    constexpr bool cube = row_cube && dx >= -R && dx <= R;
-                    if constexpr (w != 0 || cube) {
-                        u32 v;
-                        if constexpr (CLAMP)
-                            v = ldgv<T>(rp + clampi(x + dx, 0, nx - 1));
-                        else
-                            v = ldgv<T>(rp + dx);
+        if constexpr (G::OURS) {
+            u32 u[4] = {0u, 0u, 0u, 0u};
+            sfor<G::W * G::W>([&](auto ri) {
+                constexpr int rix = decltype(ri)::value;
+                constexpr int dy = rix % G::W - G::H, dz = rix / G::W - G::H;
+                if constexpr (ours_row(R, dy, dz)) {
+                    const T *rp = row(in, x, y, z, dy, dz, nx, ny, nz, sxy);
+                    sfor<G::W>([&](auto ci) {
+                        constexpr int dx = decltype(ci)::value - G::H;
+                        constexpr int w = ours_weight(R, dx, dy, dz);
                         if constexpr (w != 0)
-                            u[t % NA] += (u32)w * v;
-                        if constexpr (cube) {
-                            constexpr int q = t % NA;
-                            constexpr bool cross = (dx == 0 && dy == 0) || (dx == 0 && dz == 0) || (dy == 0 && dz == 0);
-                            b[q] += v;
-                            if (v - slo <= swd) {
-                                if constexpr (G::SPACK) {
-                                    sg[q] += (v << G::SSH) | 1u;
-                                } else {
-                                    sg[q] += v;
-                                    n[q] += 1u;
-                                }
-                            }
-                            if constexpr (cross) {
-                                if (v - olo <= owd)
-                                    o[t % (NA > 1 ? 2 : 1)] += (v << 8) | 1u;
-                            }
-                            const u32 lo = v - lbase;
-                            if constexpr (LUTALL)
-                                e[q] += lut_sh[lo];
-                            else
-                                e[q] += lo < (u32)G::LUTN ? lut_sh[lo] : __ldg(lut + v);
+                            u[(rix * G::W + decltype(ci)::value) % NA] += (u32)w * tap<dx>(rp, x, nx);
+                    });
+                }
+            });
+            U = (u[0] + u[1]) + (u[2] + u[3]);
+        }
+        if constexpr (G::CUBE) {
+            u32 b[4] = {0u, 0u, 0u, 0u}, sg[4] = {0u, 0u, 0u, 0u}, n[4] = {0u, 0u, 0u, 0u}, e[4] = {0u, 0u, 0u, 0u};
+            u32 o[2] = {0u, 0u};
+#pragma unroll 1
+            for (int dz = -R; dz <= R; ++dz) {
+                const bool mid = dz == 0;   // the Okada cross has its x and y arms in this plane
+                sfor<G::M * G::M>([&](auto ti) {
+                    constexpr int t = decltype(ti)::value;
+                    constexpr int q = t % NA;
+                    constexpr int dx = t % G::M - R, dy = t / G::M - R;
+                    const T *rp = row(in, x, y, z, dy, dz, nx, ny, nz, sxy);
+                    const u32 v = tap<dx>(rp, x, nx);
+                    b[q] += v;
+                    if (v - slo <= swd) {
+                        if constexpr (G::SPACK) {
+                            sg[q] += (v << G::SSH) | 1u;
+                        } else {
+                            sg[q] += v;
+                            n[q] += 1u;
                         }
                     }
+                    constexpr bool zarm = dx == 0 && dy == 0;   // on the cross in every plane
+                    constexpr bool xyarm = dx == 0 || dy == 0;  // on the cross in the middle plane
+                    if constexpr (zarm) {
+                        if (v - olo <= owd)
+                            o[t & 1] += (v << 8) | 1u;
+                    } else if constexpr (xyarm) {
+                        if (mid && v - olo <= owd)
+                            o[t & 1] += (v << 8) | 1u;
+                    }
+                    const u32 lo = v - lbase;
+                    if constexpr (LUTALL)
+                        e[q] += lut_sh[lo];
+                    else
+                        e[q] += lo < (u32)G::LUTN ? lut_sh[lo] : __ldg(lut + v);
                 });
             }
-        });
-        U = (u[0] + u[1]) + (u[2] + u[3]);
-        B = (b[0] + b[1]) + (b[2] + b[3]);
-        S = (sg[0] + sg[1]) + (sg[2] + sg[3]);
-        N = (n[0] + n[1]) + (n[2] + n[3]);
-        E = (e[0] + e[1]) + (e[2] + e[3]);
-        O = o[0] + o[1];
+            B = (b[0] + b[1]) + (b[2] + b[3]);
+            S = (sg[0] + sg[1]) + (sg[2] + sg[3]);
+            N = (n[0] + n[1]) + (n[2] + n[3]);
+            E = (e[0] + e[1]) + (e[2] + e[3]);
+            O = o[0] + o[1];
+        }
     }
 };
 
-// the sums of a voxel near a face, out of line so that the common path stays compact
+// The sums of a voxel near a face (taps clamped), or of any voxel whose levels'
+// entropy weights do not all fit in shared memory: out of line, so that the
+// common path stays compact.
 template <typename T, int R, int SET>
 __device__ __noinline__ void sums_clamped(Sums<T, R, SET, false, true> &sm, const T *in, int x, int y, int z,
                                           int nx, int ny, int nz, u32 slo, u32 swd, u32 olo, u32 owd,
@@ -329,12 +276,12 @@ __device__ __noinline__ void sums_clamped(Sums<T, R, SET, false, true> &sm, cons
 }
 
 template <typename T, int R, int SET>
-__global__ void __launch_bounds__(kEvalThreads, 2) k_eval(const EvalArgs a)
+__global__ void __launch_bounds__(kThreadsC, 2) k_gate(const GateArgs a)
 {
     typedef GGeo<T, R, SET> G;
     const DevParams &P = *a.prm;
     if (!lnf_gate_mode(P))
-        return;
+        return;   // many voxels pass the gate: the plane-ring kernels do the work
     extern __shared__ __align__(16) unsigned char smem[];
     u32 *hsh = reinterpret_cast<u32 *>(smem);                                  // NOUT windows of 16-bit bins
     u32 *lut_sh = reinterpret_cast<u32 *>(smem + G::HISTB);                    // LUTN entropy weights
@@ -353,9 +300,9 @@ __global__ void __launch_bounds__(kEvalThreads, 2) k_eval(const EvalArgs a)
         te = (long long)(((unsigned __int128)(G::CT ? G::CT : 1) * P.hw_sum) / P.N);
     const u32 lbase = G::ES == 1 ? 0u : P.minv;
     const bool lutall = G::LUTN > 0 && (P.maxv - lbase) + 1u <= (u32)G::LUTN;
-    for (int i = tid; i < G::NOUT * kHistW / 2; i += kEvalThreads)
+    for (int i = tid; i < G::NOUT * kHistW / 2; i += kThreadsC)
         hsh[i] = 0;
-    for (int i = tid; i < G::LUTN; i += kEvalThreads)
+    for (int i = tid; i < G::LUTN; i += kThreadsC)
         lut_sh[i] = (lbase + i < (G::ES == 1 ? 256u : 65536u)) ? a.lut[lbase + i] : 0u;
     __syncthreads();
 
@@ -365,6 +312,7 @@ __global__ void __launch_bounds__(kEvalThreads, 2) k_eval(const EvalArgs a)
     constexpr u32 KO = 27u * G::M, KM = (u32)(G::M * G::M * G::M);
     const u32 KOT = KO * T_, KMT = KM * T_;
     const u32 nxny = (u32)a.nx * (u32)a.ny;
+    const u64 nvec = a.n / 8;
     u32 nzc[5] = {0u, 0u, 0u, 0u, 0u};
     u32 *L = lst + warp * kListCap;
 
@@ -393,16 +341,10 @@ __global__ void __launch_bounds__(kEvalThreads, 2) k_eval(const EvalArgs a)
                 fv[LNF_ENTROPY] = (long long)sm.E > te ? P0 : 0u;
             }
         };
-        if (inner) {
-            if (lutall || !G::CUBE) {
-                Sums<T, R, SET, true, false> sm;
-                sm.run(in, x, y, z, a.nx, a.ny, a.nz, slo, swd, olo, owd, lut_sh, lbase, a.lut);
-                finish(sm);
-            } else {
-                Sums<T, R, SET, false, false> sm;
-                sm.run(in, x, y, z, a.nx, a.ny, a.nz, slo, swd, olo, owd, lut_sh, lbase, a.lut);
-                finish(sm);
-            }
+        if (inner && (lutall || !G::CUBE)) {
+            Sums<T, R, SET, true, false> sm;
+            sm.run(in, x, y, z, a.nx, a.ny, a.nz, slo, swd, olo, owd, lut_sh, lbase, a.lut);
+            finish(sm);
         } else {
             Sums<T, R, SET, false, true> sm;
             sums_clamped<T, R, SET>(sm, in, x, y, z, a.nx, a.ny, a.nz, slo, swd, olo, owd, lut_sh, lbase, a.lut);
@@ -436,7 +378,7 @@ __global__ void __launch_bounds__(kEvalThreads, 2) k_eval(const EvalArgs a)
         }
     };
 
-    // ---- chunks of the bitmask: the set bits into this warp's list, then full rounds
+    // ---- chunks: stream, list, evaluate full rounds
     u32 nlist = 0;   // listed voxels not yet evaluated (the same in every lane)
     for (;;) {
         u32 c = 0;
@@ -445,22 +387,63 @@ __global__ void __launch_bounds__(kEvalThreads, 2) k_eval(const EvalArgs a)
         c = __shfl_sync(0xFFFFFFFFu, c, 0);
         const bool done = c >= a.nchunks;
         if (!done) {
-            const u32 w = a.mask[(u64)c * kChunkWords + lane];
-            const u32 k = (u32)__popc(w);
-            u32 incl = k;
+            // lane's vectors: chunk vector lane + 32 k (consecutive lanes, consecutive 16 bytes)
+            uint4 w[kVecL];
+#pragma unroll
+            for (int k = 0; k < kVecL; ++k) {
+                const u64 v = (u64)c * kChunkVec + lane + 32 * k;
+                w[k] = make_uint4(0u, 0u, 0u, 0u);
+                if (v < nvec) {
+                    if (sizeof(T) == 2) {
+                        w[k] = __ldg(reinterpret_cast<const uint4 *>(a.in) + v);
+                    } else {
+                        const uint2 h = __ldg(reinterpret_cast<const uint2 *>(a.in) + v);
+                        w[k] = make_uint4(h.x, h.y, 0u, 0u);
+                    }
+                }
+            }
+            u32 word = 0;   // bit 8k + q: voxel 8 (chunk vector lane + 32 k) + q passes
+#pragma unroll
+            for (int k = 0; k < kVecL; ++k) {
+                const u64 v = (u64)c * kChunkVec + lane + 32 * k;
+                if (v < nvec) {
+                    word |= pass_bits<T>(w[k], T_) << (8 * k);
+#pragma unroll
+                    for (int f = 0; f < 5; ++f)
+                        if (((f == LNF_OURS) ? G::OURS : G::CUBE) && a.out[f]) {
+                            if (sizeof(T) == 2)
+                                reinterpret_cast<uint4 *>(a.out[f])[v] = make_uint4(0u, 0u, 0u, 0u);
+                            else
+                                reinterpret_cast<uint2 *>(a.out[f])[v] = make_uint2(0u, 0u);
+                        }
+                } else if (v == nvec) {
+                    // the last voxels (n not a multiple of 8), one by one
+                    u32 bits = 0;
+                    for (u32 q = 0; q < (u32)(a.n - nvec * 8); ++q) {
+                        const u64 vi = nvec * 8 + q;
+                        bits |= (ldgv<T>(in + vi) >= T_ ? 1u : 0u) << q;
+                        for (int f = 0; f < 5; ++f)
+                            if (((f == LNF_OURS) ? G::OURS : G::CUBE) && a.out[f])
+                                static_cast<T *>(a.out[f])[vi] = (T)0;
+                    }
+                    word |= bits << (8 * k);
+                }
+            }
+            // the warp's list: an exclusive prefix sum of the lanes' counts
+            const u32 cnt = (u32)__popc(word);
+            u32 incl = cnt;
 #pragma unroll
             for (int d = 1; d < 32; d <<= 1) {
                 const u32 t = __shfl_up_sync(0xFFFFFFFFu, incl, d);
                 if (lane >= d)
                     incl += t;
             }
-            u32 pos = nlist + incl - k;
-            const u32 base = c * (u32)kChunkVox + (u32)lane * 32u;
-            u32 m = w;
-            while (m) {
-                const int bit = __ffs(m) - 1;
-                m &= m - 1u;
-                L[pos++] = base + (u32)bit;
+            u32 pos = nlist + incl - cnt;
+            while (word) {
+                const int bit = __ffs(word) - 1;
+                word &= word - 1u;
+                const u32 v = c * (u32)kChunkVec + (u32)lane + 32u * (u32)(bit >> 3);
+                L[pos++] = v * 8u + (u32)(bit & 7);
             }
             nlist += __shfl_sync(0xFFFFFFFFu, incl, 31);
             __syncwarp();
@@ -489,7 +472,7 @@ __global__ void __launch_bounds__(kEvalThreads, 2) k_eval(const EvalArgs a)
         if (!(((f == LNF_OURS) ? G::OURS : G::CUBE) && a.out[f] && a.hist[f]))
             continue;
         const u32 *h = hsh + oslot<SET>(f) * (kHistW / 2);
-        for (int i = tid; i < kHistW / 2; i += kEvalThreads) {
+        for (int i = tid; i < kHistW / 2; i += kThreadsC) {
             const u32 w = h[i];
             if (w & 0xFFFFu)
                 atomicAdd(&a.hist[f][hbase + 2 * i], (u64)(w & 0xFFFFu));
@@ -508,32 +491,33 @@ __global__ void __launch_bounds__(kEvalThreads, 2) k_eval(const EvalArgs a)
 // ------------------------------------------------------------------ launch
 
 template <typename T, int R, int SET>
-lnf_status eval_launch_t(lnf_ctx *ctx, const EvalArgs &a, cudaStream_t st)
+lnf_status gate_launch_t(lnf_ctx *ctx, const GateArgs &a, cudaStream_t st)
 {
     typedef GGeo<T, R, SET> G;
-    if (cudaFuncSetAttribute(k_eval<T, R, SET>, cudaFuncAttributeMaxDynamicSharedMemorySize, G::SMEM) !=
+    if (cudaFuncSetAttribute(k_gate<T, R, SET>, cudaFuncAttributeMaxDynamicSharedMemorySize, G::SMEM) !=
         cudaSuccess)
-        return lnf_fail(ctx, LNF_ECUDA, "gate evaluation kernel: shared memory attribute (%d bytes)", G::SMEM);
+        return lnf_fail(ctx, LNF_ECUDA, "gate kernel: shared memory attribute (%d bytes)", G::SMEM);
     int occ = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_eval<T, R, SET>, kEvalThreads, G::SMEM);
-    const int grid = std::max(1, std::min((int)a.nchunks, ctx->num_sms * std::max(1, occ)));
-    k_eval<T, R, SET><<<grid, kEvalThreads, G::SMEM, st>>>(a);
-    return cudaGetLastError() == cudaSuccess ? LNF_OK
-                                             : lnf_fail(ctx, LNF_ECUDA, "gate evaluation kernel launch failed");
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_gate<T, R, SET>, kThreadsC, G::SMEM);
+    const int grid = std::max(1, std::min((int)((a.nchunks + kWarpsC - 1) / kWarpsC), ctx->num_sms * std::max(1, occ)));
+    if (cudaMemsetAsync(a.counter, 0, sizeof(u32), st) != cudaSuccess)
+        return lnf_fail(ctx, LNF_ECUDA, "gate kernel: counter reset");
+    k_gate<T, R, SET><<<grid, kThreadsC, G::SMEM, st>>>(a);
+    return cudaGetLastError() == cudaSuccess ? LNF_OK : lnf_fail(ctx, LNF_ECUDA, "gate kernel launch failed");
 }
 
 template <typename T, int SET>
-lnf_status eval_by_radius(lnf_ctx *ctx, int radius, const EvalArgs &a, cudaStream_t st)
+lnf_status gate_by_radius(lnf_ctx *ctx, int radius, const GateArgs &a, cudaStream_t st)
 {
     switch (radius) {
-    case 1: return eval_launch_t<T, 1, SET>(ctx, a, st);
-    case 2: return eval_launch_t<T, 2, SET>(ctx, a, st);
-    case 3: return eval_launch_t<T, 3, SET>(ctx, a, st);
-    default: return eval_launch_t<T, 4, SET>(ctx, a, st);
+    case 1: return gate_launch_t<T, 1, SET>(ctx, a, st);
+    case 2: return gate_launch_t<T, 2, SET>(ctx, a, st);
+    case 3: return gate_launch_t<T, 3, SET>(ctx, a, st);
+    default: return gate_launch_t<T, 4, SET>(ctx, a, st);
     }
 }
 
-// The scan and the evaluation of one job (outs / hists by filter id).
+// The gate kernel for one job (outs / hists by filter id).
 template <typename T>
 lnf_status gate_dispatch_t(lnf_ctx *ctx, const FilterJob &j, void *const outs[5], u64 *const hists[5],
                            cudaStream_t st, int *handled)
@@ -544,59 +528,30 @@ lnf_status gate_dispatch_t(lnf_ctx *ctx, const FilterJob &j, void *const outs[5]
     for (int f = 0; f < 5; ++f)
         if (outs[f] && reinterpret_cast<uintptr_t>(outs[f]) % 16 != 0)
             return LNF_OK;
-    const u64 nchunks = (n + kChunkVox - 1) / kChunkVox;
-    const size_t mbytes = nchunks * kChunkVox / 8;
-    if (ctx->gate_mask_cap < mbytes) {
-        cudaFree(ctx->gate_mask_buf);   // waits for the work that still reads it
-        ctx->gate_mask_buf = nullptr;
-        ctx->gate_mask_cap = 0;
-        if (cudaMalloc(&ctx->gate_mask_buf, mbytes) != cudaSuccess) {
-            ctx->gate_mask_buf = nullptr;
-            cudaGetLastError();
-            return LNF_OK;   // no room for the bitmask: the ring kernels do the work
-        }
-        ctx->gate_mask_cap = mbytes;
-    }
-    u32 *mask = static_cast<u32 *>(ctx->gate_mask_buf);
-    u32 *counter = ctx->d_counter + 14;
-    ScanArgs sa;
-    std::memset(&sa, 0, sizeof sa);
-    sa.in = j.in;
-    for (int f = 0; f < 5; ++f)
-        sa.out[f] = outs[f];
-    sa.mask = mask;
-    sa.n = n;
-    sa.mask_bytes = mbytes;
-    sa.prm = j.prm;
-    sa.counter = counter;
-    const int sgrid = std::max(1, ctx->num_sms * 8);
-    k_scan<T><<<sgrid, kScanThreads, 0, st>>>(sa);
-    if (cudaGetLastError() != cudaSuccess)
-        return lnf_fail(ctx, LNF_ECUDA, "gate scan kernel launch failed");
-    EvalArgs ea;
-    std::memset(&ea, 0, sizeof ea);
-    ea.in = j.in;
+    GateArgs a;
+    std::memset(&a, 0, sizeof a);
+    a.in = j.in;
     for (int f = 0; f < 5; ++f) {
-        ea.out[f] = outs[f];
-        ea.hist[f] = outs[f] ? hists[f] : nullptr;
+        a.out[f] = outs[f];
+        a.hist[f] = outs[f] ? hists[f] : nullptr;
     }
-    ea.mask = mask;
-    ea.nx = j.nx;
-    ea.ny = j.ny;
-    ea.nz = j.nz;
-    ea.nchunks = (u32)nchunks;
-    ea.prm = j.prm;
-    ea.lut = j.lut;
-    ea.counter = counter;
+    a.nx = j.nx;
+    a.ny = j.ny;
+    a.nz = j.nz;
+    a.n = n;
+    a.nchunks = (u32)((n + kChunkVox - 1) / kChunkVox);
+    a.prm = j.prm;
+    a.lut = j.lut;
+    a.counter = ctx->d_counter + 14;
     const bool ours = outs[LNF_OURS] != nullptr;
     const bool cube = outs[0] || outs[1] || outs[2] || outs[3];
     lnf_status s;
     if (ours && cube)
-        s = eval_by_radius<T, SET_ALL>(ctx, j.radius, ea, st);
+        s = gate_by_radius<T, SET_ALL>(ctx, j.radius, a, st);
     else if (ours)
-        s = eval_by_radius<T, SET_OURS>(ctx, j.radius, ea, st);
+        s = gate_by_radius<T, SET_OURS>(ctx, j.radius, a, st);
     else
-        s = eval_by_radius<T, SET_CUBE>(ctx, j.radius, ea, st);
+        s = gate_by_radius<T, SET_CUBE>(ctx, j.radius, a, st);
     if (s == LNF_OK)
         *handled = 1;
     return s;

@@ -76,8 +76,6 @@ struct lnf_ctx {
     bool no_fast = false;       // testing: force the generic kernel
     bool no_gate = false;       // testing: never launch the gate-first kernel (the ring kernels work)
     int gate_mask = 0;          // filter ids a launched gate-first kernel covers (during a multi-filter call)
-    void *gate_mask_buf = nullptr;   // gate-first path: the bitmask of passing voxels (grow-only)
-    size_t gate_mask_cap = 0;
     VolScratch vs;              // scratch of plain calls
     std::vector<VolScratch> pool;   // scratch of batched / resident volumes
     u64 *out_hist = nullptr;    // LNF_MAX_PACK output histograms of 65536 bins
@@ -173,8 +171,8 @@ bool lnf_fast_covers(int filter, int radius, int offset);
 // fast.cu: run the job through a specialised kernel if one covers it (*handled = the
 // number of kernels launched: 1, or 2 with the gate-first kernel beside, else 0);
 // `counter` is the launch's work counter (null: the context's own, for its stream)
-// `allow_gate`: the gate-first kernels may take a whole-volume job (plain calls on
-// the context's stream only: they use the context's bitmask scratch)
+// `allow_gate`: the gate-first kernel may take a whole-volume job (plain calls on
+// the context's stream only: it uses the context's chunk counter)
 lnf_status lnf_fast_dispatch(lnf_ctx *ctx, const FilterJob &job, const CUtensorMap *tmap, cudaStream_t stream,
                              int *handled, u32 *counter = nullptr, int allow_gate = 0);
 // `gated`: the gate-first kernel was launched for this job (the ring kernel
