@@ -107,8 +107,7 @@ KIND_SOURCES = {
     "filter:okada": ["fast2.cuh", "fast2_tap.cu"],
     "filter:gate": ["gate.cuh", "gate_u16.cu"],
     "gate:ours": ["gate.cuh", "gate_u16.cu"],
-    "gate:scan": ["gate.cuh", "gate_u16.cu"],
-    "gate:eval": ["gate.cuh", "gate_u16.cu"],
+    "gate:cube": ["gate.cuh", "gate_u16.cu"],
 }
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "dram_traffic_512cubed_u16_r2.txt")
 
@@ -137,18 +136,14 @@ def recorded_traffic(kind):
 
 
 def kind_of_kernel(name):
-    """Bench kind of an ncu kernel name (None for launches that are not ours, and
-    for the gather kernels, whose launch beside a ring kernel reads nothing when the
-    ring kernel does the work)."""
+    """Bench kind of an ncu kernel name (None for launches that are not ours)."""
     import re
     m = re.search(r"k_fast2<[^,]+, \d+, (\d+)", name)
     if m:
         return "filter:" + {0: "mean", 1: "sigma", 2: "entropy", 3: "okada"}[int(m.group(1))]
-    m = re.search(r"k_eval<[^,]+, \d+, (\d+)>", name)
+    m = re.search(r"k_gate<[^,]+, \d+, (\d+)>", name)
     if m:   # the filter set: 3 all five (a multi-filter call), 1 the paper's filter alone, 2 comparison filters
-        return {3: "gate:eval", 1: "gate:eval_ours", 2: "gate:eval_cube"}[int(m.group(1))]
-    if "gatek::k_scan" in name:
-        return "gate:scan"
+        return {3: "filter:gate", 1: "gate:ours", 2: "gate:cube"}[int(m.group(1))]
     if "k_ours_fast" in name:
         return "filter:ours"
     for k, kind in (("k_stats_batched", None), ("k_stats<", "stats"), ("k_params", "params"),

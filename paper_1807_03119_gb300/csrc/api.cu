@@ -419,7 +419,7 @@ lnf_status lnf_analyze(lnf_ctx *ctx, const void *in, const int64_t dims[3], int 
     CK(lnf_launch_stats_init(vs.hist, levels, vs.st, n, stream));
     lnf_prof_end(ctx, rec, "stats_init", stream, 1);
     rec = lnf_prof_begin(ctx, stream);
-    CK(lnf_launch_stats(in, n, dtype, vs.hist, vs.st, ctx->num_sms, stream));
+    CK(lnf_launch_stats(in, n, dtype, vs.hist, ctx->num_sms, stream));
     lnf_prof_end(ctx, rec, "stats", stream, 1);
     rec = lnf_prof_begin(ctx, stream);
     CK(lnf_launch_params(vs.hist, vs.st, lnf_param_cfg(ctx->cfg), vs.prm, vs.lut, vs.pscr, dtype, stream));
@@ -966,7 +966,7 @@ extern "C" lnf_status lnf_entropy(lnf_ctx *ctx, const void *vol, const int64_t d
     const u32 levels = dtype == LNF_U8 ? LNF_LEVELS_U8 : LNF_LEVELS_U16;
     const u64 n = nvox(dims);
     CK(lnf_launch_stats_init(ctx->vs.hist, levels, ctx->vs.st, n, st));
-    CK(lnf_launch_stats(vol, n, dtype, ctx->vs.hist, ctx->vs.st, ctx->num_sms, st));
+    CK(lnf_launch_stats(vol, n, dtype, ctx->vs.hist, ctx->num_sms, st));
     CK(lnf_launch_entropy(ctx->vs.hist, levels, n, ctx->d_H, st));
     CK(cudaMemcpyAsync(H, ctx->d_H, sizeof(double), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));

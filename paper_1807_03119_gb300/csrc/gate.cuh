@@ -6,8 +6,11 @@
 // the noise threshold T, whatever its neighbourhood (§Our Method; the "0,
 // otherwise" of Eq. 6 and Eq. 7).  While few voxels pass (lnf_gate_mode), one
 // persistent kernel streams the volume and evaluates only the passing voxels.
-// Its warps claim 512-voxel chunks in order; per chunk a warp
-//   - loads the chunk (two 16-byte vectors of 8 voxels per lane), stores one
+// Its warps claim chunks of 256 VL voxels in order (VL 16-byte vectors of 8
+// voxels per lane); per chunk a warp
+//   - loads the chunk (for the paper's filter alone: the next chunk's loads are
+//     issued before this one is used, and the claim of the one after it is
+//     read only at the end of the step, so that neither waits), stores one
 //     zero vector to every requested output and keeps, per lane, the bits of
 //     its voxels with P0 >= T;
 //   - appends those voxels to its own list (in-warp prefix sum) and evaluates
@@ -32,14 +35,29 @@
 #include <cstring>
 #include <utility>
 
+#ifndef LNF_GATE_MINB_CUBE
+#define LNF_GATE_MINB_CUBE 2
+#endif
+#ifndef LNF_GATE_MINB_OURS
+#define LNF_GATE_MINB_OURS 2
+#endif
+#ifndef LNF_GATE_VL_CUBE
+#define LNF_GATE_VL_CUBE 2
+#endif
+#ifndef LNF_GATE_VL_OURS
+#define LNF_GATE_VL_OURS 6
+#endif
+#ifndef LNF_GATE_PF_CUBE
+#define LNF_GATE_PF_CUBE 0
+#endif
+#ifndef LNF_GATE_PF_OURS
+#define LNF_GATE_PF_OURS 1
+#endif
+
 namespace gatek {
 
 constexpr int kWarpsC = 8;                           // warps per CTA
 constexpr int kThreadsC = kWarpsC * 32;
-constexpr int kVecL = 2;                             // 8-voxel vectors per lane and chunk
-constexpr int kChunkVec = 32 * kVecL;                // vectors per chunk
-constexpr int kChunkVox = kChunkVec * 8;             // voxels per chunk
-constexpr int kListCap = kChunkVox + 32;             // a warp's list: one chunk plus 31 carried over
 constexpr int kHistW = 4096;                         // shared histogram window per output (16-bit bins)
 constexpr int kLutW = 4096;                          // entropy weights kept in shared memory (16-bit data)
 
@@ -86,8 +104,18 @@ struct GGeo {
     static constexpr int NOUT = (OURS ? 1 : 0) + (CUBE ? 4 : 0);
     static constexpr int LUTN = CUBE ? (ES == 1 ? 256 : kLutW) : 0;
     static constexpr int HISTB = NOUT * kHistW * 2;   // two 16-bit bins per 32-bit word
-    static constexpr int LSTB = kWarpsC * kListCap * 4;
+    // chunks: VL 16-byte vectors of 8 voxels per lane; PF: the next chunk's loads
+    // are issued before the current chunk is used
+    static constexpr int VL = CUBE ? LNF_GATE_VL_CUBE : LNF_GATE_VL_OURS;
+    static constexpr bool PF = (CUBE ? LNF_GATE_PF_CUBE : LNF_GATE_PF_OURS) != 0;
+    static constexpr int CVEC = 32 * VL;            // vectors per chunk
+    static constexpr int CVOX = CVEC * 8;           // voxels per chunk
+    static constexpr int LCAP = CVOX + 32;          // a warp's list: one chunk plus 31 carried over
+    static constexpr int LSTB = kWarpsC * LCAP * 4;
     static constexpr int SMEM = HISTB + LUTN * 4 + LSTB;
+    // CTAs per SM the register budget aims for: the kernel waits on loads, so
+    // more warps hide more of it where the evaluation needs fewer registers
+    static constexpr int MINB = CUBE ? LNF_GATE_MINB_CUBE : LNF_GATE_MINB_OURS;
     // sigma: value and count packed in one word (count in the low bits) while exact
     static constexpr int SSH = ES == 1 ? 10 : 8;
     static constexpr bool SPACK = CT < (1 << SSH) &&
@@ -276,7 +304,7 @@ __device__ __noinline__ void sums_clamped(Sums<T, R, SET, false, true> &sm, cons
 }
 
 template <typename T, int R, int SET>
-__global__ void __launch_bounds__(kThreadsC, 2) k_gate(const GateArgs a)
+__global__ void __launch_bounds__(kThreadsC, GGeo<T, R, SET>::MINB) k_gate(const GateArgs a)
 {
     typedef GGeo<T, R, SET> G;
     const DevParams &P = *a.prm;
@@ -314,7 +342,7 @@ __global__ void __launch_bounds__(kThreadsC, 2) k_gate(const GateArgs a)
     const u32 nxny = (u32)a.nx * (u32)a.ny;
     const u64 nvec = a.n / 8;
     u32 nzc[5] = {0u, 0u, 0u, 0u, 0u};
-    u32 *L = lst + warp * kListCap;
+    u32 *L = lst + warp * G::LCAP;
 
     // one listed voxel (linear index i), evaluated by this lane
     auto eval_voxel = [&](u32 i) {
@@ -379,35 +407,52 @@ __global__ void __launch_bounds__(kThreadsC, 2) k_gate(const GateArgs a)
     };
 
     // ---- chunks: stream, list, evaluate full rounds
-    u32 nlist = 0;   // listed voxels not yet evaluated (the same in every lane)
-    for (;;) {
+    auto claim = [&]() -> u32 {
         u32 c = 0;
         if (lane == 0)
             c = atomicAdd(a.counter, 1u);
-        c = __shfl_sync(0xFFFFFFFFu, c, 0);
-        const bool done = c >= a.nchunks;
-        if (!done) {
-            // lane's vectors: chunk vector lane + 32 k (consecutive lanes, consecutive 16 bytes)
-            uint4 w[kVecL];
+        return __shfl_sync(0xFFFFFFFFu, c, 0);
+    };
+    // the lane's vectors of chunk c: chunk vector lane + 32 k (consecutive lanes,
+    // consecutive 16 bytes)
+    auto load_chunk = [&](u32 c, uint4 *w) {
 #pragma unroll
-            for (int k = 0; k < kVecL; ++k) {
-                const u64 v = (u64)c * kChunkVec + lane + 32 * k;
-                w[k] = make_uint4(0u, 0u, 0u, 0u);
-                if (v < nvec) {
-                    if (sizeof(T) == 2) {
-                        w[k] = __ldg(reinterpret_cast<const uint4 *>(a.in) + v);
-                    } else {
-                        const uint2 h = __ldg(reinterpret_cast<const uint2 *>(a.in) + v);
-                        w[k] = make_uint4(h.x, h.y, 0u, 0u);
-                    }
+        for (int k = 0; k < G::VL; ++k) {
+            const u64 v = (u64)c * G::CVEC + lane + 32 * k;
+            w[k] = make_uint4(0u, 0u, 0u, 0u);
+            if (c < a.nchunks && v < nvec) {
+                if (sizeof(T) == 2) {
+                    w[k] = __ldg(reinterpret_cast<const uint4 *>(a.in) + v);
+                } else {
+                    const uint2 h = __ldg(reinterpret_cast<const uint2 *>(a.in) + v);
+                    w[k] = make_uint4(h.x, h.y, 0u, 0u);
                 }
             }
-            u32 word = 0;   // bit 8k + q: voxel 8 (chunk vector lane + 32 k) + q passes
+        }
+    };
+    u32 nlist = 0;   // listed voxels not yet evaluated (the same in every lane)
+    uint4 w[G::VL], wn[G::VL];
+    u32 c = claim();
+    load_chunk(c, w);
+    // with PF: the next chunk (its loads in flight while this one is used) and the
+    // claim of the one after it, whose result is read only at the end of the step
+    u32 cn = G::PF ? claim() : 0u;
+    for (;;) {
+        const bool done = c >= a.nchunks;
+        u32 cnn = 0;
+        if (!done) {
+            if constexpr (G::PF) {
+                load_chunk(cn, wn);
+                if (lane == 0)
+                    cnn = atomicAdd(a.counter, 1u);
+            }
+            static_assert(G::VL >= 1 && G::VL <= 8, "one pass bit per voxel of the lane's vectors");
+            u64 word = 0;          // bit 8k + q: voxel 8 (chunk vector lane + 32 k) + q passes
 #pragma unroll
-            for (int k = 0; k < kVecL; ++k) {
-                const u64 v = (u64)c * kChunkVec + lane + 32 * k;
+            for (int k = 0; k < G::VL; ++k) {
+                const u64 v = (u64)c * G::CVEC + lane + 32 * k;
                 if (v < nvec) {
-                    word |= pass_bits<T>(w[k], T_) << (8 * k);
+                    word |= (u64)pass_bits<T>(w[k], T_) << (8 * k);
 #pragma unroll
                     for (int f = 0; f < 5; ++f)
                         if (((f == LNF_OURS) ? G::OURS : G::CUBE) && a.out[f]) {
@@ -426,11 +471,11 @@ __global__ void __launch_bounds__(kThreadsC, 2) k_gate(const GateArgs a)
                             if (((f == LNF_OURS) ? G::OURS : G::CUBE) && a.out[f])
                                 static_cast<T *>(a.out[f])[vi] = (T)0;
                     }
-                    word |= bits << (8 * k);
+                    word |= (u64)bits << (8 * k);
                 }
             }
             // the warp's list: an exclusive prefix sum of the lanes' counts
-            const u32 cnt = (u32)__popc(word);
+            const u32 cnt = (u32)__popcll(word);
             u32 incl = cnt;
 #pragma unroll
             for (int d = 1; d < 32; d <<= 1) {
@@ -440,9 +485,9 @@ __global__ void __launch_bounds__(kThreadsC, 2) k_gate(const GateArgs a)
             }
             u32 pos = nlist + incl - cnt;
             while (word) {
-                const int bit = __ffs(word) - 1;
-                word &= word - 1u;
-                const u32 v = c * (u32)kChunkVec + (u32)lane + 32u * (u32)(bit >> 3);
+                const int bit = __ffsll((long long)word) - 1;
+                word &= word - 1ull;
+                const u32 v = c * (u32)G::CVEC + (u32)lane + 32u * (u32)(bit >> 3);
                 L[pos++] = v * 8u + (u32)(bit & 7);
             }
             nlist += __shfl_sync(0xFFFFFFFFu, incl, 31);
@@ -463,6 +508,16 @@ __global__ void __launch_bounds__(kThreadsC, 2) k_gate(const GateArgs a)
         nlist = rest;
         if (done)
             break;
+        if constexpr (G::PF) {
+            c = cn;
+            cn = __shfl_sync(0xFFFFFFFFu, cnn, 0);
+#pragma unroll
+            for (int k = 0; k < G::VL; ++k)
+                w[k] = wn[k];
+        } else {
+            c = claim();
+            load_chunk(c, w);
+        }
     }
 
     // ---- histograms: the shared windows, and the zeros as N minus the nonzero outputs
@@ -491,9 +546,11 @@ __global__ void __launch_bounds__(kThreadsC, 2) k_gate(const GateArgs a)
 // ------------------------------------------------------------------ launch
 
 template <typename T, int R, int SET>
-lnf_status gate_launch_t(lnf_ctx *ctx, const GateArgs &a, cudaStream_t st)
+lnf_status gate_launch_t(lnf_ctx *ctx, const GateArgs &a0, cudaStream_t st)
 {
     typedef GGeo<T, R, SET> G;
+    GateArgs a = a0;
+    a.nchunks = (u32)((a.n + G::CVOX - 1) / G::CVOX);
     if (cudaFuncSetAttribute(k_gate<T, R, SET>, cudaFuncAttributeMaxDynamicSharedMemorySize, G::SMEM) !=
         cudaSuccess)
         return lnf_fail(ctx, LNF_ECUDA, "gate kernel: shared memory attribute (%d bytes)", G::SMEM);
@@ -539,7 +596,6 @@ lnf_status gate_dispatch_t(lnf_ctx *ctx, const FilterJob &j, void *const outs[5]
     a.ny = j.ny;
     a.nz = j.nz;
     a.n = n;
-    a.nchunks = (u32)((n + kChunkVox - 1) / kChunkVox);
     a.prm = j.prm;
     a.lut = j.lut;
     a.counter = ctx->d_counter + 14;

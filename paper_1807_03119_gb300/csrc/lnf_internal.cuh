@@ -12,13 +12,11 @@ typedef unsigned int u32;
 #define LNF_LEVELS_U8 256
 #define LNF_LEVELS_U16 65536
 
-// Statistics of one volume, accumulated on the device by the stats kernel.
+// Size of one volume's statistics pass; the pass itself accumulates only the
+// grey-level histogram (sum P, sum P^2, min and max follow from it in the
+// parameter kernels).
 struct DevStats {
-    u64 N;          // voxel count (set by the host before the pass)
-    u64 S;          // sum P
-    u64 Q;          // sum P^2 (fits: N < 2^32 and P <= 65535)
-    u32 minv;
-    u32 maxv;
+    u64 N;          // voxel count (set before the pass)
     u32 levels;     // 256 or 65536
     u32 pad;
 };
@@ -33,7 +31,7 @@ struct ParamCfg {
     long long entropy_te;       // >= 0, -1 = pass all, -2 = auto (per radius)
 };
 
-// Parameters derived on the device from DevStats + histogram (one per volume).
+// Parameters derived on the device from the histogram (one per volume).
 struct DevParams {
     u64 N, S, Q;
     u32 minv, maxv;
@@ -227,10 +225,9 @@ __device__ __forceinline__ void prefetch_tmap(const CUtensorMap *map)
 
 // ----------------------------------------------------------------- launchers
 // (defined in stats.cu / filter.cu; all enqueue on `stream`)
-cudaError_t lnf_launch_stats(const void *vol, u64 n, int dtype, u64 *hist, DevStats *st, int num_sms,
-                             cudaStream_t stream);
+cudaError_t lnf_launch_stats(const void *vol, u64 n, int dtype, u64 *hist, int num_sms, cudaStream_t stream);
 cudaError_t lnf_launch_stats_init(u64 *hist, u32 levels, DevStats *st, u64 n, cudaStream_t stream);
-// parameter derivation: two launches over chunks of 1024 grey levels; pscr is
+// parameter derivation: two launches over chunks of 256 grey levels; pscr is
 // per-volume device scratch of lnf_param_scratch_bytes() bytes, zeroed once
 cudaError_t lnf_launch_params(const u64 *hist, const DevStats *st, const ParamCfg &cfg, DevParams *prm,
                               u32 *lut, void *pscr, int dtype, cudaStream_t stream);

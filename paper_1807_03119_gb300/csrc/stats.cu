@@ -1,13 +1,15 @@
 // Statistics pre-pass and parameter derivation, on the device.
 //
-//   k_stats   : one read of the volume -> grey-level histogram h[v], S = sum P,
-//               Q = sum P^2, min, max  (the "normalized frequency distribution"
-//               the entropy filter precomputes, section "Entropy Filter", and
-//               the inputs of the Otsu threshold, Eq. 1, and the global sigma
-//               of the sigma filter, Eq. 5).
-//   k_params  : one CTA -> Otsu threshold T (Eq. 1) in exact integer
-//               arithmetic, sigma band delta, Okada T_d, the fixed-point
-//               entropy weights w[v] of Eq. 7, and the input image entropy.
+//   k_stats   : one read of the volume -> grey-level histogram h[v] (the
+//               "normalized frequency distribution" the entropy filter
+//               precomputes, section "Entropy Filter", and all the Otsu
+//               threshold, Eq. 1, and the global sigma of the sigma filter,
+//               Eq. 5, need: S = sum v h[v], Q = sum v^2 h[v], min and max
+//               are taken from it).
+//   k_param_totals / k_params : per chunk of 256 levels, then the last chunk
+//               -> Otsu threshold T (Eq. 1) in exact integer arithmetic, sigma
+//               band delta, Okada T_d, the fixed-point entropy weights w[v] of
+//               Eq. 7, and the input image entropy.
 //   k_entropy : image entropy H = -sum (c/N) log2(c/N) of a histogram (the
 //               measure of the paper's Fig. 4), FP64 only in this reduction.
 #include "lnf_internal.cuh"
@@ -18,8 +20,25 @@ typedef __int128 i128;
 namespace {
 
 constexpr int kStatsThreads = 1024;
-constexpr int kSmemBinsU16 = 32768;   // u16 values >= this go straight to global atomics
-constexpr int kReplicasU8 = 16;       // sub-histograms for 8-bit data (fewer bank conflicts)
+// CTA histograms in shared memory, laid out so that the lanes of a warp rarely
+// meet in one bank (random grey levels otherwise collide about 3-4 deep):
+//   8-bit  : one copy of the 256 bins per lane, bin v of lane L at word 32 v + L
+//            (its own bank: no conflicts within a warp);
+//   16-bit, chosen per CTA from the vectors its threads stream first:
+//     low  : (7/8 of them hold only levels below 4096: 12-bit data) eight copies
+//            of the levels v < 4096, bin v of lane group g = L % 8 at word
+//            8 v + g (bank 8 (v % 4) + g); levels above to the global histogram;
+//     wide : one copy of the levels v < 32768; levels above to the global
+//            histogram.
+// Both 16-bit layouts take 128 KB, which leaves L1 room for the loads in
+// flight (larger CTA histograms measured slower).
+constexpr int kLaneCopiesU8 = 32;
+constexpr int kLowBinsU16 = 4096;
+constexpr int kLowCopiesU16 = 8;
+constexpr int kWideBinsU16 = 32768;
+constexpr int kSmemWordsU8 = LNF_LEVELS_U8 * kLaneCopiesU8;
+constexpr int kSmemWordsU16 = kWideBinsU16;
+static_assert(kLowBinsU16 * kLowCopiesU16 == kSmemWordsU16, "both 16-bit layouts fill the same words");
 
 // ------------------------------------------------------------------ init
 
@@ -29,10 +48,6 @@ __global__ void k_stats_init(u64 *hist, u32 levels, DevStats *st, u64 n)
         hist[i] = 0;
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         st->N = n;
-        st->S = 0;
-        st->Q = 0;
-        st->minv = 0xFFFFFFFFu;
-        st->maxv = 0;
         st->levels = levels;
         st->pad = 0;
     }
@@ -47,10 +62,6 @@ __global__ void k_stats_init_batched(const __grid_constant__ StatsPack pk)
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         DevStats *st = j.st;
         st->N = j.n;
-        st->S = 0;
-        st->Q = 0;
-        st->minv = 0xFFFFFFFFu;
-        st->maxv = 0;
         st->levels = levels;
         st->pad = 0;
     }
@@ -64,48 +75,53 @@ __global__ void k_zero(u64 *p, u64 count)
 
 // ------------------------------------------------------------------ stats
 
-struct StatsAcc {
-    u64 s, q;
-    u32 mn, mx;
-};
-
+// one grey level into the CTA's histogram.  8-bit: word 32 v + lane.  16-bit:
+// levels below `lim` to word v mul + lw (low layout: mul = 8, lw = L % 8,
+// lim = 4096; wide layout: mul = 1, lw = 0, lim = 32768), the rest to the
+// global histogram.
 template <typename T>
-__device__ __forceinline__ void stats_value(u32 v, u32 *sh, u64 *hist, StatsAcc &a)
+__device__ __forceinline__ void stats_value(u32 v, u32 *sh, u32 lw, u32 mul, u32 lim, u64 *hist)
 {
     if (sizeof(T) == 1) {
-        atomicAdd(&sh[v], 1u);
+        atomicAdd(&sh[v * kLaneCopiesU8 + lw], 1u);
+    } else if (v < lim) {
+        atomicAdd(&sh[v * mul + lw], 1u);
     } else {
-        if (v < (u32)kSmemBinsU16)
-            atomicAdd(&sh[v], 1u);
-        else
-            atomicAdd(&hist[v], 1ull);
+        atomicAdd(&hist[v], 1ull);
     }
-    a.s += v;
-    a.q += (u64)v * v;
-    a.mn = min(a.mn, v);
-    a.mx = max(a.mx, v);
 }
 
 template <typename T>
-__device__ void stats_body(const T *vol, u64 n, u64 *hist, DevStats *st, u64 cta, u64 nctas, u32 *smem)
+__device__ void stats_body(const T *vol, u64 n, u64 *hist, u64 cta, u64 nctas, u32 *sh)
 {
-    const int bins = sizeof(T) == 1 ? LNF_LEVELS_U8 * kReplicasU8 : kSmemBinsU16;
-    for (int i = threadIdx.x; i < bins; i += blockDim.x)
-        smem[i] = 0;
-    __syncthreads();
-    u32 *sh = sizeof(T) == 1 ? smem + ((threadIdx.x >> 5) % kReplicasU8) * LNF_LEVELS_U8 : smem;
-
-    StatsAcc a{0, 0, 0xFFFFFFFFu, 0};
     const u64 gtid = cta * blockDim.x + threadIdx.x;
     const u64 gsz = nctas * blockDim.x;
     // elements before the first 16-byte boundary
     u64 head = ((16 - (reinterpret_cast<uintptr_t>(vol) & 15)) & 15) / sizeof(T);
     if (head > n)
         head = n;
-    for (u64 i = gtid; i < head; i += gsz)
-        stats_value<T>(vol[i], sh, hist, a);
-    const uint4 *v4 = reinterpret_cast<const uint4 *>(vol + head);
     const u64 nv = (n - head) * sizeof(T) / 16;
+    const int words = sizeof(T) == 1 ? kSmemWordsU8 : kSmemWordsU16;
+    for (int i = threadIdx.x; i < words; i += blockDim.x)
+        sh[i] = 0;
+    // 16-bit: the layout from the vector each thread streams first (contiguous
+    // over the grid, so the sample costs no scattered reads; a thread without
+    // one counts as low): low where 7/8 of the CTA's threads saw only levels
+    // below 4096.  The count is also the barrier after the zeroing.
+    bool lo = true;
+    if (sizeof(T) == 2 && gtid < nv) {
+        const uint4 q = __ldg(reinterpret_cast<const uint4 *>(vol + head) + gtid);
+        lo = ((q.x | q.y | q.z | q.w) & 0xF000F000u) == 0u;
+    }
+    const bool low = __syncthreads_count(lo) * 8 >= (int)blockDim.x * 7;
+    const u32 lane = threadIdx.x & 31;
+    const u32 lw = sizeof(T) == 1 ? lane : (low ? lane % kLowCopiesU16 : 0u);
+    const u32 mul = low ? (u32)kLowCopiesU16 : 1u;
+    const u32 lim = low ? (u32)kLowBinsU16 : (u32)kWideBinsU16;
+
+    for (u64 i = gtid; i < head; i += gsz)
+        stats_value<T>(vol[i], sh, lw, mul, lim, hist);
+    const uint4 *v4 = reinterpret_cast<const uint4 *>(vol + head);
     // four independent 16-byte loads in flight per thread before any is consumed
     constexpr int kU = 4;
     for (u64 i = gtid; i < nv; i += kU * gsz) {
@@ -119,62 +135,48 @@ __device__ void stats_body(const T *vol, u64 n, u64 *hist, DevStats *st, u64 cta
         for (int u = 0; u < kU; ++u) {
             if (i + u * gsz >= nv)
                 break;
-            const u32 words[4] = {w[u].x, w[u].y, w[u].z, w[u].w};
+            const u32 words4[4] = {w[u].x, w[u].y, w[u].z, w[u].w};
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
                 if (sizeof(T) == 1) {
 #pragma unroll
                     for (int b = 0; b < 4; ++b)
-                        stats_value<T>((words[k] >> (8 * b)) & 0xFFu, sh, hist, a);
+                        stats_value<T>((words4[k] >> (8 * b)) & 0xFFu, sh, lw, mul, lim, hist);
                 } else {
-                    stats_value<T>(words[k] & 0xFFFFu, sh, hist, a);
-                    stats_value<T>(words[k] >> 16, sh, hist, a);
+                    stats_value<T>(words4[k] & 0xFFFFu, sh, lw, mul, lim, hist);
+                    stats_value<T>(words4[k] >> 16, sh, lw, mul, lim, hist);
                 }
             }
         }
     }
     for (u64 i = head + nv * (16 / sizeof(T)) + gtid; i < n; i += gsz)
-        stats_value<T>(vol[i], sh, hist, a);
+        stats_value<T>(vol[i], sh, lw, mul, lim, hist);
     __syncthreads();
+    // the copies of each level added up, one global atomic per occupied level
     if (sizeof(T) == 1) {
         for (int v = threadIdx.x; v < LNF_LEVELS_U8; v += blockDim.x) {
             u32 c = 0;
-            for (int r = 0; r < kReplicasU8; ++r)
-                c += smem[r * LNF_LEVELS_U8 + v];
+            for (int r = 0; r < kLaneCopiesU8; ++r)
+                c += sh[v * kLaneCopiesU8 + ((r + v) & 31)];
             if (c)
                 atomicAdd(&hist[v], (u64)c);
         }
     } else {
-        for (int v = threadIdx.x; v < kSmemBinsU16; v += blockDim.x) {
-            u32 c = smem[v];
+        for (u32 v = threadIdx.x; v < lim; v += blockDim.x) {
+            u32 c = 0;
+            for (u32 r = 0; r < mul; ++r)
+                c += sh[v * mul + r];
             if (c)
                 atomicAdd(&hist[v], (u64)c);
         }
     }
-    // warp reduction of the moments, then one atomic per warp
-    for (int o = 16; o > 0; o >>= 1) {
-        a.s += __shfl_xor_sync(0xFFFFFFFFu, a.s, o);
-        a.q += __shfl_xor_sync(0xFFFFFFFFu, a.q, o);
-        a.mn = min(a.mn, __shfl_xor_sync(0xFFFFFFFFu, a.mn, o));
-        a.mx = max(a.mx, __shfl_xor_sync(0xFFFFFFFFu, a.mx, o));
-    }
-    if ((threadIdx.x & 31) == 0) {
-        if (a.s)
-            atomicAdd(&st->S, a.s);
-        if (a.q)
-            atomicAdd(&st->Q, a.q);
-        if (a.mn != 0xFFFFFFFFu)
-            atomicMin(&st->minv, a.mn);
-        if (a.mx)
-            atomicMax(&st->maxv, a.mx);
-    }
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kStatsThreads) k_stats(const T *vol, u64 n, u64 *hist, DevStats *st)
+__global__ void __launch_bounds__(kStatsThreads) k_stats(const T *vol, u64 n, u64 *hist)
 {
     extern __shared__ u32 smem[];
-    stats_body<T>(vol, n, hist, st, blockIdx.x, gridDim.x, smem);
+    stats_body<T>(vol, n, hist, blockIdx.x, gridDim.x, smem);
 }
 
 __global__ void __launch_bounds__(kStatsThreads) k_stats_batched(const __grid_constant__ StatsPack pk)
@@ -182,9 +184,9 @@ __global__ void __launch_bounds__(kStatsThreads) k_stats_batched(const __grid_co
     extern __shared__ u32 smem[];
     const StatsJob &j = pk.jobs[blockIdx.y];
     if (j.dtype == 0)
-        stats_body<uint8_t>(static_cast<const uint8_t *>(j.vol), j.n, j.hist, j.st, blockIdx.x, gridDim.x, smem);
+        stats_body<uint8_t>(static_cast<const uint8_t *>(j.vol), j.n, j.hist, blockIdx.x, gridDim.x, smem);
     else
-        stats_body<uint16_t>(static_cast<const uint16_t *>(j.vol), j.n, j.hist, j.st, blockIdx.x, gridDim.x, smem);
+        stats_body<uint16_t>(static_cast<const uint16_t *>(j.vol), j.n, j.hist, blockIdx.x, gridDim.x, smem);
 }
 
 // ------------------------------------------------------------------ exact helpers
@@ -282,8 +284,11 @@ struct ParamPartial {          // one per chunk
 };
 
 struct ParamScratch {
-    u64 tot_n[LNF_LEVELS_U16 / kChunk];
-    u64 tot_s[LNF_LEVELS_U16 / kChunk];
+    u64 tot_n[LNF_LEVELS_U16 / kChunk];   // per chunk: sum h[v]
+    u64 tot_s[LNF_LEVELS_U16 / kChunk];   //            sum v h[v]
+    u64 tot_q[LNF_LEVELS_U16 / kChunk];   //            sum v^2 h[v]
+    u32 lo[LNF_LEVELS_U16 / kChunk];      //            first occupied level (0xFFFFFFFF: none)
+    u32 hi[LNF_LEVELS_U16 / kChunk];      //            last occupied level (0: none)
     ParamPartial part[LNF_LEVELS_U16 / kChunk];
     u32 done;                  // chunks finished (reset by the last one)
     u32 pad[3];
@@ -291,42 +296,64 @@ struct ParamScratch {
 
 __device__ __forceinline__ int n_chunks(u32 levels) { return (int)((levels + kChunk - 1) / kChunk); }
 
-// pass 1: per chunk, count and sum of its levels
+// pass 1: per chunk, the count, sum and sum of squares of its levels and its
+// first and last occupied level
 __device__ void chunk_totals(const u64 *hist, u32 levels, ParamScratch *ps, int c)
 {
-    __shared__ u64 rn[kPThreads / 32], rs[kPThreads / 32];
-    u64 n = 0, s = 0;
+    __shared__ u64 rn[kPThreads / 32], rs[kPThreads / 32], rq[kPThreads / 32];
+    __shared__ u32 rlo[kPThreads / 32], rhi[kPThreads / 32];
+    u64 n = 0, s = 0, q = 0;
+    u32 lo = 0xFFFFFFFFu, hi = 0;
     for (int i = threadIdx.x; i < kChunk; i += blockDim.x) {
         const u32 v = c * kChunk + i;
         if (v < levels) {
             const u64 h = hist[v];
             n += h;
             s += h * v;
+            q += h * ((u64)v * v);
+            if (h) {
+                lo = min(lo, v);
+                hi = max(hi, v);
+            }
         }
     }
     for (int o = 16; o > 0; o >>= 1) {
         n += __shfl_xor_sync(0xFFFFFFFFu, n, o);
         s += __shfl_xor_sync(0xFFFFFFFFu, s, o);
+        q += __shfl_xor_sync(0xFFFFFFFFu, q, o);
+        lo = min(lo, __shfl_xor_sync(0xFFFFFFFFu, lo, o));
+        hi = max(hi, __shfl_xor_sync(0xFFFFFFFFu, hi, o));
     }
     if ((threadIdx.x & 31) == 0) {
         rn[threadIdx.x >> 5] = n;
         rs[threadIdx.x >> 5] = s;
+        rq[threadIdx.x >> 5] = q;
+        rlo[threadIdx.x >> 5] = lo;
+        rhi[threadIdx.x >> 5] = hi;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        u64 tn = 0, ts = 0;
+        u64 tn = 0, ts = 0, tq = 0;
+        u32 tlo = 0xFFFFFFFFu, thi = 0;
         for (int w = 0; w < kPThreads / 32; ++w) {
             tn += rn[w];
             ts += rs[w];
+            tq += rq[w];
+            tlo = min(tlo, rlo[w]);
+            thi = max(thi, rhi[w]);
         }
         ps->tot_n[c] = tn;
         ps->tot_s[c] = ts;
+        ps->tot_q[c] = tq;
+        ps->lo[c] = tlo;
+        ps->hi[c] = thi;
     }
 }
 
 struct PSmem {
     u64 h[kChunk];
-    u64 pn[kPThreads], ps[kPThreads];
+    u64 pn[kPThreads], ps[kPThreads], pq[kPThreads];
+    u32 plo[kPThreads], phi[kPThreads];
     u128 q[kPThreads];
     u64 fnum[kPThreads], fden[kPThreads];
     u32 t[kPThreads];
@@ -342,28 +369,49 @@ __device__ void chunk_params(const u64 *hist, const DevStats *st, const ParamCfg
 {
     const int tid = threadIdx.x;
     const u32 L = st->levels;
-    const u64 N = st->N, S = st->S, Q = st->Q;
+    const u64 N = st->N;
     const int nc = n_chunks(L);
-    // prefix of the chunks before this one (c < kPThreads: one total per thread)
-    u64 n0 = 0, s0 = 0;
+    // prefix of the chunks before this one (c < kPThreads: one total per thread),
+    // and the whole volume's S = sum P, Q = sum P^2, min and max over all chunks
+    u64 n0 = 0, s0 = 0, S = 0, Q = 0;
+    u32 minv = 0xFFFFFFFFu, maxv = 0;
     {
-        u64 an = 0, as = 0;
-        for (int k = tid; k < c; k += blockDim.x) {
-            an += ps->tot_n[k];
-            as += ps->tot_s[k];
+        u64 an = 0, as = 0, ss = 0, sq = 0;
+        u32 mn = 0xFFFFFFFFu, mx = 0;
+        for (int k = tid; k < nc; k += blockDim.x) {
+            if (k < c) {
+                an += ps->tot_n[k];
+                as += ps->tot_s[k];
+            }
+            ss += ps->tot_s[k];
+            sq += ps->tot_q[k];
+            mn = min(mn, ps->lo[k]);
+            mx = max(mx, ps->hi[k]);
         }
         for (int o = 16; o > 0; o >>= 1) {
             an += __shfl_xor_sync(0xFFFFFFFFu, an, o);
             as += __shfl_xor_sync(0xFFFFFFFFu, as, o);
+            ss += __shfl_xor_sync(0xFFFFFFFFu, ss, o);
+            sq += __shfl_xor_sync(0xFFFFFFFFu, sq, o);
+            mn = min(mn, __shfl_xor_sync(0xFFFFFFFFu, mn, o));
+            mx = max(mx, __shfl_xor_sync(0xFFFFFFFFu, mx, o));
         }
         if ((tid & 31) == 0) {
             sm.pn[tid >> 5] = an;
             sm.ps[tid >> 5] = as;
+            sm.pq[tid >> 5] = sq;
+            sm.hw[tid >> 5] = ss;
+            sm.plo[tid >> 5] = mn;
+            sm.phi[tid >> 5] = mx;
         }
         __syncthreads();
         for (int w = 0; w < kPThreads / 32; ++w) {
             n0 += sm.pn[w];
             s0 += sm.ps[w];
+            S += sm.hw[w];
+            Q += sm.pq[w];
+            minv = min(minv, sm.plo[w]);
+            maxv = max(maxv, sm.phi[w]);
         }
         __syncthreads();
     }
@@ -516,7 +564,7 @@ __device__ void chunk_params(const u64 *hist, const DevStats *st, const ParamCfg
     const u32 t_best = sm.t[0];
     const u64 hws = sm.hw[0];
     const double Hs = sm.d[0];
-    const u32 T_gate = cfg.threshold_mode == 0 ? (t_best ? t_best : st->minv)
+    const u32 T_gate = cfg.threshold_mode == 0 ? (t_best ? t_best : minv)
                                                : (cfg.threshold_mode == 1 ? cfg.threshold_value : 0u);
     {
         const int cT = (int)(T_gate / kChunk);
@@ -541,7 +589,7 @@ __device__ void chunk_params(const u64 *hist, const DevStats *st, const ParamCfg
     OtsuJ b;
     b.t = t_best;
     ps->done = 0;
-    const u32 t_otsu = b.t ? b.t : st->minv;   // single level: T = that level
+    const u32 t_otsu = b.t ? b.t : minv;   // single level: T = that level
     const u128 var_num = (u128)N * Q - (u128)S * S;   // N^2 sigma^2
     const u128 nn = (u128)N * N;
     const u128 k2 = (u128)cfg.sigma_k * (u128)cfg.sigma_k;
@@ -551,8 +599,8 @@ __device__ void chunk_params(const u64 *hist, const DevStats *st, const ParamCfg
     p.N = N;
     p.S = S;
     p.Q = Q;
-    p.minv = st->minv;
-    p.maxv = st->maxv;
+    p.minv = minv;
+    p.maxv = maxv;
     p.T = cfg.threshold_mode == 0 ? t_otsu : (cfg.threshold_mode == 1 ? cfg.threshold_value : 0u);
     p.delta = delta > 0xFFFFFFFFull ? 0xFFFFFFFFu : (u32)delta;
     p.td = cfg.okada_td >= 0 ? cfg.okada_td : (long long)(sig + 1);
@@ -674,7 +722,7 @@ __global__ void __launch_bounds__(256) k_entropy_pack(const __grid_constant__ En
 
 size_t stats_smem_bytes(int dtype)
 {
-    return dtype == 0 ? sizeof(u32) * LNF_LEVELS_U8 * kReplicasU8 : sizeof(u32) * kSmemBinsU16;
+    return sizeof(u32) * (dtype == 0 ? kSmemWordsU8 : kSmemWordsU16);
 }
 
 }  // namespace
@@ -698,8 +746,7 @@ cudaError_t lnf_launch_zero(u64 *p, u64 count, cudaStream_t stream)
     return cudaGetLastError();
 }
 
-cudaError_t lnf_launch_stats(const void *vol, u64 n, int dtype, u64 *hist, DevStats *st, int num_sms,
-                             cudaStream_t stream)
+cudaError_t lnf_launch_stats(const void *vol, u64 n, int dtype, u64 *hist, int num_sms, cudaStream_t stream)
 {
     const size_t smem = stats_smem_bytes(dtype);
     cudaError_t e;
@@ -709,14 +756,14 @@ cudaError_t lnf_launch_stats(const void *vol, u64 n, int dtype, u64 *hist, DevSt
             return e;
         u64 want = (n + 16ull * kStatsThreads - 1) / (16ull * kStatsThreads);
         int grid = (int)(want < (u64)(2 * num_sms) ? (want ? want : 1) : 2 * num_sms);
-        k_stats<uint8_t><<<grid, kStatsThreads, smem, stream>>>(static_cast<const uint8_t *>(vol), n, hist, st);
+        k_stats<uint8_t><<<grid, kStatsThreads, smem, stream>>>(static_cast<const uint8_t *>(vol), n, hist);
     } else {
         e = cudaFuncSetAttribute(k_stats<uint16_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess)
             return e;
         u64 want = (n + 8ull * kStatsThreads - 1) / (8ull * kStatsThreads);
         int grid = (int)(want < (u64)num_sms ? (want ? want : 1) : num_sms);
-        k_stats<uint16_t><<<grid, kStatsThreads, smem, stream>>>(static_cast<const uint16_t *>(vol), n, hist, st);
+        k_stats<uint16_t><<<grid, kStatsThreads, smem, stream>>>(static_cast<const uint16_t *>(vol), n, hist);
     }
     return cudaGetLastError();
 }

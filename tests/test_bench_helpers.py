@@ -35,19 +35,19 @@ def test_kind_of_kernel():
     k = bench.kind_of_kernel
     assert k("void <unnamed>::k_fast2<unsigned short, 2, 1, 0>(CUtensorMap_st, <unnamed>::Args2)") == "filter:sigma"
     assert k("void <unnamed>::k_fast2<unsigned char, 1, 0, 1>(CUtensorMap_st, <unnamed>::Args2)") == "filter:mean"
-    assert k("void gatek::k_eval<unsigned short, 2, 3>(gatek::EvalArgs)") == "gate:eval"
-    assert k("void gatek::k_eval<unsigned char, 4, 1>(gatek::EvalArgs)") == "gate:eval_ours"
-    assert k("void gatek::k_scan<unsigned short>(gatek::ScanArgs)") == "gate:scan"
+    assert k("void gatek::k_gate<unsigned short, 2, 3>(gatek::GateArgs)") == "filter:gate"
+    assert k("void gatek::k_gate<unsigned char, 4, 1>(gatek::GateArgs)") == "gate:ours"
+    assert k("void gatek::k_gate<unsigned short, 1, 2>(gatek::GateArgs)") == "gate:cube"
     assert k("void <unnamed>::k_ours_fast<unsigned short, 2, 0>(CUtensorMap_st, <unnamed>::FastArgs)") == "filter:ours"
     assert k("void at::native::vectorized_elementwise_kernel<4>(int)") is None
 
 
 def test_record_traffic_leaves_out_launches_that_returned(tmp_path, monkeypatch):
     rows = [
-        ("1", "void gatek::k_eval<unsigned short, 2, 3>(X)", 150e6, 600e6),
+        ("1", "void gatek::k_gate<unsigned short, 2, 3>(X)", 150e6, 600e6),
         ("2", "void <unnamed>::k_fast2<unsigned short, 2, 1, 0>(X)", 0.0, 0.0),   # returned at once
         ("3", "void <unnamed>::k_ours_fast<unsigned short, 2, 0>(X)", 151e6, 105e6),
-        ("4", "void gatek::k_eval<unsigned short, 2, 3>(X)", 152e6, 602e6),
+        ("4", "void gatek::k_gate<unsigned short, 2, 3>(X)", 152e6, 602e6),
     ]
     lines = ['"ID","Kernel Name","Metric Name","Metric Unit","Metric Value"']
     for i, name, rd, wr in rows:
@@ -59,6 +59,6 @@ def test_record_traffic_leaves_out_launches_that_returned(tmp_path, monkeypatch)
     monkeypatch.setattr(bench, "TRAFFIC_FILE", str(out))
     bench.record_traffic(str(csv), 2.0)
     got = {ln.split()[0]: int(ln.split()[1]) for ln in out.read_text().splitlines()}
-    assert set(got) == {"gate:eval", "filter:ours"}
-    assert got["gate:eval"] == round((150e6 + 600e6 + 152e6 + 602e6) / 2 * 2.0)
+    assert set(got) == {"filter:gate", "filter:ours"}
+    assert got["filter:gate"] == round((150e6 + 600e6 + 152e6 + 602e6) / 2 * 2.0)
     assert got["filter:ours"] == round((151e6 + 105e6) * 2.0)

@@ -249,6 +249,43 @@ def test_entropy_call(ctx):
         assert abs(H - want) <= H_TOL * max(1.0, want)
 
 
+def test_histogram_at_scale_with_a_dominant_level(ctx):
+    """50 M voxels, 90% of them one grey level (a 12-bit one, one near 31000,
+    and an 8-bit one), the rest spread over the 12-bit levels, the levels up
+    to 32767 and the levels above: N, sum P, sum P^2, min, max and the image
+    entropy from the device histogram against exact host sums."""
+    rng = np.random.default_rng(91)
+    for dt, base in (("u16", 1000), ("u16", 31000), ("u8", 77)):
+        n = 512 * 512 * 192
+        if dt == "u16":
+            # base 1000: 12-bit data (the CTAs take the eight-copy layout of the
+            # low levels); base 31000: the one-copy layout up to 32767
+            vol = np.full(n, base, np.uint16)
+            k = n // 10
+            idx = rng.choice(n, k, replace=False)
+            part = rng.integers(0, 3, k)
+            vals = np.where(part == 0, rng.integers(0, 4096, k),
+                            np.where(part == 1, rng.integers(4096, 32768, k), rng.integers(32768, 65536, k)))
+            vol[idx] = vals.astype(np.uint16)
+        else:
+            vol = np.full(n, base, np.uint8)
+            idx = rng.choice(n, n // 10, replace=False)
+            vol[idx] = rng.integers(0, 256, n // 10).astype(np.uint8)
+        vol = vol.reshape(192, 512, 512)
+        t = dev(vol)
+        H = ctx.entropy(t)
+        ctx.filter_volume(t, oracle.OURS, 1)
+        p = ctx.params()
+        v64 = vol.astype(np.uint64)
+        assert p["n_voxels"] == n
+        assert p["sum"] == int(v64.sum()), dt
+        assert p["sum_sq"] == int((v64 * v64).sum()), dt
+        assert p["min_value"] == int(vol.min()) and p["max_value"] == int(vol.max()), dt
+        want = oracle.image_entropy(np.bincount(vol.ravel(), minlength=65536 if dt == "u16" else 256))
+        assert abs(H - want) <= H_TOL * max(1.0, want), (dt, H, want)
+        del t
+
+
 def test_multi_host_buffers(ctx):
     vol = phantoms.insect_phantom((48, 40, 33), 15, "u16")
     st = oracle.stats(vol)
