@@ -235,11 +235,12 @@ class ClockSampler:
 
 # ----------------------------------------------------------------------------- CPU oracle
 
-def oracle_step_sample(vol, st, planes, threads):
+def oracle_step_sample(vol, planes, threads):
     """Time the oracle on a bounded sample of one step: statistics and parameter
     derivation of the whole volume, then each filter on `planes` z-planes of the
     full 512x512 cross-section, split over `threads` threads (the C oracle
-    releases the GIL).  Returns (seconds for one full step, description)."""
+    releases the GIL).  Returns a dict: `sample_s` the wall time measured,
+    `projected_s` the full step (filter time scaled by nz / planes), `desc`."""
     import oracle
     from concurrent.futures import ThreadPoolExecutor
     t0 = time.perf_counter()
@@ -258,12 +259,41 @@ def oracle_step_sample(vol, st, planes, threads):
         with ThreadPoolExecutor(max_workers=threads) as ex:
             list(ex.map(lambda s: oracle.filter_volume(vol, f, RADIUS, params=prm,
                                                        roi=(0, 0, s[0], nx, ny, s[1])), slabs))
-        t_filters += (time.perf_counter() - t0) * (nz / planes)
-    total = t_stats + t_params + t_filters
+        t_filters += time.perf_counter() - t0
     desc = (f"oracle (plain C per-voxel enumeration + exact Python parameters): statistics and parameters "
-            f"of the whole 512^3 volume, each filter on {planes} z-planes x 512x512 ({planes * nx * ny} voxels) "
-            f"over {threads} threads, filter time scaled by {nz}/{planes} to the full step")
-    return total, desc
+            f"of the whole {nx}x{ny}x{nz} volume, each filter on {planes} z-planes x {nx}x{ny} "
+            f"({planes * nx * ny} voxels) over {threads} threads; the full step projects the filter time "
+            f"by {nz}/{planes}")
+    return {"sample_s": t_stats + t_params + t_filters,
+            "projected_s": t_stats + t_params + t_filters * (nz / planes),
+            "stats_params_s": t_stats + t_params, "filter_sample_s": t_filters, "desc": desc}
+
+
+def oracle_single_thread(vol, planes=2):
+    """The oracle's filters on one thread: `planes` z-planes of the volume per
+    filter at the bench radius (parameters derived beforehand, not timed).
+    Returns the filter throughput in GVoxel/s (five filters' voxels) and a
+    description."""
+    import oracle
+    st = oracle.stats(vol)
+    prm = oracle.derive_params(st, RADIUS)
+    nz, ny, nx = vol.shape
+    z0 = nz // 2 - planes // 2
+    t0 = time.perf_counter()
+    for f in range(5):
+        oracle.filter_volume(vol, f, RADIUS, params=prm, roi=(0, 0, z0, nx, ny, planes))
+    dt = time.perf_counter() - t0
+    return 5 * planes * nx * ny / dt / 1e9, (f"one thread, each filter on {planes} z-planes x {nx}x{ny} "
+                                             f"({planes * nx * ny} voxels), statistics and parameters not timed")
+
+
+def cpu_baseline_entry(vol, threads, sample):
+    """The cpu_baseline object from one step sample (see oracle_step_sample)."""
+    st_value, st_desc = oracle_single_thread(vol)
+    return {"value": 5 * N_VOX / sample["projected_s"] / 1e9, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": sample["desc"], "sample_ms": sample["sample_s"] * 1e3,
+            "projected_step_ms": sample["projected_s"] * 1e3,
+            "single_thread": {"value": st_value, "unit": UNIT, "sample": st_desc}}
 
 
 def run_reference(args):
@@ -274,23 +304,152 @@ def run_reference(args):
     vol = phantoms.P2()
     threads = os.cpu_count() or 1
     planes = max(threads, 4)
-    st = None
     for _ in range(args.warmup):
-        oracle_step_sample(vol, st, planes, threads)
-    times = []
-    desc = ""
-    for _ in range(args.steps):
-        t, desc = oracle_step_sample(vol, st, planes, threads)
-        times.append(t)
-    t = sum(times) / len(times)
-    value = 5 * N_VOX / t / 1e9
+        oracle_step_sample(vol, planes, threads)
+    samples = [oracle_step_sample(vol, planes, threads) for _ in range(args.steps)]
+    mean = {k: sum(s[k] for s in samples) / len(samples) for k in ("sample_s", "projected_s")}
+    mean["desc"] = samples[-1]["desc"]
+    cpu = cpu_baseline_entry(vol, threads, mean)
+    value = cpu["value"]
+    # ms_per_step: what one step of this run timed (the bounded sample); the metric's
+    # value: the full 512^3 step projected from it (projected_step_ms)
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": mean["sample_s"] * 1e3,
+            "projected_step_ms": mean["projected_s"] * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u16", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "radius": RADIUS, "filters": FILTER_NAMES},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": desc},
+            "config": {"workload": WORKLOAD, "radius": RADIUS, "filters": FILTER_NAMES,
+                       "sample": "each step: the oracle on a bounded sample of the step (cpu_baseline.sample)"},
+            "cpu_baseline": cpu,
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
+
+
+# ----------------------------------------------------------------------------- extra configurations
+
+def start_generation():
+    """Draw the extra workloads' volumes (the 1024^3 uint8 phantom, the 64^3
+    phantom, the served and the batched volumes) in a spawn process pool started
+    before any CUDA call, while the GPU runs the main step."""
+    import multiprocessing as mp
+    from concurrent.futures import ProcessPoolExecutor
+    import phantoms
+    ex = ProcessPoolExecutor(max_workers=max(1, min(16, os.cpu_count() or 1)), mp_context=mp.get_context("spawn"))
+    specs = phantoms.batch_volume_specs(64)
+    sizes = served_sizes()
+    futs = {"P3": ex.submit(phantoms.P3), "P1": ex.submit(phantoms.P1),
+            "served": [ex.submit(phantoms.insect_phantom, (n, n, n), 2000 + i, "u16") for i, n in enumerate(sizes)],
+            "batch": [ex.submit(phantoms.batch_volume, sp) for sp in specs]}
+    return ex, futs, specs, sizes
+
+
+def finish_generation(gen):
+    ex, futs, specs, sizes = gen
+    out = {"P3": futs["P3"].result(), "P1": futs["P1"].result(), "served": [f.result() for f in futs["served"]],
+           "batch": [f.result() for f in futs["batch"]], "specs": specs, "sizes": sizes}
+    ex.shutdown()
+    return out
+
+
+def timed_calls(ctx, fn, torch, warmup, steps):
+    """CUDA-event ms per call of `fn` on torch's current stream, and the mean ms
+    per call of each kernel kind the library's profiler bracketed."""
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    ctx.profile(True)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        fn()
+    e1.record()
+    torch.cuda.synchronize()
+    kern, _ = ctx.profile_read()
+    ctx.profile(False)
+    return e0.elapsed_time(e1) / steps, {k: v[1] / steps for k, v in kern.items()}
+
+
+def ours_kernel(kern):
+    """The kernel that did the paper's filter's work in a single-filter call: the
+    gate-first kernel or the ring kernel (the other returns at once)."""
+    cands = {k: v for k, v in kern.items() if k in ("gate:ours", "filter:ours")}
+    k = max(cands, key=cands.get)
+    return k, cands[k]
+
+
+def extra_configs(lnf, torch, gen, t_p2, hbm_gbs, warmup, steps):
+    """The workloads beside the main step, each on its own inputs (all larger
+    than L2 except the 64^3 latency case, which flushes L2 between calls)."""
+    import numpy as np
+    res = {}
+    # (a) the paper's filter on a dense volume: the 512^3 phantom with no noise
+    # threshold, so every voxel passes the gate and the ring kernel does the work
+    ctx = lnf.Context(threshold_mode=lnf.THRESH_NONE)
+    out = torch.empty_like(t_p2)
+    call_ms, kern = timed_calls(ctx, lambda: ctx.filter_volume(t_p2, lnf.OURS, RADIUS, out=out), torch, warmup, steps)
+    kind, kms = ours_kernel(kern)
+    n = t_p2.numel()
+    res["ours_dense_512_u16"] = {
+        "workload": "512^3 uint16 phantom, paper's filter r=2, no noise threshold (every voxel passes)",
+        "call_ms": call_ms, "kernel": kind, "kernel_ms": kms, "gvox_s": n / call_ms / 1e6,
+        "hbm_frac": 2 * n * 2 / (kms / 1e3) / 1e9 / hbm_gbs}
+    ctx.close()
+    del out
+    # (b) the 1024^3 uint8 phantom, the paper's filter at r = 1..4
+    t3 = torch.from_numpy(gen["P3"]).cuda()
+    o3 = torch.empty_like(t3)
+    n3 = t3.numel()
+    ctx = lnf.Context()
+    sweep = {}
+    for r in (1, 2, 3, 4):
+        call_ms, kern = timed_calls(ctx, lambda: ctx.filter_volume(t3, lnf.OURS, r, out=o3), torch, warmup, steps)
+        kind, kms = ours_kernel(kern)
+        sweep[str(r)] = {"call_ms": call_ms, "gvox_s": n3 / call_ms / 1e6, "kernel": kind, "kernel_ms": kms,
+                         "kernel_gvox_s": n3 / kms / 1e6, "hbm_frac": 2 * n3 / (kms / 1e3) / 1e9 / hbm_gbs}
+    T = ctx.params()["threshold"]
+    res["radius_sweep_1024_u8"] = {
+        "workload": "1024^3 uint8 insect-like phantom, paper's filter r = 1..4 (call: statistics, parameters, "
+                    "filter; kernel: the filter kernel alone, 2 bytes per voxel)",
+        "pass_fraction": float(np.count_nonzero(gen["P3"] >= T)) / n3, "radii": sweep}
+    ctx.close()
+    del t3, o3
+    # (c) latency of one call on the 64^3 uint8 phantom: the paper's filter at r=1
+    # and the entropy of input and output, L2 flushed (a 256 MB write) before each
+    t1 = torch.from_numpy(gen["P1"]).cuda()
+    o1 = torch.empty_like(t1)
+    H1 = torch.zeros(2, dtype=torch.float64, device="cuda")
+    flush = torch.empty(64 << 20, dtype=torch.int32, device="cuda")
+    ctx = lnf.Context()
+    for _ in range(warmup):
+        ctx.filter_multi(t1, [lnf.OURS], 1, outs=[o1], H=H1)
+    dev_ms, host_ms = [], []
+    for _ in range(50):
+        flush.add_(1)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        h0 = time.perf_counter()
+        e0.record()
+        ctx.filter_multi(t1, [lnf.OURS], 1, outs=[o1], H=H1)
+        e1.record()
+        torch.cuda.synchronize()
+        host_ms.append((time.perf_counter() - h0) * 1e3)
+        dev_ms.append(e0.elapsed_time(e1))
+    res["p1_latency_64_u8"] = {
+        "workload": "64^3 uint8 ellipsoid phantom, paper's filter r=1 with input and output entropy, "
+                    "one call, L2 flushed before each",
+        "device_ms_p50": float(np.percentile(dev_ms, 50)), "device_ms_p99": float(np.percentile(dev_ms, 99)),
+        "host_ms_p50": float(np.percentile(host_ms, 50)), "calls": len(dev_ms)}
+    ctx.close()
+    del t1, o1, flush
+    torch.cuda.empty_cache()
+    # (d) batched and (e) served
+    b = batched_result(lnf, torch, gen["batch"], gen["specs"], warmup, steps)
+    res["batched"] = {k: b[k] for k in ("workload", "voxels_per_batch", "batched", "per_volume_loop", "speedup")}
+    torch.cuda.empty_cache()
+    res["served"] = served_result(lnf, torch, gen["served"], gen["sizes"], 200.0, 5.0)
+    torch.cuda.empty_cache()
+    return res
 
 
 # ----------------------------------------------------------------------------- GPU arm
@@ -311,6 +470,8 @@ def main():
     ap.add_argument("--dims", type=int, nargs=3, default=None,
                     help="profiling: a smaller phantom of the same workload (nx ny nz); not a bench line")
     ap.add_argument("--no-e2e", action="store_true", help="profiling: skip the host-buffer leg")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the extra configurations (radius sweep, dense, latency, batched, served)")
     ap.add_argument("--clocks-csv", default=None, help="keep the nvidia-smi clock samples in this file")
     ap.add_argument("--record-traffic", default=None, metavar="NCU_CSV",
                     help="write the per-kind DRAM traffic file from an ncu CSV log and exit")
@@ -340,6 +501,11 @@ def main():
         return run_variants(args)
     if args.mode == "spacing":
         return run_spacing(args)
+
+    # the extra workloads' volumes are drawn meanwhile, in processes started before CUDA
+    gen = None
+    if world == 1 and not args.dims and not args.no_extras:
+        gen = start_generation()
 
     import numpy as np
     import torch
@@ -399,6 +565,8 @@ def main():
     ms = max_over_ranks(ms, world, "cuda")
     value = world * 5 * N_VOX / (ms / 1e3) / 1e9
 
+    # the host legs below (end to end, the oracle) run with the generator pool done
+    gen_data = finish_generation(gen) if gen else None
     if args.no_e2e:
         args.e2e_steps = 0
     # end to end through the host-buffer entry point, from pinned host memory
@@ -467,8 +635,14 @@ def main():
         import oracle
         oracle.build()
         threads = os.cpu_count() or 1
-        tcpu, desc = oracle_step_sample(vol, None, max(threads, 4), threads)
-        cpu = {"value": 5 * N_VOX / tcpu / 1e9, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": desc}
+        cpu = cpu_baseline_entry(vol, threads, oracle_step_sample(vol, max(threads, 4), threads))
+
+    extras = None
+    if gen_data is not None:
+        sampler = ClockSampler(local, None)
+        sampler.start()
+        extras = extra_configs(lnf, torch, gen_data, t, pk["hbm_gbs"], args.warmup, 10)
+        extras["clocks"] = sampler.stop()
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -483,6 +657,8 @@ def main():
         "cpu_baseline": cpu, "clocks": clocks,
         "entropy": [float(x) for x in H.cpu().numpy()],
     }
+    if extras is not None:
+        line["extra"] = extras
     print(json.dumps(line))
     ctx.close()
     if world > 1:
@@ -491,18 +667,17 @@ def main():
 
 # ----------------------------------------------------------------------------- delivery forms
 
-def run_batched(args):
-    """64 uneven volumes (96..384 per axis, half uint8 half uint16), the paper's
-    filter at r in {1, 2}: one persistent graph-captured launch (lnf_filter_batch)
-    against the per-volume launch loop (lnf_filter_volume per volume)."""
-    import torch
-    import phantoms
-    import paper_1807_03119_gb300 as lnf
-    from paper_1807_03119_gb300 import builder
-    builder.build()
-    lnf.load()
-    specs = phantoms.batch_volume_specs(64)
-    vols = [torch.from_numpy(phantoms.batch_volume(s)).cuda() for s in specs]
+def served_sizes():
+    """Side lengths of the eight resident volumes of the served workload."""
+    import numpy as np
+    return [int(np.random.default_rng(2000 + i).integers(128, 769)) for i in range(8)]
+
+
+def batched_result(lnf, torch, host_vols, specs, warmup, steps):
+    """64 uneven volumes, the paper's filter at each spec's radius: one
+    persistent graph-captured launch (lnf_filter_batch) against the per-volume
+    launch loop (lnf_filter_volume per volume); CUDA-event ms per batch."""
+    vols = [torch.from_numpy(v).cuda() for v in host_vols]
     outs = [torch.empty_like(v) for v in vols]
     nvox = sum(v.numel() for v in vols)
     ctx = lnf.Context(autotune=True)
@@ -516,47 +691,54 @@ def run_batched(args):
             ctx.filter_volume(v, lnf.OURS, s["radius"], out=o)
 
     res = {}
-    for name, fn in (("batched", batched), ("loop", loop)):
-        for _ in range(args.warmup):
+    for name, fn in (("batched", batched), ("per_volume_loop", loop)):
+        for _ in range(warmup):
             fn()
         torch.cuda.synchronize()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record()
-        for _ in range(args.steps):
+        for _ in range(steps):
             fn()
         e1.record()
         torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1) / args.steps
+        ms = e0.elapsed_time(e1) / steps
         res[name] = {"ms_per_batch": ms, "gvox_s": nvox / (ms / 1e3) / 1e9}
-    line = {"metric": "batched vs per-volume loop, GVoxel/s", "mode": "batched",
-            "value": res["batched"]["gvox_s"], "unit": UNIT, "n_gpus": 1, "steps": args.steps,
-            "warmup": args.warmup, "higher_is_better": True, "dtype": "u8+u16", "data": "synthetic",
-            "config": {"workload": "64 uneven volumes 96..384 per axis, half uint8 half uint16, paper's filter r in {1,2}",
-                       "voxels_per_batch": nvox},
-            "batched": res["batched"], "per_volume_loop": res["loop"],
-            "speedup": res["loop"]["ms_per_batch"] / res["batched"]["ms_per_batch"]}
-    print(json.dumps(line))
     ctx.close()
+    res["speedup"] = res["per_volume_loop"]["ms_per_batch"] / res["batched"]["ms_per_batch"]
+    res["voxels_per_batch"] = nvox
+    res["workload"] = "64 uneven volumes 96..384 per axis, half uint8 half uint16, paper's filter r in {1,2}"
+    return res
 
 
-def run_served(args):
-    """8 resident uint16 volumes (128..768 per side), a Poisson request stream
-    (args.rate per second) of full-volume or ROI requests with random filter and
-    r in {1,2,3}, admitted under a 40 GiB budget: p50/p99 latency and throughput,
-    against serial plain calls on the same requests."""
-    import numpy as np
+def run_batched(args):
+    """The batched workload on its own line."""
     import torch
     import phantoms
     import paper_1807_03119_gb300 as lnf
     from paper_1807_03119_gb300 import builder
     builder.build()
     lnf.load()
-    sizes = [int(np.random.default_rng(2000 + i).integers(128, 769)) for i in range(8)]
-    vols = [phantoms.insect_phantom((n, n, n), 2000 + i, "u16") for i, n in enumerate(sizes)]
+    specs = phantoms.batch_volume_specs(64)
+    res = batched_result(lnf, torch, [phantoms.batch_volume(s) for s in specs], specs, args.warmup, args.steps)
+    line = {"metric": "batched vs per-volume loop, GVoxel/s", "mode": "batched",
+            "value": res["batched"]["gvox_s"], "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "higher_is_better": True, "dtype": "u8+u16", "data": "synthetic",
+            "config": {"workload": res["workload"], "voxels_per_batch": res["voxels_per_batch"]},
+            "batched": res["batched"], "per_volume_loop": res["per_volume_loop"], "speedup": res["speedup"]}
+    print(json.dumps(line))
+
+
+def served_result(lnf, torch, host_vols, sizes, rate, duration):
+    """8 resident uint16 volumes, a Poisson request stream (`rate` per second for
+    `duration` s) of full-volume or ROI requests with random filter and r in
+    {1,2,3}, admitted under a 40 GiB budget: p50/p99 latency at that load, the
+    capacity with every request queued at once, and serial plain calls on the
+    same requests."""
+    import numpy as np
     rng = np.random.default_rng(42)
-    n_req = int(args.rate * args.duration)
-    gaps = rng.exponential(1.0 / args.rate, n_req)
+    n_req = int(rate * duration)
+    gaps = rng.exponential(1.0 / rate, n_req)
     reqs = []
     for k in range(n_req):
         vi = int(rng.integers(0, 8))
@@ -570,13 +752,14 @@ def run_served(args):
             o = [int(rng.integers(0, n - d[a] + 1)) for a in range(3)]
             reqs.append((vi, f, r, (o, d)))
     ctx = lnf.Context(hbm_budget_bytes=40 << 30, max_inflight=64)
-    ids = [ctx.register_volume(torch.from_numpy(v).cuda()) for v in vols]
+    ids = [ctx.register_volume(torch.from_numpy(v).cuda()) for v in host_vols]
     now = ctx.lib.lnf_now
     # warm-up: one request per filter
     for f in range(5):
         t = ctx.submit(ids[0], f, 1)
         ctx.wait(t)
         ctx.release(t)
+
     def voxels(req):
         vi, f, r, roi = req
         return int(np.prod(roi[1])) if roi else sizes[vi] ** 3
@@ -602,7 +785,7 @@ def run_served(args):
             ctx.release(tk)
         return t_last
 
-    # (1) latency at the stated load: Poisson arrivals at args.rate per second
+    # (1) latency at the stated load: Poisson arrivals at `rate` per second
     pending, lat = [], []
     t0 = now()
     t_next = t0
@@ -624,7 +807,7 @@ def run_served(args):
         pending.append((submit(k, t1), t1))
     served_s = drain(pending, lat_sat, True) - t1
     # serial plain calls on the same requests (device buffers, one sync per request)
-    dvols = [torch.from_numpy(v).cuda() for v in vols]
+    dvols = [torch.from_numpy(v).cuda() for v in host_vols]
     torch.cuda.synchronize()
     ts = time.perf_counter()
     for vi, f, r, roi in reqs:
@@ -635,21 +818,37 @@ def run_served(args):
         torch.cuda.synchronize()
         del o
     serial_s = time.perf_counter() - ts
-    line = {"metric": "served p50/p99 ms and GVoxel/s vs serial plain calls", "mode": "served",
-            "value": vox / served_s / 1e9, "unit": UNIT, "n_gpus": 1, "higher_is_better": True,
-            "dtype": "u16", "data": "synthetic",
-            "config": {"workload": "8 resident uint16 volumes 128..768 per side, Poisson arrivals, "
-                                   "half full-volume half ROI 32..256, random filter, r in {1,2,3}, 40 GiB budget",
-                       "rate_per_s": args.rate, "duration_s": args.duration, "requests": n_req, "sizes": sizes},
+    ctx.close()
+    return {"workload": "8 resident uint16 volumes 128..768 per side, Poisson arrivals, half full-volume half "
+                        "ROI 32..256, random filter, r in {1,2,3}, 40 GiB budget",
+            "rate_per_s": rate, "duration_s": duration, "requests": n_req, "sizes": sizes,
             "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
-                           "max": float(lat.max()), "at_rate_per_s": args.rate,
-                           "seconds_to_last_result": load_s},
+                           "max": float(lat.max()), "at_rate_per_s": rate, "seconds_to_last_result": load_s},
             "served": {"seconds": served_s, "gvox_s": vox / served_s / 1e9,
                        "note": "all requests queued at once (capacity)"},
             "serial_plain": {"seconds": serial_s, "gvox_s": vox / serial_s / 1e9},
-            "offered_gvox_s": vox / args.duration / 1e9}
+            "offered_gvox_s": vox / duration / 1e9}
+
+
+def run_served(args):
+    """The served workload on its own line."""
+    import torch
+    import phantoms
+    import paper_1807_03119_gb300 as lnf
+    from paper_1807_03119_gb300 import builder
+    builder.build()
+    lnf.load()
+    sizes = served_sizes()
+    vols = [phantoms.insect_phantom((n, n, n), 2000 + i, "u16") for i, n in enumerate(sizes)]
+    res = served_result(lnf, torch, vols, sizes, args.rate, args.duration)
+    line = {"metric": "served p50/p99 ms and GVoxel/s vs serial plain calls", "mode": "served",
+            "value": res["served"]["gvox_s"], "unit": UNIT, "n_gpus": 1, "higher_is_better": True,
+            "dtype": "u16", "data": "synthetic",
+            "config": {"workload": res["workload"], "rate_per_s": args.rate, "duration_s": args.duration,
+                       "requests": res["requests"], "sizes": sizes},
+            "latency_ms": res["latency_ms"], "served": res["served"], "serial_plain": res["serial_plain"],
+            "offered_gvox_s": res["offered_gvox_s"]}
     print(json.dumps(line))
-    ctx.close()
 
 
 def run_render(args):

@@ -4,10 +4,12 @@
 // budget, statistics and parameters computed once on the device).  lnf_submit
 // queues a request and returns a ticket.  A scheduler thread admits queued
 // requests in arrival order while in-flight slots and budget allow, groups
-// what it admitted into a "wave" and launches the wave at once as one
-// persistent batched launch (filter.cu) on the next of several streams, so
-// waves overlap on the device while later requests keep arriving; it never
-// waits for a running wave before admitting more.  A host function enqueued
+// what it admitted into a "wave" and enqueues the wave on the next of several
+// streams: one filter launch per request, each sized for its own filter,
+// radius and region (the specialised kernel where it covers the request, else
+// the generic one), then one entropy launch for the whole wave.  Waves overlap
+// on the device while later requests keep arriving; the scheduler never waits
+// for a running wave before admitting more.  A host function enqueued
 // after each wave stamps its finish time and wakes the scheduler, which
 // retires the wave's requests and frees their memory.  No device code waits
 // on the host or on another kernel.
