@@ -11,8 +11,10 @@ What lives where:
     nine-cluster filter Eq. 2-3), and the grey-level statistics;
   * this module -- the scalar parameter derivations in exact Python integer
     arithmetic: the Otsu threshold (Eq. 1), the sigma band, the Okada
-    difference threshold, the entropy-filter weights and threshold, and the
-    image entropy measure the paper uses to compare filters (Fig. 4).
+    difference threshold, the entropy-filter weights and threshold, the
+    fixed-point table and threshold of the entropy filter with the cube's own
+    grey-level probabilities ("Related Work"), and the image entropy measure
+    the paper uses to compare filters (Fig. 4).
 
 Parity status: every function here is pinned by the ``-m "not gpu"`` tests in
 ``tests/test_oracle_*.py`` except the paper's printed fly-data numbers (T=101,
@@ -35,7 +37,7 @@ __all__ = [
     "log2_fixed", "entropy_weights", "entropy_te_default", "derive_params", "filter_volume",
     "filter_points", "image_entropy", "histogram", "MEAN", "SIGMA", "ENTROPY", "OKADA", "OURS",
     "FILTER_NAMES", "LOG2_FRAC_BITS", "ENTROPY_W_BITS", "spacing_radii", "quantize_f32", "dequantize_f32",
-    "filter_volume_f32",
+    "filter_volume_f32", "local_entropy_table", "local_entropy_te_default", "ENTROPY_LOCAL",
 ]
 
 MEAN, SIGMA, ENTROPY, OKADA, OURS = 0, 1, 2, 3, 4
@@ -44,6 +46,8 @@ MEAN, SIGMA, ENTROPY, OKADA, OURS = 0, 1, 2, 3, 4
 OURS_CROSS7, OURS_CUBE = 5, 6
 # the sigma filter with the local standard deviation of its cube (Lee's original form)
 SIGMA_LOCAL = 7
+# the entropy filter with the grey-level probabilities of its own cube
+ENTROPY_LOCAL = 8
 FILTER_NAMES = {MEAN: "mean", SIGMA: "sigma", ENTROPY: "entropy", OKADA: "okada", OURS: "ours"}
 
 # fixed point of the entropy-filter criterion (a stated reading: the paper gives
@@ -85,6 +89,8 @@ class _Params(ctypes.Structure):
         ("aniso", ctypes.c_int32),
         ("rad", ctypes.c_int32 * 3),
         ("off", ctypes.c_int32 * 3),
+        ("entropy_lt", ctypes.POINTER(ctypes.c_uint64)),
+        ("entropy_lte", ctypes.c_int64),
     ]
 
 
@@ -262,19 +268,54 @@ def entropy_te_default(hist, w, m):
     return (m * tot) // N
 
 
+def local_entropy_table(m):
+    """Fixed point of the local entropy filter (a reading: the paper states the
+    kernel's entropy in real numbers only): t[c] = round(2^22 c log2 c) for
+    c = 0..m, computed as floor((c lg c + 2^(F-23)) / 2^(F-22)) with lg the
+    fixed-point log2 above (F fractional bits); t[0] = t[1] = 0.  With c_g the
+    number of cube voxels at grey level g, the cube's first order entropy is
+    H = log2 m - (1/m) sum_g c_g log2 c_g, and m 2^22 H is t[m] - sum_g t[c_g]."""
+    F, W = LOG2_FRAC_BITS, ENTROPY_W_BITS
+    t = np.zeros(m + 1, np.uint64)
+    for c in range(2, m + 1):
+        t[c] = (c * log2_fixed(c) + (1 << (F - W - 1))) >> (F - W)
+    return t
+
+
+_local_tables = {}
+
+
+def _local_table(m):
+    """local_entropy_table(m), kept per m (read-only)."""
+    with _lock:
+        t = _local_tables.get(m)
+        if t is None:
+            t = _local_tables[m] = local_entropy_table(m)
+            t.flags.writeable = False
+        return t
+
+
+def local_entropy_te_default(t, m):
+    """Default threshold theta of the local entropy filter, in 2^-22 bits (a
+    reading: the paper gives no value): half the largest entropy a cube of m
+    voxels can have, log2(m) / 2, as floor(t[m] / (2 m))."""
+    return int(t[m]) // (2 * m)
+
+
 # --------------------------------------------------------------------------- params
 
 class Config:
     """Filter configuration.  threshold_mode: 'otsu' (default), 'fixed' or 'none'."""
 
     def __init__(self, threshold_mode="otsu", threshold_value=0, sigma_k=2, okada_td=None,
-                 entropy_te=None, offset=1):
+                 entropy_te=None, offset=1, entropy_local_te=None):
         self.threshold_mode = threshold_mode
         self.threshold_value = threshold_value
         self.sigma_k = sigma_k
         self.okada_td = okada_td        # None -> floor(sigma) + 1
         self.entropy_te = entropy_te    # None -> expectation; -1 -> pass-all
         self.offset = offset
+        self.entropy_local_te = entropy_local_te   # None -> log2(m)/2; -1 -> pass-all
 
 
 def _axes(v):
@@ -319,8 +360,11 @@ def derive_params(st, radius, cfg=None):
     td = okada_td_default(st.N, st.S, st.Q) if cfg.okada_td is None else int(cfg.okada_td)
     w = entropy_weights(st.hist)
     te = entropy_te_default(st.hist, w, m) if cfg.entropy_te is None else int(cfg.entropy_te)
+    # the local entropy filter's threshold: None = the default of the cube the
+    # filter runs with (local_entropy_te_default), else the configured value
+    lte = None if cfg.entropy_local_te is None else int(cfg.entropy_local_te)
     return {"T": T, "delta": delta, "td": td, "w": w, "te": te, "offset": cfg.offset,
-            "radius": radius, "k": int(cfg.sigma_k)}
+            "radius": radius, "k": int(cfg.sigma_k), "lte": lte}
 
 
 def _cparams(filter_id, prm):
@@ -343,7 +387,15 @@ def _cparams(filter_id, prm):
     w = np.ascontiguousarray(prm["w"], dtype=np.uint32)
     p.entropy_w = w.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32))
     p.sigma_k = int(prm.get("k", 2))
-    return p, w
+    # the local entropy filter: the table and the default threshold of this
+    # call's cube
+    rx, ry, rz = _axes(prm["radius"])
+    m = (2 * rx + 1) * (2 * ry + 1) * (2 * rz + 1)
+    lt = _local_table(m)
+    p.entropy_lt = lt.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64))
+    lte = prm.get("lte")
+    p.entropy_lte = local_entropy_te_default(lt, m) if lte is None else int(lte)
+    return p, (w, lt)
 
 
 def filter_volume(vol, filter_id, radius, cfg=None, params=None, roi=None, st=None):

@@ -19,7 +19,9 @@
  * Filter ids follow the order of the paper's Fig. 5: 0 mean, 1 sigma,
  * 2 entropy, 3 Okada, 4 the paper's own filter ("ours"); 5 and 6 are two
  * cluster-layout variants of it (see filter_ours_variant); 7 is the sigma
- * filter with the local standard deviation (see filter_sigma_local).
+ * filter with the local standard deviation (see filter_sigma_local); 8 is the
+ * entropy filter with the cube's own grey-level probabilities (see
+ * filter_entropy_local).
  */
 #include <stdint.h>
 #include <stddef.h>
@@ -40,7 +42,15 @@ typedef struct oracle_params {
     int32_t aniso;
     int32_t rad[3];
     int32_t off[3];
+    /* entropy filter with local probabilities (id 8): entropy_lt[c] =
+     * round(2^22 c log2 c) for c = 0..m (m voxels in the cube), and the
+     * threshold theta in 2^-22 bits: keep P0 iff lt[m] - sum_g lt[c_g] > m theta */
+    const uint64_t *entropy_lt;
+    int64_t entropy_lte;
 } oracle_params;
+
+/* largest cube of the local entropy filter: radius 8 on every axis */
+#define ORACLE_MAX_CUBE (17 * 17 * 17)
 
 typedef struct vol_view {
     const void *data;
@@ -265,6 +275,46 @@ static uint32_t filter_entropy(const vol_view *v, const oracle_params *p, int64_
     return 0;
 }
 
+/* Entropy filter with the cube's own grey-level probabilities ("Related Work":
+ * the information entropy of the kernel, the average uncertainty of its
+ * values).  Of the m = Mx My Mz cube voxels, c_g carry grey level g; the first
+ * order entropy of the cube is
+ *   H = -sum_g (c_g / m) log2 (c_g / m) = log2 m - (1/m) sum_g c_g log2 c_g,
+ * so m 2^22 H = lt[m] - sum_g lt[c_g] in the fixed point of the table lt.
+ * Each level is counted once, at its first tap in enumeration order.  The
+ * voxel keeps P0 iff P0 >= T and m 2^22 H > m theta (strict, like Eq. 7). */
+static uint32_t filter_entropy_local(const vol_view *v, const oracle_params *p, int64_t x, int64_t y, int64_t z)
+{
+    int r[3], d[3];
+    axis_extents(p, r, d);
+    uint32_t vals[ORACLE_MAX_CUBE];
+    int64_t m = 0;
+    for (int k = -r[2]; k <= r[2]; ++k)
+        for (int j = -r[1]; j <= r[1]; ++j)
+            for (int i = -r[0]; i <= r[0]; ++i)
+                vals[m++] = sample(v, x + i, y + j, z + k);
+    uint64_t K = 0;
+    for (int64_t a = 0; a < m; ++a) {
+        int first = 1;
+        for (int64_t b = 0; b < a; ++b)
+            if (vals[b] == vals[a]) {
+                first = 0;
+                break;
+            }
+        if (!first)
+            continue;
+        int64_t c = 0;
+        for (int64_t b = a; b < m; ++b)
+            c += vals[b] == vals[a];
+        K += p->entropy_lt[c];
+    }
+    const int64_t crit = (int64_t)(p->entropy_lt[m] - K);
+    const uint32_t P0 = sample(v, x, y, z);
+    if (P0 < p->threshold)
+        return 0;
+    return crit > m * p->entropy_lte ? P0 : 0;
+}
+
 /* Cluster-layout variants of the paper's filter ("Our Method": the source
  * carries a commented-out S_0 that averages the centre and its six direct
  * neighbours, and the conclusion proposes analysing other cluster layouts).
@@ -321,8 +371,28 @@ static uint32_t filter_at(const vol_view *v, const oracle_params *p, int64_t x, 
     case 5:
     case 6: return filter_ours_variant(v, p, x, y, z);
     case 7: return filter_sigma_local(v, p, x, y, z);
+    case 8: return filter_entropy_local(v, p, x, y, z);
     default: return 0;
     }
+}
+
+/* Filter id and extents in range; the local entropy filter needs its table and
+ * a cube of at most ORACLE_MAX_CUBE voxels. */
+static int params_ok(const oracle_params *p)
+{
+    if (p->filter_id < 0 || p->filter_id > 8 || p->radius < 0)
+        return 0;
+    if (p->aniso)
+        for (int a = 0; a < 3; ++a)
+            if (p->rad[a] < 0 || p->off[a] < 0)
+                return 0;
+    if (p->filter_id == 8) {
+        int r[3], d[3];
+        axis_extents(p, r, d);
+        if (!p->entropy_lt || (int64_t)(2 * r[0] + 1) * (2 * r[1] + 1) * (2 * r[2] + 1) > ORACLE_MAX_CUBE)
+            return 0;
+    }
+    return 1;
 }
 
 /* Filter the box [x0,x1) x [y0,y1) x [z0,z1) of the volume into `out`, which is
@@ -336,12 +406,8 @@ int oracle_filter_box(const void *vol, int64_t nx, int64_t ny, int64_t nz, int d
         return -1;
     if (x0 < 0 || y0 < 0 || z0 < 0 || x1 > nx || y1 > ny || z1 > nz || x1 < x0 || y1 < y0 || z1 < z0)
         return -1;
-    if (p->filter_id < 0 || p->filter_id > 7 || p->radius < 0)
+    if (!params_ok(p))
         return -1;
-    if (p->aniso)
-        for (int a = 0; a < 3; ++a)
-            if (p->rad[a] < 0 || p->off[a] < 0)
-                return -1;
     vol_view v = {vol, nx, ny, nz, dtype};
     int64_t bx = x1 - x0, by = y1 - y0;
     for (int64_t z = z0; z < z1; ++z)
@@ -362,6 +428,8 @@ int oracle_filter_points(const void *vol, int64_t nx, int64_t ny, int64_t nz, in
                          const oracle_params *p, const int64_t *pts, int64_t npts, uint32_t *vals)
 {
     if (!vol || !p || !pts || !vals || nx < 1 || ny < 1 || nz < 1 || (dtype != 0 && dtype != 1))
+        return -1;
+    if (!params_ok(p))
         return -1;
     vol_view v = {vol, nx, ny, nz, dtype};
     for (int64_t i = 0; i < npts; ++i) {
@@ -494,12 +562,8 @@ int oracle_render(const void *vol, int64_t nx, int64_t ny, int64_t nz, int dtype
 {
     if (!vol || !p || !image || !depth || !value || nx < 1 || ny < 1 || nz < 1 || (dtype != 0 && dtype != 1))
         return -1;
-    if (p->filter_id < 0 || p->filter_id > 7 || p->radius < 0)
+    if (!params_ok(p))
         return -1;
-    if (p->aniso)
-        for (int a = 0; a < 3; ++a)
-            if (p->rad[a] < 0 || p->off[a] < 0)
-                return -1;
     int64_t W, H, len;
     if (render_extent(view, nx, ny, nz, &W, &H, &len) != 0)
         return -1;

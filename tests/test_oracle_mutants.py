@@ -1,5 +1,6 @@
 """Plant plausible slips in a copy of the C oracle and check that the pin
-suites (test_oracle_pins.py, test_oracle_aniso.py) reject every one of them.  The mistakes are planted
+suites (test_oracle_pins.py, test_oracle_aniso.py, test_oracle_local_entropy.py)
+reject every one of them.  The mistakes are planted
 on the CPU, in a temporary copy; the oracle in the repository is untouched."""
 import os
 import subprocess
@@ -35,6 +36,12 @@ MUTANTS = {
     "sum_of_squares_slip": ("q += (unsigned __int128)P * P;", "q += (unsigned __int128)P * P + (P > 200);"),
     "mean_gate_dropped": ("if (P0 < p->threshold || B < n * (uint64_t)p->threshold)",
                           "if (B < n * (uint64_t)p->threshold)"),
+    # the entropy filter with local probabilities
+    "local_entropy_ge": ("crit > m * p->entropy_lte", "crit >= m * p->entropy_lte"),
+    "local_entropy_every_tap": ("        if (!first)\n            continue;\n        int64_t c = 0;",
+                                "        int64_t c = 0;"),
+    "local_entropy_no_gate": ("    if (P0 < p->threshold)\n        return 0;\n    return crit > m",
+                              "    return crit > m"),
 }
 
 
@@ -52,6 +59,7 @@ def test_pins_reject_planted_slip(name, tmp_path):
     env = dict(os.environ, LNF_ORACLE_SO=str(so))
     res = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
                           os.path.join(ROOT, "tests", "test_oracle_pins.py"),
-                          os.path.join(ROOT, "tests", "test_oracle_aniso.py")],
+                          os.path.join(ROOT, "tests", "test_oracle_aniso.py"),
+                          os.path.join(ROOT, "tests", "test_oracle_local_entropy.py")],
                          cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
     assert res.returncode != 0, f"planted slip {name} survived the pins:\n{res.stdout[-2000:]}"

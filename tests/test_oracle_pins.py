@@ -562,14 +562,17 @@ def test_symmetry_48(dt):
     vol = phantoms.random_volume((6, 6, 6), 31, dt, p_extreme=0.2)
     st = oracle.stats(vol)
     outs = {}
-    for f in range(8):
-        prm = oracle.derive_params(st, 1)
-        outs[f] = (prm, oracle.filter_volume(vol, f, 1, params=prm))
+    for f in range(10):
+        # 9: the local entropy filter (id 8) on a threshold inside the cubes' range of entropies
+        cfg = oracle.Config(entropy_local_te=int(4.3 * (1 << oracle.ENTROPY_W_BITS))) if f == 9 else None
+        prm = oracle.derive_params(st, 1, cfg)
+        outs[f] = (prm, oracle.filter_volume(vol, min(f, 8), 1, params=prm))
+    assert 0 < np.count_nonzero(outs[9][1]) < np.count_nonzero(outs[8][1])
     for perm, flips in _transforms():
         tv = _apply(vol, perm, flips)
-        for f in range(8):
+        for f in range(10):
             prm, ref = outs[f]
-            got = oracle.filter_volume(tv, f, 1, params=prm)
+            got = oracle.filter_volume(tv, min(f, 8), 1, params=prm)
             assert (got == _apply(ref, perm, flips)).all(), (f, perm, flips)
 
 
