@@ -910,9 +910,10 @@ def run_render(args):
 def run_variants(args):
     """The variants beside the filters they vary, on the 512^3 uint16 phantom at
     r = 2: the cluster-layout variants of the paper's filter (axis-cross and cube
-    clusters) and the sigma filter with the local sigma of its cube; device ms
-    per launch (the variants run on the generic kernel, the paper's filter and
-    the sigma filter on their specialised ones)."""
+    clusters), the sigma filter with the local sigma of its cube and the entropy
+    filter with the grey-level probabilities of its cube; device ms per launch
+    (the variants run on the generic kernel, the paper's filter and the sigma
+    filter on their specialised ones)."""
     import torch
     import phantoms
     import paper_1807_03119_gb300 as lnf
@@ -924,7 +925,7 @@ def run_variants(args):
     out = torch.empty_like(t)
     ctx = lnf.Context()
     res = {}
-    for name in ("ours", "ours_cross", "ours_cube", "sigma", "sigma_local"):
+    for name in ("ours", "ours_cross", "ours_cube", "sigma", "sigma_local", "entropy_local"):
         f = lnf.FILTERS[name]
         for _ in range(args.warmup):
             ctx.filter_volume(t, f, RADIUS, out=out)
@@ -935,34 +936,40 @@ def run_variants(args):
         torch.cuda.synchronize()
         kern, _ = ctx.profile_read()
         ctx.profile(False)
-        n, tot = kern["filter:" + name]
+        # the paper's filter: the kernel that did the work (gate-first or ring)
+        kind = ours_kernel({k: v[1] for k, v in kern.items()})[0] if name == "ours" else "filter:" + name
+        n, tot = kern[kind]
         ms = tot / n
         res[name] = {"ms_per_launch": ms, "gvox_s": N_VOX / (ms / 1e3) / 1e9,
                      "hbm_frac": N_VOX * ES * 2 / (ms / 1e3) / 1e9 / peaks()["hbm_gbs"]}
-    # the gather kernels against the plane-ring kernels on a sparse volume: 12-bit
-    # background noise (400, sigma 30) with 0.1% salt, so about 0.1% of the voxels
-    # pass the gate; the ring context never pairs the gather kernels
+    # the gate-first kernels against the plane-ring kernels alone on a sparse
+    # volume: 12-bit background noise (400, sigma 30) with 0.1% salt, so about
+    # 0.1% of the voxels pass the gate; the paper's filter alone and the five
+    # filters of one multi-filter call
     import numpy as np
     rng = np.random.default_rng(9)
     sv = np.clip(np.rint(rng.normal(400.0, 30.0, vol.shape).astype(np.float32)), 0, 4095).astype(np.uint16)
     sv.reshape(-1)[rng.integers(0, sv.size, sv.size // 1000)] = 4095
     ts = torch.from_numpy(sv).cuda()
-    os.environ["LNF_NO_GATHER"] = "1"
+    os.environ["LNF_NO_GATE"] = "1"
     ring_ctx = lnf.Context()
-    del os.environ["LNF_NO_GATHER"]
+    del os.environ["LNF_NO_GATE"]
+    five = [lnf.FILTERS[n] for n in FILTER_NAMES]
+    outs = [torch.empty_like(ts) for _ in five]
+    calls = {"ours": lambda c: c.filter_volume(ts, lnf.OURS, RADIUS, out=out),
+             "five_filters": lambda c: c.filter_multi(ts, five, RADIUS, outs=outs)}
     sparse = {}
-    for name in FILTER_NAMES:
-        f = lnf.FILTERS[name]
+    for name, call in calls.items():
         row = {}
-        for label, c in (("gather", ctx), ("ring", ring_ctx)):
+        for label, c in (("gate", ctx), ("ring", ring_ctx)):
             for _ in range(args.warmup):
-                c.filter_volume(ts, f, RADIUS, out=out)
+                call(c)
             torch.cuda.synchronize()
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record()
             for _ in range(args.steps):
-                c.filter_volume(ts, f, RADIUS, out=out)
+                call(c)
             e1.record()
             torch.cuda.synchronize()
             row[label + "_ms_per_call"] = e0.elapsed_time(e1) / args.steps
@@ -970,12 +977,13 @@ def run_variants(args):
     sparse["passing_fraction"] = float(np.count_nonzero(sv >= ctx.params()["threshold"]) / sv.size)
     del sv
     ring_ctx.close()
-    line = {"metric": "filter variants (cluster layouts, local sigma), 512^3 uint16, r=2", "mode": "variants",
+    line = {"metric": "filter variants (cluster layouts, local sigma, local entropy), 512^3 uint16, r=2",
+            "mode": "variants",
             "value": res["ours_cube"]["gvox_s"], "unit": UNIT, "higher_is_better": True, "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "dtype": "u16", "data": "synthetic",
             "config": {"workload": WORKLOAD, "radius": RADIUS,
                        "sparse_workload": "512^3 uint16, noise 400 +- 30 with 0.1% salt at 4095"},
-            "filters": res, "sparse_gather_vs_ring": sparse}
+            "filters": res, "sparse_gate_vs_ring": sparse}
     print(json.dumps(line))
     ctx.close()
 

@@ -75,8 +75,12 @@ typedef enum lnf_filter_id {
        cluster centres and combination, each cluster being */
     LNF_OURS_CROSS7 = 5,  /* its centre and axis cross of arm r, averaged (r = 1: (P0 + 6 neighbours) / 7) */
     LNF_OURS_CUBE = 6,    /* the M^3 cube around its centre, averaged */
-    LNF_SIGMA_LOCAL = 7   /* Eq. 5 with the local sigma of the M^3 cube (Lee's original, "Related Work"):
+    LNF_SIGMA_LOCAL = 7,  /* Eq. 5 with the local sigma of the M^3 cube (Lee's original, "Related Work"):
                              |P_i - P0| <= k sigma_cube, k = sigma_k */
+    LNF_ENTROPY_LOCAL = 8 /* entropy filter with the cube's own grey-level probabilities (the kernel
+                             entropy of "Related Work"): with c_g cube voxels at level g, keep P0 iff
+                             P0 >= T and t[m] - sum_g t[c_g] > m theta, t[c] = round(2^22 c log2 c)
+                             (40-bit repeated-squaring log2), theta = entropy_local_te_q */
 } lnf_filter_id;
 
 typedef enum lnf_threshold_mode {
@@ -103,6 +107,8 @@ typedef struct lnf_config {
     int64_t entropy_te_q;       /* T_e in weight units (>= 0), LNF_TE_AUTO or LNF_TE_PASS_ALL */
     int32_t cluster_offset;     /* d of the diagonal clusters (paper: 1, distance sqrt(3)); 0..8 */
     int32_t autotune;           /* 1: pick tile shapes by measurement on first use */
+    int64_t entropy_local_te_q; /* theta of LNF_ENTROPY_LOCAL in 2^-22 bits (>= 0), LNF_TE_AUTO
+                                   (log2(m) / 2: floor(t[m] / 2m)) or LNF_TE_PASS_ALL */
 } lnf_config;
 
 /* Parameters derived from a volume's statistics (read back by lnf_get_params). */

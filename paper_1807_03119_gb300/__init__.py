@@ -15,7 +15,7 @@ import os
 import threading
 
 __all__ = [
-    "MEAN", "SIGMA", "ENTROPY", "OKADA", "OURS", "OURS_CROSS7", "OURS_CUBE", "FILTERS", "THRESH_OTSU", "THRESH_FIXED", "THRESH_NONE",
+    "MEAN", "SIGMA", "ENTROPY", "OKADA", "OURS", "OURS_CROSS7", "OURS_CUBE", "SIGMA_LOCAL", "ENTROPY_LOCAL", "FILTERS", "THRESH_OTSU", "THRESH_FIXED", "THRESH_NONE",
     "TD_AUTO", "TE_AUTO", "TE_PASS_ALL", "LnfError", "load", "build", "Context", "Config", "Job", "Request",
     "Result", "Params", "spacing_radii",
 ]
@@ -23,8 +23,10 @@ __all__ = [
 MEAN, SIGMA, ENTROPY, OKADA, OURS = 0, 1, 2, 3, 4
 OURS_CROSS7, OURS_CUBE = 5, 6   # cluster-layout variants of the paper's filter
 SIGMA_LOCAL = 7                 # the sigma filter with the local sigma of its cube
+ENTROPY_LOCAL = 8               # the entropy filter with the grey-level probabilities of its cube
 FILTERS = {"mean": MEAN, "sigma": SIGMA, "entropy": ENTROPY, "okada": OKADA, "ours": OURS,
-           "ours_cross": OURS_CROSS7, "ours_cube": OURS_CUBE, "sigma_local": SIGMA_LOCAL}
+           "ours_cross": OURS_CROSS7, "ours_cube": OURS_CUBE, "sigma_local": SIGMA_LOCAL,
+           "entropy_local": ENTROPY_LOCAL}
 THRESH_OTSU, THRESH_FIXED, THRESH_NONE = 0, 1, 2
 TD_AUTO, TE_AUTO, TE_PASS_ALL = -1, -2, -1
 STATUS = {0: "LNF_OK", 1: "LNF_EINVAL", 2: "LNF_ENOMEM", 3: "LNF_EBUDGET", 4: "LNF_EPENDING",
@@ -55,6 +57,7 @@ class Config(ctypes.Structure):
         ("entropy_te_q", ctypes.c_int64),
         ("cluster_offset", ctypes.c_int32),
         ("autotune", ctypes.c_int32),
+        ("entropy_local_te_q", ctypes.c_int64),
     ]
 
 
@@ -245,7 +248,7 @@ class Context:
 
     def __init__(self, threshold_mode=THRESH_OTSU, threshold_value=0, sigma_k=2, okada_td=TD_AUTO,
                  entropy_te=TE_AUTO, cluster_offset=1, autotune=False, hbm_budget_bytes=0,
-                 max_inflight=0, stream=None):
+                 max_inflight=0, stream=None, entropy_local_te=TE_AUTO):
         self.lib = load()
         cfg = Config()
         self.lib.lnf_config_default(ctypes.byref(cfg))
@@ -255,6 +258,7 @@ class Context:
         cfg.okada_td = okada_td
         cfg.entropy_te_q = entropy_te
         cfg.cluster_offset = cluster_offset
+        cfg.entropy_local_te_q = entropy_local_te
         cfg.autotune = 1 if autotune else 0
         if hbm_budget_bytes:
             cfg.hbm_budget_bytes = hbm_budget_bytes

@@ -96,8 +96,8 @@ bool lnf_fault_parse(const char *spec, FaultPlan &plan)
 
 static lnf_status check_filter(lnf_ctx *ctx, int filter_id, int radius)
 {
-    if (filter_id < LNF_MEAN || filter_id > LNF_SIGMA_LOCAL)
-        return lnf_fail(ctx, LNF_EINVAL, "filter_id %d not in 0..7", filter_id);
+    if (filter_id < LNF_MEAN || filter_id > LNF_ENTROPY_LOCAL)
+        return lnf_fail(ctx, LNF_EINVAL, "filter_id %d not in 0..8", filter_id);
     if (radius < 0 || radius > LNF_MAX_RADIUS)
         return lnf_fail(ctx, LNF_EINVAL, "radius %d not in 0..%d", radius, LNF_MAX_RADIUS);
     return LNF_OK;
@@ -130,10 +130,12 @@ extern "C" void lnf_config_default(lnf_config *cfg)
     cfg->entropy_te_q = LNF_TE_AUTO;
     cfg->cluster_offset = 1;
     cfg->autotune = 0;
+    cfg->entropy_local_te_q = LNF_TE_AUTO;
 }
 
-ParamCfg lnf_param_cfg(const lnf_config &c)
+ParamCfg lnf_param_cfg(const lnf_ctx *ctx)
 {
+    const lnf_config &c = ctx->cfg;
     ParamCfg p;
     std::memset(&p, 0, sizeof p);
     p.threshold_mode = c.threshold_mode;
@@ -141,6 +143,8 @@ ParamCfg lnf_param_cfg(const lnf_config &c)
     p.sigma_k = c.sigma_k;
     p.okada_td = c.okada_td;
     p.entropy_te = c.entropy_te_q;
+    p.entropy_local_te = c.entropy_local_te_q;
+    p.lt = ctx->d_lt;
     return p;
 }
 
@@ -197,7 +201,7 @@ extern "C" lnf_status lnf_create(const lnf_config *cfg_in, lnf_ctx **out)
         lnf_config_default(&cfg);
     if (cfg.threshold_mode < 0 || cfg.threshold_mode > 2 || cfg.sigma_k < 0 || cfg.sigma_k > 255 ||
         cfg.cluster_offset < 0 || cfg.cluster_offset > 8 || cfg.okada_td < LNF_TD_AUTO ||
-        cfg.entropy_te_q < LNF_TE_AUTO)
+        cfg.entropy_te_q < LNF_TE_AUTO || cfg.entropy_local_te_q < LNF_TE_AUTO)
         return LNF_EINVAL;
     if (cfg.hbm_budget_bytes == 0)
         cfg.hbm_budget_bytes = 40ull << 30;
@@ -234,6 +238,8 @@ extern "C" lnf_status lnf_create(const lnf_config *cfg_in, lnf_ctx **out)
             s = LNF_ENOMEM;
             break;
         }
+        if ((s = lnf_lt_upload(ctx)) != LNF_OK)
+            break;
         cudaMemset(ctx->d_err, 0, sizeof(u32));
         cudaMemset(ctx->d_counter, 0, sizeof(u32) * 16);
         cudaMemset(ctx->d_ent_done, 0, sizeof(u32) * LNF_MAX_ENT);
@@ -283,6 +289,7 @@ extern "C" void lnf_destroy(lnf_ctx *ctx)
     cudaFree(ctx->pitched);
     cudaFree(ctx->f32_lv);
     cudaFree(ctx->d_range);
+    cudaFree(ctx->d_lt);
     for (cudaEvent_t e : ctx->filter_done)
         cudaEventDestroy(e);
     if (ctx->copy_stream)
@@ -404,8 +411,9 @@ extern "C" lnf_status lnf_profile_read(lnf_ctx *ctx, lnf_kernel_time *out, int m
 static const char *filter_name(int f)
 {
     static const char *names[] = {"filter:mean", "filter:sigma", "filter:entropy", "filter:okada",
-                                  "filter:ours", "filter:ours_cross", "filter:ours_cube", "filter:sigma_local"};
-    return f >= 0 && f <= 7 ? names[f] : "filter:?";
+                                  "filter:ours", "filter:ours_cross", "filter:ours_cube", "filter:sigma_local",
+                                  "filter:entropy_local"};
+    return f >= 0 && f <= 8 ? names[f] : "filter:?";
 }
 
 // ------------------------------------------------------------------ device steps
@@ -422,7 +430,7 @@ lnf_status lnf_analyze(lnf_ctx *ctx, const void *in, const int64_t dims[3], int 
     CK(lnf_launch_stats(in, n, dtype, vs.hist, ctx->num_sms, stream));
     lnf_prof_end(ctx, rec, "stats", stream, 1);
     rec = lnf_prof_begin(ctx, stream);
-    CK(lnf_launch_params(vs.hist, vs.st, lnf_param_cfg(ctx->cfg), vs.prm, vs.lut, vs.pscr, dtype, stream));
+    CK(lnf_launch_params(vs.hist, vs.st, lnf_param_cfg(ctx), vs.prm, vs.lut, vs.pscr, dtype, stream));
     lnf_prof_end(ctx, rec, "params", stream, 1);
     return LNF_OK;
 }

@@ -110,7 +110,7 @@ static lnf_status check_job(lnf_ctx *ctx, const lnf_job &j, int i)
     lnf_status s = lnf_check_volume(ctx, j.in, j.dims, j.dtype);
     if (s != LNF_OK)
         return s;
-    if (j.filter_id < LNF_MEAN || j.filter_id > LNF_SIGMA_LOCAL || j.radius < 0 || j.radius > LNF_MAX_RADIUS)
+    if (j.filter_id < LNF_MEAN || j.filter_id > LNF_ENTROPY_LOCAL || j.radius < 0 || j.radius > LNF_MAX_RADIUS)
         return lnf_fail(ctx, LNF_EINVAL, "job %d: filter %d / radius %d out of range", i, j.filter_id, j.radius);
     if (!j.out)
         return lnf_fail(ctx, LNF_EINVAL, "job %d: null output", i);
@@ -159,7 +159,7 @@ lnf_status lnf_enqueue_batch(lnf_ctx *ctx, const lnf_job *jobs, int n, int zchun
     const int per = std::max(1, (2 * ctx->num_sms + sp.n_jobs - 1) / sp.n_jobs);
     CK(lnf_launch_stats_init_batched(sp, st));
     CK(lnf_launch_stats_batched(sp, per, st));
-    CK(lnf_launch_params_batched(sp, lnf_param_cfg(ctx->cfg), st));
+    CK(lnf_launch_params_batched(sp, lnf_param_cfg(ctx), st));
 
     // padded copies of the inputs TMA cannot address
     std::vector<int64_t> pitch(vols.size(), 0);

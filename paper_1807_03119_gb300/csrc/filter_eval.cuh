@@ -26,6 +26,8 @@ struct StepParams {
     long long te;
     int r[3], d[3];     // radius and cluster offset per axis (x, y, z)
     const u32 *lut;
+    const unsigned long long *lt;   // local entropy filter: t[c] = round(2^22 c log2 c)
+    long long lte;                  // ... and its theta (2^-22 bits)
 };
 
 template <class S>
@@ -127,6 +129,38 @@ __device__ __forceinline__ u32 eval_filter(int filter, const S &R, const StepPar
             return 0;
         return rnd_div(s, n);
     }
+    case 8: {   // entropy filter with the box's own grey-level probabilities: with c_g of
+        // the m box voxels at level g, m 2^22 H = t[m] - sum_g t[c_g].  The sum is
+        // taken as the telescoping sum over the taps a of t[k_a] - t[k_a - 1], k_a
+        // the taps up to a (enumeration order) at a's level.  P0 >= T first.
+        if (P0 < p.T)
+            return 0;
+        const int m = (int)box;
+        u64 K = 0;
+        int a = 0;
+        for (int ka = -rz; ka <= rz; ++ka)
+            for (int ja = -ry; ja <= ry; ++ja)
+                for (int ia = -rx; ia <= rx; ++ia, ++a) {
+                    const u32 va = R.at(ia, ja, ka);
+                    // taps b <= a at level va (a itself included)
+                    auto rank = [&]() -> u32 {
+                        u32 k = 0;
+                        int b = 0;
+                        for (int kb = -rz; kb <= rz; ++kb)
+                            for (int jb = -ry; jb <= ry; ++jb)
+                                for (int ib = -rx; ib <= rx; ++ib, ++b) {
+                                    if (b > a)
+                                        return k;
+                                    k += R.at(ib, jb, kb) == va;
+                                }
+                        return k;
+                    };
+                    const u32 k = rank();
+                    K += __ldg(p.lt + k) - __ldg(p.lt + k - 1);
+                }
+        const long long crit = (long long)(__ldg(p.lt + m) - K);
+        return crit > (long long)m * p.lte ? P0 : 0u;
+    }
     case 5:     // cluster-layout variants of the paper's filter: the nine cluster
     case 6: {   // centres of Eq. 2-3, each cluster its axis cross of arms r_a (5) or its box (6)
         u64 U = 0;
@@ -206,6 +240,12 @@ __device__ __forceinline__ StepParams make_step_params3(const DevParams &P, cons
     } else {
         sp.te = P.te_cfg;
     }
+    // the local entropy filter: default theta log2(m) / 2 as floor(t[m] / 2m)
+    sp.lt = P.lt;
+    if (P.lte_cfg == -2)
+        sp.lte = (P.lt && m <= LNF_LT_MAX) ? (long long)(__ldg(P.lt + m) / (2 * m)) : 0;
+    else
+        sp.lte = P.lte_cfg;
     return sp;
 }
 

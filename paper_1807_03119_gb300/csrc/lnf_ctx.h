@@ -81,6 +81,7 @@ struct lnf_ctx {
     u64 *out_hist = nullptr;    // LNF_MAX_PACK output histograms of 65536 bins
     double *d_H = nullptr;
     u32 *d_err = nullptr;
+    unsigned long long *d_lt = nullptr;   // local entropy filter's table, LNF_LT_MAX + 1 entries
     u32 *d_counter = nullptr;   // work counters: [0] generic, [1..4] serving streams (generic),
                                 // [8] paper's filter, [9] comparison filters, [10..13] serving
                                 // streams (specialised), [14] fused kernel, [15] the self-test's status word
@@ -135,7 +136,9 @@ inline bool lnf_fault(lnf_ctx *ctx, FaultSite site)
     return n < 0 || k == n;
 }
 lnf_status lnf_check_volume(lnf_ctx *ctx, const void *p, const int64_t dims[3], int dtype);
-ParamCfg lnf_param_cfg(const lnf_config &c);
+ParamCfg lnf_param_cfg(const lnf_ctx *ctx);
+// the local entropy filter's table t[0..LNF_LT_MAX] to ctx->d_lt (lnf_create)
+lnf_status lnf_lt_upload(lnf_ctx *ctx);
 lnf_status lnf_scratch_pool(lnf_ctx *ctx, size_t n);
 lnf_status lnf_analyze(lnf_ctx *ctx, const void *in, const int64_t dims[3], int dtype, VolScratch &vs,
                        cudaStream_t stream);

@@ -29,6 +29,8 @@ struct ParamCfg {
     int pad;
     long long okada_td;         // >= 0, or -1 = auto
     long long entropy_te;       // >= 0, -1 = pass all, -2 = auto (per radius)
+    long long entropy_local_te; // local entropy filter's theta: >= 0, -1 = pass all, -2 = auto
+    const unsigned long long *lt;   // its table t[c] = round(2^22 c log2 c), c = 0..LNF_LT_MAX
 };
 
 // Parameters derived on the device from the histogram (one per volume).
@@ -46,7 +48,13 @@ struct DevParams {
     u32 sigma_k;                // k of the sigma bands (global: in delta; local: applied per cube)
     u32 pad;
     u64 n_pass;                 // voxels whose own value passes the gate (P0 >= T)
+    long long lte_cfg;          // local entropy filter's theta setting (see ParamCfg)
+    const unsigned long long *lt;   // its table (see ParamCfg)
 };
+
+// Entries of the local entropy filter's table: cubes of up to 17^3 voxels
+// (radius 8 on every axis).
+#define LNF_LT_MAX (17 * 17 * 17)
 
 // Whether the gate-first kernel (gate.cuh) does the work of the filters it is
 // launched for: it streams the volume once and evaluates only the voxels that

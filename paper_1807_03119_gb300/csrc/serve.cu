@@ -548,7 +548,7 @@ extern "C" lnf_status lnf_submit(lnf_ctx *ctx, const lnf_request *req, uint64_t 
     if (st != LNF_OK)
         return st;
     Server *s = ctx->srv;
-    if (req->filter_id < LNF_MEAN || req->filter_id > LNF_SIGMA_LOCAL || req->radius < 0 || req->radius > LNF_MAX_RADIUS)
+    if (req->filter_id < LNF_MEAN || req->filter_id > LNF_ENTROPY_LOCAL || req->radius < 0 || req->radius > LNF_MAX_RADIUS)
         return lnf_fail(ctx, LNF_EINVAL, "request: filter %d / radius %d out of range", req->filter_id, req->radius);
     std::unique_lock<std::mutex> lk(s->mu);
     auto it = s->vols.find(req->vol_id);

@@ -612,6 +612,8 @@ __device__ void chunk_params(const u64 *hist, const DevStats *st, const ParamCfg
     p.sigma_k = (u32)cfg.sigma_k;
     p.pad = 0;
     p.n_pass = sm.hw[0];
+    p.lte_cfg = cfg.entropy_local_te;
+    p.lt = cfg.lt;
     *prm = p;
 }
 
