@@ -445,7 +445,8 @@ def extra_configs(lnf, torch, gen, t_p2, hbm_gbs, warmup, steps):
     torch.cuda.empty_cache()
     # (d) batched and (e) served
     b = batched_result(lnf, torch, gen["batch"], gen["specs"], warmup, steps)
-    res["batched"] = {k: b[k] for k in ("workload", "voxels_per_batch", "batched", "per_volume_loop", "speedup")}
+    res["batched"] = {k: b[k] for k in ("workload", "voxels_per_batch", "batched", "per_volume_loop", "speedup",
+                                        "autotune")}
     torch.cuda.empty_cache()
     res["served"] = served_result(lnf, torch, gen["served"], gen["sizes"], 200.0, 5.0)
     torch.cuda.empty_cache()
@@ -704,6 +705,7 @@ def batched_result(lnf, torch, host_vols, specs, warmup, steps):
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1) / steps
         res[name] = {"ms_per_batch": ms, "gvox_s": nvox / (ms / 1e3) / 1e9}
+    res["autotune"] = ctx.tuning()
     ctx.close()
     res["speedup"] = res["per_volume_loop"]["ms_per_batch"] / res["batched"]["ms_per_batch"]
     res["voxels_per_batch"] = nvox
@@ -725,7 +727,8 @@ def run_batched(args):
             "value": res["batched"]["gvox_s"], "unit": UNIT, "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "higher_is_better": True, "dtype": "u8+u16", "data": "synthetic",
             "config": {"workload": res["workload"], "voxels_per_batch": res["voxels_per_batch"]},
-            "batched": res["batched"], "per_volume_loop": res["per_volume_loop"], "speedup": res["speedup"]}
+            "batched": res["batched"], "per_volume_loop": res["per_volume_loop"], "speedup": res["speedup"],
+            "autotune": res["autotune"]}
     print(json.dumps(line))
 
 

@@ -252,6 +252,24 @@ lnf_status lnf_entropy(lnf_ctx *ctx, const void *vol, const int64_t dims[3], int
  * (256 or 65536 uint32 entries, host memory).  Synchronises the stream.
  */
 lnf_status lnf_get_params(lnf_ctx *ctx, lnf_params *out, uint32_t *weights);
+/* It returns LNF_ETIMEOUT if a kernel's bounded wait gave up since the context
+ * was created, LNF_ECUDA if a debug build's bounds check failed. */
+
+/*
+ * Debug builds.  A library compiled with LNF_DEBUG_CHECKS makes its kernels
+ * check, before each access, the TMA box coordinates (innermost coordinate on a
+ * 16-byte boundary, destination on a 128-byte one), the gate-first kernel's
+ * list, histogram-window and voxel indices and the generic kernel's taps in its
+ * staged planes; a failed check records LNF_DERR_BADJOB in the context's error
+ * word and skips the access.
+ *
+ * lnf_debug_checks: 1 for such a build, else 0.
+ * lnf_debug_poll: debug builds wait for the context's stream and return
+ *   LNF_ECUDA if a check failed since the last poll (the record is cleared);
+ *   release builds return LNF_OK at once.  NULL ctx: LNF_EINVAL.
+ */
+int lnf_debug_checks(void);
+lnf_status lnf_debug_poll(lnf_ctx *ctx);
 
 /*
  * Ray-cast the volume with a filter deciding at each candidate surface point:
@@ -337,15 +355,31 @@ typedef struct lnf_job {
 } lnf_job;
 
 /*
- * Run a batch of jobs (different volumes, sizes, dtypes, filters and radii)
- * as ONE persistent launch over the flattened tile list of all jobs, preceded
- * by one batched statistics launch and one batched parameter launch; the
- * three launches are captured once into a CUDA graph and replayed when the
- * same batch (same pointers and shapes) is run again.  Tile shape and threads
- * per tile come from the autotuner when lnf_config.autotune is set.
- * Enqueued; no host synchronisation.
+ * Run a batch of jobs (different volumes, sizes, dtypes, filters and radii):
+ * one batched statistics launch and one batched parameter launch over the
+ * distinct input volumes, then the jobs a specialised kernel covers as its
+ * launches (a whole volume of the paper's filter also gets the gate-first
+ * kernel, which takes the job on the device while few voxels pass the gate),
+ * and ONE persistent launch of the generic kernel over the flattened tile list
+ * of all other jobs, then one entropy launch.  The sequence is captured once
+ * into a CUDA graph and replayed when the same batch (same pointers and
+ * shapes) is run again.  With lnf_config.autotune set, the first batch times
+ * the candidate z lengths of the specialised kernels' work items per job class
+ * and the generic kernel's z chunk (lnf_get_tuning).  Enqueued; no host
+ * synchronisation (the autotuner's first run synchronises).
  */
 lnf_status lnf_filter_batch(lnf_ctx *ctx, const lnf_job *jobs, int n_jobs);
+
+/*
+ * The autotuner's choices on this context.  For up to `cap` job classes:
+ * classes[k] = (dtype * 16 + filter_id) * 16 + radius, zlen[k] = the chosen z
+ * length (planes) of a specialised work item, and, if ms is not NULL,
+ * ms[4k .. 4k+3] = the class's batch time (ms) with z lengths 4, 8, 16, 32.
+ * *n = the number of tuned classes (may exceed cap); *generic_zchunk (if not
+ * NULL) = the generic kernel's tuned z chunk, 0 if not tuned.  Host arrays.
+ */
+lnf_status lnf_get_tuning(lnf_ctx *ctx, int32_t *classes, int32_t *zlen, float *ms, int cap, int *n,
+                          int32_t *generic_zchunk);
 
 /* ------------------------------------------------------------------ serving */
 

@@ -158,6 +158,11 @@ _SIGS = {
     "lnf_entropy": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, _i64p, ctypes.c_int,
                                    ctypes.POINTER(ctypes.c_double)]),
     "lnf_get_params": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Params), ctypes.c_void_p]),
+    "lnf_debug_checks": (ctypes.c_int, []),
+    "lnf_get_tuning": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
+                                      ctypes.POINTER(ctypes.c_float), ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                      ctypes.POINTER(ctypes.c_int32)]),
+    "lnf_debug_poll": (ctypes.c_int, [ctypes.c_void_p]),
     "lnf_filter_batch": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Job), ctypes.c_int]),
     "lnf_volume_register": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, _i64p,
                                            ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
@@ -183,11 +188,13 @@ def build(verbose=False, force=False):
 
 
 def load(path=None):
-    """Load liblnf.so and declare its C signatures.  Raises if it is missing."""
+    """Load liblnf.so (or `path`, or the library the environment variable LNF_LIB
+    names, e.g. the bounds-checking liblnf_debug.so) and declare its C
+    signatures.  Raises if it is missing."""
     global _lib
     with _lock:
         if _lib is None:
-            p = path or LIB_PATH
+            p = path or os.environ.get("LNF_LIB") or LIB_PATH
             if not os.path.exists(p):
                 raise ImportError(f"liblnf.so not built at {p}: run paper_1807_03119_gb300.build() first")
             L = ctypes.CDLL(p)
@@ -271,6 +278,7 @@ class Context:
         if rc != OK:
             raise LnfError(rc, "lnf_create failed")
         self.h = h
+        self._debug = bool(self.lib.lnf_debug_checks())
 
     # -- plumbing
     def _stream_handle(self):
@@ -283,6 +291,9 @@ class Context:
         self.lib.lnf_set_stream(self.h, self._stream_handle())
 
     def _check(self, rc):
+        if rc == OK and self._debug:
+            # a bounds-checking build: wait for the call's kernels and report a failed check
+            rc = self.lib.lnf_debug_poll(self.h)
         if rc != OK:
             raise LnfError(rc, (self.lib.lnf_last_error(self.h) or b"").decode())
         return rc
@@ -463,6 +474,24 @@ class Context:
         self._check(self.lib.lnf_filter_batch(self.h, arr, n))
 
     # -- profiling
+    def tuning(self):
+        """The autotuner's choices: {"classes": [{dtype, filter, radius, zlen, ms}],
+        "generic_zchunk": z chunk or 0}."""
+        cap = 64
+        cls = (ctypes.c_int32 * cap)()
+        zl = (ctypes.c_int32 * cap)()
+        ms = (ctypes.c_float * (4 * cap))()
+        n = ctypes.c_int()
+        gz = ctypes.c_int32()
+        self._sync_stream()
+        self._check(self.lib.lnf_get_tuning(self.h, cls, zl, ms, cap, ctypes.byref(n), ctypes.byref(gz)))
+        out = []
+        for k in range(min(n.value, cap)):
+            c = cls[k]
+            out.append({"dtype": "u8" if c // 256 == 0 else "u16", "filter": (c // 16) % 16, "radius": c % 16,
+                        "zlen": zl[k], "ms": {z: ms[4 * k + q] for q, z in enumerate((4, 8, 16, 32))}})
+        return {"classes": out, "generic_zchunk": gz.value}
+
     def profile(self, on=True):
         self._check(self.lib.lnf_profile_enable(self.h, 1 if on else 0))
 

@@ -2,7 +2,9 @@
 
 Each .cu file is compiled to an object in parallel, then linked into a shared
 library next to this file.  Nothing is rebuilt when every object is newer than
-its sources and the headers.
+its sources and the headers.  build(debug=True) makes liblnf_debug.so, whose
+kernels bound-check their accesses (LNF_DEBUG_CHECKS, see lnf_debug_poll in
+include/lnf.h), from objects of its own.
 """
 import concurrent.futures as cf
 import glob
@@ -17,6 +19,8 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "liblnf.so")
+BUILD_DEBUG = os.path.join(HERE, "_build_debug")
+LIB_DEBUG = os.path.join(HERE, "liblnf_debug.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off",
          "--expt-relaxed-constexpr", "-I", INCLUDE, "-I", CSRC]
@@ -41,21 +45,23 @@ def _stale(target, sources):
     return any(os.path.getmtime(s) > t for s in sources)
 
 
-def build(verbose=False, force=False, jobs=None):
-    os.makedirs(BUILD, exist_ok=True)
+def build(verbose=False, force=False, jobs=None, debug=False):
+    build_dir, lib = (BUILD_DEBUG, LIB_DEBUG) if debug else (BUILD, LIB)
+    extra = ["-DLNF_DEBUG_CHECKS=1"] if debug else []
+    os.makedirs(build_dir, exist_ok=True)
     srcs = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
     deps = _deps()
     objs = []
     todo = []
     for s in srcs:
-        o = os.path.join(BUILD, os.path.basename(s)[:-3] + ".o")
+        o = os.path.join(build_dir, os.path.basename(s)[:-3] + ".o")
         objs.append(o)
         if force or _stale(o, [s] + deps):
             todo.append((s, o))
 
     def compile_one(so):
         s, o = so
-        cmd = [nvcc()] + ARCH + FLAGS + ["-c", s, "-o", o + ".tmp"]
+        cmd = [nvcc()] + ARCH + FLAGS + extra + ["-c", s, "-o", o + ".tmp"]
         if verbose:
             cmd.append("-Xptxas=-v")
         r = subprocess.run(cmd, capture_output=True, text=True)
@@ -69,14 +75,14 @@ def build(verbose=False, force=False, jobs=None):
             for out in ex.map(compile_one, todo):
                 if verbose and out:
                     sys.stderr.write(out)
-    if force or todo or _stale(LIB, objs):
-        tmp = LIB + f".tmp{os.getpid()}"
+    if force or todo or _stale(lib, objs):
+        tmp = lib + f".tmp{os.getpid()}"
         cmd = [nvcc()] + ARCH + ["-shared", "-cudart", "shared", "-o", tmp] + objs
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-        os.replace(tmp, LIB)
-    return LIB
+        os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":

@@ -1005,8 +1005,39 @@ extern "C" lnf_status lnf_get_params(lnf_ctx *ctx, lnf_params *out, uint32_t *we
     out->weight_sum = p.hw_sum;
     out->input_entropy = p.H_in;
     u32 err = 0;
-    if (cudaMemcpy(&err, ctx->d_err, sizeof err, cudaMemcpyDeviceToHost) == cudaSuccess && err)
+    if (cudaMemcpy(&err, ctx->d_err, sizeof err, cudaMemcpyDeviceToHost) == cudaSuccess && err) {
+        if (err & LNF_DERR_BADJOB)
+            return lnf_fail(ctx, LNF_ECUDA, "a debug bounds check failed (code %u)", err);
         return lnf_fail(ctx, LNF_ETIMEOUT, "a bounded device wait gave up (code %u)", err);
+    }
+    return LNF_OK;
+}
+
+extern "C" int lnf_debug_checks(void)
+{
+#ifdef LNF_DEBUG_CHECKS
+    return 1;
+#else
+    return 0;
+#endif
+}
+
+extern "C" lnf_status lnf_debug_poll(lnf_ctx *ctx)
+{
+    if (!ctx)
+        return LNF_EINVAL;
+#ifdef LNF_DEBUG_CHECKS
+    if (cudaStreamSynchronize(ctx->stream) != cudaSuccess)
+        return lnf_fail(ctx, LNF_ECUDA, "debug poll: stream synchronisation failed");
+    u32 err = 0;
+    if (cudaMemcpy(&err, ctx->d_err, sizeof err, cudaMemcpyDeviceToHost) != cudaSuccess)
+        return lnf_fail(ctx, LNF_ECUDA, "debug poll: error word unreadable");
+    if (err & LNF_DERR_BADJOB) {
+        const u32 keep = err & ~LNF_DERR_BADJOB;
+        cudaMemcpy(ctx->d_err, &keep, sizeof keep, cudaMemcpyHostToDevice);
+        return lnf_fail(ctx, LNF_ECUDA, "a debug bounds check failed");
+    }
+#endif
     return LNF_OK;
 }
 

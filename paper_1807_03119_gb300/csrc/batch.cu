@@ -1,11 +1,20 @@
 // Batched delivery: many volumes / ROIs / filters / radii behind one batched
 // statistics launch and one batched parameter launch; jobs a specialised kernel
-// covers run as its launches (inputs TMA cannot address first get one padded
-// copy per volume), all other jobs share ONE persistent launch of the generic
-// kernel over their flattened tile list.  The whole sequence is captured once
-// into a CUDA graph and replayed for the same batch.  An autotuner picks the z
-// chunk of a generic work item (the tile's depth, which sets the halo re-read
-// share and the load balance) by timing the candidates on the first batch it sees.
+// covers run as its launches (a whole volume of the paper's filter also gets
+// the gate-first kernel, which takes the job on the device while few voxels
+// pass the gate; inputs TMA cannot address first get one padded copy per
+// volume), all other jobs share ONE persistent launch of the generic kernel
+// over their flattened tile list.  The whole sequence is captured once into a
+// CUDA graph and replayed for the same batch.
+//
+// The autotuner (lnf_config.autotune) times the candidates on the first batch
+// it sees: for each class of specialised jobs (dtype, filter, radius), the z
+// length of a work item of the plane-ring kernels (planes per item: the halo
+// planes re-read per item against the balance of the persistent grid), timed on
+// that class's jobs alone; then, when the batch has generic jobs, the generic
+// kernel's z chunk.  The choices are kept per context (lnf_get_tuning).  The
+// tile shape and threads per tile of the specialised kernels are compile-time
+// (set by their register and shared-memory budgets), so they are not tuned.
 #include "lnf_ctx.h"
 
 #include <algorithm>
@@ -131,7 +140,20 @@ static lnf_status check_job(lnf_ctx *ctx, const lnf_job &j, int i)
 // histogram zeroing, the padded copies named by `stage` (one per distinct
 // input, null: none), the specialised launches, the persistent generic launch
 // over the remaining jobs and the entropies.
-lnf_status lnf_enqueue_batch(lnf_ctx *ctx, const lnf_job *jobs, int n, int zchunk, cudaStream_t st,
+// the autotuner's job class: dtype, filter, radius
+static int job_class(const lnf_job &j) { return (j.dtype * 16 + j.filter_id) * 16 + j.radius; }
+
+// z length of a specialised work item for job j: the tuned one of its class, the
+// override `zlen` (> 0, used while tuning), else the default
+static int zlen_for(const lnf_ctx *ctx, const lnf_job &j, int zlen)
+{
+    if (zlen > 0)
+        return zlen;
+    auto it = ctx->tuned_zlen.find(job_class(j));
+    return it != ctx->tuned_zlen.end() ? it->second : 16;
+}
+
+lnf_status lnf_enqueue_batch(lnf_ctx *ctx, const lnf_job *jobs, int n, int zchunk, int zlen, cudaStream_t st,
                              std::vector<VolScratch> *scratch_out, const std::vector<void *> *stage)
 {
     // distinct input volumes share one statistics pass
@@ -179,7 +201,7 @@ lnf_status lnf_enqueue_batch(lnf_ctx *ctx, const lnf_job *jobs, int n, int zchun
     int g = 0;   // jobs left to the generic kernel
     EntropyPack ep;
     std::memset(&ep, 0, sizeof ep);
-    const int zsave = ctx->zchunk;
+    const int zsave = ctx->zchunk, lsave = ctx->fast_zlen;
     ctx->zchunk = zchunk;
     for (int i = 0; i < n; ++i) {
         const lnf_job &j = jobs[i];
@@ -202,17 +224,23 @@ lnf_status lnf_enqueue_batch(lnf_ctx *ctx, const lnf_job *jobs, int n, int zchun
                          j.roi_origin, j.roi_dims, ctx->pool[v], oh, staged ? pitch[v] : 0);
         int handled = 0;
         if (s == LNF_OK && fast) {
-            const FilterJob &fj = pk.jobs[g];
-            s = lnf_fast_dispatch(ctx, fj, fj.tmap_idx >= 0 ? &pk.tmaps[fj.tmap_idx] : nullptr, st, &handled);
+            FilterJob &fj = pk.jobs[g];
+            // the gate-first kernel reads the caller's dense volume, not a padded copy
+            fj.orig = j.in;
+            ctx->fast_zlen = zlen_for(ctx, j, zlen);
+            s = lnf_fast_dispatch(ctx, fj, fj.tmap_idx >= 0 ? &pk.tmaps[fj.tmap_idx] : nullptr, st, &handled,
+                                  nullptr, 1);
         }
         if (s != LNF_OK) {
             ctx->zchunk = zsave;
+            ctx->fast_zlen = lsave;
             return s;
         }
         if (!handled)
             ++g;
     }
     ctx->zchunk = zsave;
+    ctx->fast_zlen = lsave;
     pk.n_jobs = g;
     if (g > 0 && (s = lnf_run_pack(ctx, pk, 1, st)) != LNF_OK)
         return s;
@@ -225,8 +253,9 @@ lnf_status lnf_enqueue_batch(lnf_ctx *ctx, const lnf_job *jobs, int n, int zchun
     return LNF_OK;
 }
 
-// time one enqueue of the batch with zchunk `zc` (events on the context stream)
-static float time_batch(lnf_ctx *ctx, const lnf_job *jobs, int n, int zc, const std::vector<void *> *stage)
+// time one enqueue of the batch with zchunk `zc` and specialised z length `zl`
+// (0: the tuned / default one), best of three (events on the context stream)
+static float time_batch(lnf_ctx *ctx, const lnf_job *jobs, int n, int zc, int zl, const std::vector<void *> *stage)
 {
     cudaEvent_t a, b;
     cudaEventCreate(&a);
@@ -234,7 +263,7 @@ static float time_batch(lnf_ctx *ctx, const lnf_job *jobs, int n, int zc, const 
     float best = 1e30f;
     for (int rep = 0; rep < 3; ++rep) {
         cudaEventRecord(a, ctx->stream);
-        if (lnf_enqueue_batch(ctx, jobs, n, zc, ctx->stream, nullptr, stage) != LNF_OK) {
+        if (lnf_enqueue_batch(ctx, jobs, n, zc, zl, ctx->stream, nullptr, stage) != LNF_OK) {
             best = 1e30f;
             break;
         }
@@ -247,6 +276,87 @@ static float time_batch(lnf_ctx *ctx, const lnf_job *jobs, int n, int zc, const 
     cudaEventDestroy(a);
     cudaEventDestroy(b);
     return best;
+}
+
+// The autotuner: per class of specialised jobs not tuned yet, the work items' z
+// length by timing the class's jobs alone; then, once per context and when the
+// batch has jobs the specialised kernels do not cover, the generic z chunk.
+static void autotune(lnf_ctx *ctx, const lnf_job *jobs, int n, const std::vector<void *> &stage)
+{
+    std::map<int, std::vector<int>> classes;   // class -> indices of its specialised jobs
+    bool generic = false;
+    for (int i = 0; i < n; ++i) {
+        if (!ctx->no_fast && lnf_fast_covers(jobs[i].filter_id, jobs[i].radius, ctx->cfg.cluster_offset))
+            classes[job_class(jobs[i])].push_back(i);
+        else
+            generic = true;
+    }
+    std::vector<int> vol_of;
+    distinct_inputs(jobs, n, vol_of);
+    for (auto &c : classes) {
+        if (ctx->tuned_zlen.count(c.first))
+            continue;
+        std::vector<lnf_job> sub;
+        std::vector<void *> sub_stage;   // padded copies, in the class's own order of first use
+        std::vector<int> seen;
+        for (int i : c.second) {
+            sub.push_back(jobs[i]);
+            const int v = vol_of[i];
+            if (std::find(seen.begin(), seen.end(), v) == seen.end()) {
+                seen.push_back(v);
+                sub_stage.push_back(v < (int)stage.size() ? stage[v] : nullptr);
+            }
+        }
+        int best = 16;
+        float best_ms = 1e30f;
+        std::vector<float> times;
+        for (int zl : {4, 8, 16, 32}) {
+            const float ms = time_batch(ctx, sub.data(), (int)sub.size(), ctx->zchunk, zl, &sub_stage);
+            times.push_back(ms);
+            if (ms < best_ms) {
+                best_ms = ms;
+                best = zl;
+            }
+        }
+        ctx->tuned_zlen[c.first] = best;
+        ctx->tuned_zlen_ms[c.first] = times;
+    }
+    if (generic && ctx->tuned_zchunk == 0) {
+        int best_zc = 64;
+        float best_ms = 1e30f;
+        for (int zc : {16, 32, 64, 128}) {
+            const float ms = time_batch(ctx, jobs, n, zc, 0, &stage);
+            if (ms < best_ms) {
+                best_ms = ms;
+                best_zc = zc;
+            }
+        }
+        ctx->tuned_zchunk = best_zc;
+    }
+}
+
+extern "C" lnf_status lnf_get_tuning(lnf_ctx *ctx, int32_t *classes, int32_t *zlen, float *ms, int cap, int *n,
+                                     int32_t *generic_zchunk)
+{
+    if (!ctx || !n || cap < 0 || (cap > 0 && (!classes || !zlen)))
+        return LNF_EINVAL;
+    int k = 0;
+    for (const auto &c : ctx->tuned_zlen) {
+        if (k < cap) {
+            classes[k] = c.first;
+            zlen[k] = c.second;
+            if (ms) {
+                const std::vector<float> &t = ctx->tuned_zlen_ms[c.first];
+                for (int q = 0; q < 4; ++q)
+                    ms[4 * k + q] = q < (int)t.size() ? t[q] : 0.0f;
+            }
+        }
+        ++k;
+    }
+    *n = k;
+    if (generic_zchunk)
+        *generic_zchunk = ctx->tuned_zchunk;
+    return LNF_OK;
 }
 
 extern "C" lnf_status lnf_filter_batch(lnf_ctx *ctx, const lnf_job *jobs, int n_jobs)
@@ -285,19 +395,8 @@ extern "C" lnf_status lnf_filter_batch(lnf_ctx *ctx, const lnf_job *jobs, int n_
         return ss;
     if ((ss = alloc_stage(ctx, jobs, n_jobs, e->stage)) != LNF_OK)
         return ss;
-    // autotune the z chunk once per context
-    if (ctx->cfg.autotune && ctx->tuned_zchunk == 0) {
-        int best_zc = 64;
-        float best_ms = 1e30f;
-        for (int zc : {16, 32, 64, 128}) {
-            float ms = time_batch(ctx, jobs, n_jobs, zc, &e->stage);
-            if (ms < best_ms) {
-                best_ms = ms;
-                best_zc = zc;
-            }
-        }
-        ctx->tuned_zchunk = best_zc;
-    }
+    if (ctx->cfg.autotune)
+        autotune(ctx, jobs, n_jobs, e->stage);
     const int zc = ctx->tuned_zchunk ? ctx->tuned_zchunk : 64;
     e->key.assign(jobs, jobs + n_jobs);
     e->stream = ctx->stream;
@@ -309,7 +408,7 @@ extern "C" lnf_status lnf_filter_batch(lnf_ctx *ctx, const lnf_job *jobs, int n_
         own = true;
     }
     CK(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
-    lnf_status s = lnf_enqueue_batch(ctx, jobs, n_jobs, zc, cap, nullptr, &e->stage);
+    lnf_status s = lnf_enqueue_batch(ctx, jobs, n_jobs, zc, 0, cap, nullptr, &e->stage);
     cudaGraph_t g = nullptr;
     cudaError_t ce = cudaStreamEndCapture(cap, &g);
     if (s != LNF_OK || ce != cudaSuccess) {

@@ -124,7 +124,8 @@ __device__ void box_items(const Args2 &a, const CUtensorMap *tmap, unsigned char
             const int slot = p % G::NP;
             fence_proxy_async_smem();
             mbar_arrive_expect_tx(&bars[slot], pbytes);
-            tma_load_3d(ring + slot * G::PBYTES, tmap, &bars[slot], px0, py0, clampi(z0 - R + p, 0, a.nz - 1));
+            if (lnf_dbg_tma(px0, (int)sizeof(T), ring + slot * G::PBYTES, a.err))
+                tma_load_3d(ring + slot * G::PBYTES, tmap, &bars[slot], px0, py0, clampi(z0 - R + p, 0, a.nz - 1));
         };
         auto prefetch = [&](int p) {   // thread 0 only: plane p into L2
             if (p < nplanes)

@@ -121,10 +121,15 @@ struct Ring {
     int pstride, PW, NP;
     int slot0;          // slot of the plane at dz = 0 for the current step
     int col, row;       // this thread's centre column / row in the plane
+    int PH;             // rows of a plane (debug checks)
+    u32 *err;           // error word (debug checks)
     __device__ __forceinline__ u32 at(int dx, int dy, int dz) const
     {
         int s = slot0 + dz;
         s = s < 0 ? s + NP : (s >= NP ? s - NP : s);
+        // debug builds: the tap inside the staged plane and the ring
+        if (!lnfdev::lnf_dbg_ok(s >= 0 && s < NP && row + dy >= 0 && row + dy < PH && col + dx >= 0 && col + dx < PW, err))
+            return 0;
         return base[s * pstride + (row + dy) * PW + col + dx];
     }
 };
@@ -227,7 +232,8 @@ __device__ void process_item(const FilterJob &J, const CUtensorMap *tmap, int it
             for (int p = 0; p < pre; ++p) {
                 const int z = clampi(z0 - h + p, 0, J.nz - 1);
                 mbar_arrive_expect_tx(&bars[p], plane_bytes);
-                tma_load_3d(ring + (size_t)p * g.pstride, tmap, &bars[p], px0, py0, z);
+                if (lnf_dbg_tma(px0, (int)sizeof(T), ring + (size_t)p * g.pstride, err))
+                    tma_load_3d(ring + (size_t)p * g.pstride, tmap, &bars[p], px0, py0, z);
             }
         }
     } else {
@@ -245,6 +251,8 @@ __device__ void process_item(const FilterJob &J, const CUtensorMap *tmap, int it
     R.NP = g.NP;
     R.col = cx0 + tl;
     R.row = h + tr;
+    R.PH = g.PH;
+    R.err = err;
     T *vout = static_cast<T *>(J.out);
     u64 *gh = J.out_hist;
 
@@ -284,7 +292,8 @@ __device__ void process_item(const FilterJob &J, const CUtensorMap *tmap, int it
                 const int z = clampi(z0 - h + p, 0, J.nz - 1);
                 fence_proxy_async_smem();
                 mbar_arrive_expect_tx(&bars[p % g.NP], plane_bytes);
-                tma_load_3d(ring + (size_t)(p % g.NP) * g.pstride, tmap, &bars[p % g.NP], px0, py0, z);
+                if (lnf_dbg_tma(px0, (int)sizeof(T), ring + (size_t)(p % g.NP) * g.pstride, err))
+                    tma_load_3d(ring + (size_t)(p % g.NP) * g.pstride, tmap, &bars[p % g.NP], px0, py0, z);
             }
         } else {
             const int p = s + 2 * h + 1;

@@ -141,6 +141,7 @@ struct GateArgs {
     const DevParams *prm;
     const u32 *lut;
     u32 *counter;                  // chunk counter, 0 at launch
+    u32 *err;                      // error word (debug builds' bounds checks)
 };
 
 __device__ __forceinline__ int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
@@ -346,6 +347,8 @@ __global__ void __launch_bounds__(kThreadsC, GGeo<T, R, SET>::MINB) k_gate(const
 
     // one listed voxel (linear index i), evaluated by this lane
     auto eval_voxel = [&](u32 i) {
+        if (!lnfdev::lnf_dbg_ok(i < a.n, a.err))
+            return;
         const int z = (int)(i / nxny);
         const u32 rem = i - (u32)z * nxny;
         const int y = (int)(rem / (u32)a.nx);
@@ -369,6 +372,10 @@ __global__ void __launch_bounds__(kThreadsC, GGeo<T, R, SET>::MINB) k_gate(const
                 fv[LNF_ENTROPY] = (long long)sm.E > te ? P0 : 0u;
             }
         };
+        // debug builds: an interior voxel's taps lie within the volume's linear range
+        const u64 reach = (u64)G::H * ((u64)nxny + (u64)a.nx + 1ull);
+        if (inner && !lnfdev::lnf_dbg_ok((u64)i >= reach && (u64)i + reach < a.n, a.err))
+            return;
         if (inner && (lutall || !G::CUBE)) {
             Sums<T, R, SET, true, false> sm;
             sm.run(in, x, y, z, a.nx, a.ny, a.nz, slo, swd, olo, owd, lut_sh, lbase, a.lut);
@@ -392,6 +399,8 @@ __global__ void __launch_bounds__(kThreadsC, GGeo<T, R, SET>::MINB) k_gate(const
                 if (hb < (u32)kHistW) {
                     // 16-bit bins: the add that makes a bin 0x8000 moves 0x8000 to the
                     // global bin, so that no bin passes 0xFFFF
+                    if (!lnfdev::lnf_dbg_ok(oslot<SET>(f) < G::NOUT, a.err))
+                        continue;
                     u32 *wd = &hsh[oslot<SET>(f) * (kHistW / 2) + (hb >> 1)];
                     const u32 sh = 16u * (hb & 1u);
                     const u32 old = atomicAdd(wd, 1u << sh);
@@ -488,18 +497,21 @@ __global__ void __launch_bounds__(kThreadsC, GGeo<T, R, SET>::MINB) k_gate(const
                 const int bit = __ffsll((long long)word) - 1;
                 word &= word - 1ull;
                 const u32 v = c * (u32)G::CVEC + (u32)lane + 32u * (u32)(bit >> 3);
-                L[pos++] = v * 8u + (u32)(bit & 7);
+                if (lnfdev::lnf_dbg_ok(pos < (u32)G::LCAP, a.err))
+                    L[pos] = v * 8u + (u32)(bit & 7);
+                ++pos;
             }
             nlist += __shfl_sync(0xFFFFFFFFu, incl, 31);
             __syncwarp();
         }
         const u32 neval = done ? nlist : (nlist & ~31u);
         for (u32 e = (u32)lane; e < neval; e += 32)
-            eval_voxel(L[e]);
+            if (lnfdev::lnf_dbg_ok(e < (u32)G::LCAP, a.err))
+                eval_voxel(L[e]);
         __syncwarp();
         const u32 rest = nlist - neval;   // at most 31: to the front of the list
         u32 keep = 0;
-        if ((u32)lane < rest)
+        if ((u32)lane < rest && lnfdev::lnf_dbg_ok(neval + lane < (u32)G::LCAP, a.err))
             keep = L[neval + lane];
         __syncwarp();
         if ((u32)lane < rest)
@@ -599,6 +611,7 @@ lnf_status gate_dispatch_t(lnf_ctx *ctx, const FilterJob &j, void *const outs[5]
     a.prm = j.prm;
     a.lut = j.lut;
     a.counter = ctx->d_counter + 14;
+    a.err = ctx->d_err;
     const bool ours = outs[LNF_OURS] != nullptr;
     const bool cube = outs[0] || outs[1] || outs[2] || outs[3];
     lnf_status s;

@@ -107,6 +107,10 @@ struct lnf_ctx {
     std::vector<BatchEntry *> batches;   // owned; freed by lnf_batch_cache_clear
     // autotuner choice for batched launches (0 = not tuned yet)
     int tuned_zchunk = 0;
+    // autotuned z length of the specialised kernels' work items, per job class
+    // (dtype, filter, radius; see batch.cu), and the candidates' times
+    std::map<int, int> tuned_zlen;
+    std::map<int, std::vector<float>> tuned_zlen_ms;
     // profiling: events around launches of the plain path, launch counter
     bool prof = false;
     int64_t prof_launches = 0;

@@ -214,6 +214,31 @@ __device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, u
         : "memory");
 }
 
+// Debug builds (compiled with LNF_DEBUG_CHECKS): kernels check the indexes of
+// the accesses named at each call before making them; a failed check records
+// LNF_DERR_BADJOB in the error word and the access is skipped.  Release builds
+// compile the checks away (both helpers return true).
+__device__ __forceinline__ bool lnf_dbg_ok(bool ok, u32 *err)
+{
+#ifdef LNF_DEBUG_CHECKS
+    if (!ok && err)
+        atomicOr(err, LNF_DERR_BADJOB);
+    return ok;
+#else
+    (void)ok;
+    (void)err;
+    return true;
+#endif
+}
+
+// ... a TMA load: its innermost coordinate starts on a 16-byte boundary (x
+// times the element size; a load left out leaves its mbarrier incomplete, so the
+// kernel's bounded wait ends it) and its destination on a 128-byte one
+__device__ __forceinline__ bool lnf_dbg_tma(int x, int elem_size, const void *dst, u32 *err)
+{
+    return lnf_dbg_ok(((x * elem_size) & 15) == 0 && (smem_u32(dst) & 127u) == 0u, err);
+}
+
 // TMA: prefetch a 3D box of the tensor map into L2 (no shared memory, no
 // completion to wait for); used to keep DRAM reads in flight further ahead
 // than the shared-memory ring allows.

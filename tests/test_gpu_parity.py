@@ -338,7 +338,7 @@ def test_batched_mixed(lnf, autotune):
 def test_invalid_arguments(ctx, lnf):
     t = dev(np.zeros((4, 4, 4), np.uint8))
     with pytest.raises(lnf.LnfError):
-        ctx.filter_volume(t, 8, 1)              # filter ids are 0..7
+        ctx.filter_volume(t, 9, 1)              # filter ids are 0..8
     with pytest.raises(lnf.LnfError):
         ctx.filter_volume(t, 0, 9)
     with pytest.raises(lnf.LnfError):
@@ -369,6 +369,29 @@ def _check_sampled(vol, outs, filters, r, prm, seed):
         assert bad.size == 0, (f, pts[bad[:5]], got[bad[:5]], want[bad[:5]])
 
 
+def _check_slabs(vol, outs, filters, r, prm, planes):
+    """Whole z-planes: every voxel below the noise threshold T must be 0, and
+    every voxel with P0 >= T is checked against the oracle element by element
+    (the planes include the volume's first and last ones, where the clamped
+    taps run)."""
+    T = prm["T"]
+    checked = 0
+    for z in planes:
+        sl = vol[z]
+        ys, xs = np.nonzero(sl >= T)
+        pts = np.stack([xs, ys, np.full_like(xs, z)], axis=1).astype(np.int64)
+        for f, o in zip(filters, outs):
+            assert not o[z][sl < T].any(), (f, z, "nonzero below the gate")
+            if len(pts):
+                want = oracle.filter_points(vol, f, r, pts, prm)
+                got = o[z][ys, xs]
+                bad = np.nonzero(got != want)[0]
+                assert bad.size == 0, (f, z, pts[bad[:5]], got[bad[:5]], want[bad[:5]])
+        checked += len(pts)
+    assert checked > 0
+    return checked
+
+
 def _check_hist_property(out, Hgot):
     # the fused output histogram must be the histogram of the output
     h = np.bincount(out.reshape(-1).astype(np.int64))
@@ -378,7 +401,8 @@ def _check_hist_property(out, Hgot):
 
 def test_full_512_u16_all_filters_r2(ctx):
     """The 512^3 uint16 insect phantom, all five filters at radius 2, entropy of
-    input and outputs, in the launch configuration the benchmark times."""
+    input and outputs, in the launch configuration the benchmark times: 3000
+    random voxels, and every voxel of nine whole z-planes."""
     vol = phantoms.P2()
     st = oracle.stats(vol)
     prm = oracle.derive_params(st, 2)
@@ -390,6 +414,8 @@ def test_full_512_u16_all_filters_r2(ctx):
     assert abs(Hh[0] - oracle.image_entropy(st.hist)) <= H_TOL * Hh[0]
     outs_h = [host(o) for o in outs]
     _check_sampled(vol, outs_h, FILTERS, 2, prm, 5)
+    # whole planes within the reach (3) of both z faces and one in the middle
+    _check_slabs(vol, outs_h, FILTERS, 2, prm, (0, 1, 2, 3, 256, 508, 509, 510, 511))
     for o, h in zip(outs_h, Hh[1:]):
         _check_hist_property(o, h)
 
@@ -403,6 +429,7 @@ def test_full_1024_u8_ours_radius_sweep(ctx):
         outs, H = ctx.filter_multi(t, [oracle.OURS], r)
         o = host(outs[0])
         _check_sampled(vol, [o], [oracle.OURS], r, prm, 10 + r)
+        _check_slabs(vol, [o], [oracle.OURS], r, prm, (0, r + 1, 511, 1022 - r, 1023))
         _check_hist_property(o, float(host(H)[1]))
         del outs, o
         torch.cuda.empty_cache()

@@ -58,8 +58,9 @@ def test_pins_reject_planted_slip(name, tmp_path):
                            "-o", str(so), str(c)])
     env = dict(os.environ, LNF_ORACLE_SO=str(so))
     res = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
+                          # the short local-entropy suite first: -x stops at the first failure
+                          os.path.join(ROOT, "tests", "test_oracle_local_entropy.py"),
                           os.path.join(ROOT, "tests", "test_oracle_pins.py"),
-                          os.path.join(ROOT, "tests", "test_oracle_aniso.py"),
-                          os.path.join(ROOT, "tests", "test_oracle_local_entropy.py")],
+                          os.path.join(ROOT, "tests", "test_oracle_aniso.py")],
                          cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
     assert res.returncode != 0, f"planted slip {name} survived the pins:\n{res.stdout[-2000:]}"
