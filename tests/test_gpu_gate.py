@@ -194,18 +194,22 @@ def test_repeated_and_partial_filter_lists(lnf):
             _check_multi(c, t, vol, 2, prm, ids)
 
 
-@pytest.mark.parametrize("dims", [(13, 11, 7), (33, 9, 5), (40, 26, 3)])
+@pytest.mark.parametrize("dims", [(13, 11, 7), (33, 9, 5), (40, 26, 3), (15, 9, 9)])
 @pytest.mark.parametrize("dt", ["u16", "u8"])
 def test_volume_tails(lnf, dt, dims):
-    """Volumes whose voxel count is not a multiple of 8 or of the 1024-voxel
-    chunks, with passing voxels at the very first and last voxels and along the
-    last row: every filter against the oracle."""
+    """Volumes whose voxel count is not a multiple of 8 or of a chunk, with
+    passing voxels at the very first and last voxels, along the last row, and
+    (where the volume has an interior) an interior voxel whose taps reach the
+    volume's last voxel, in its last partial 16-byte vector: every filter
+    against the oracle."""
     nx, ny, nz = dims
     rng = np.random.default_rng(751 + nx)
     hi = 4095 if dt == "u16" else 255
     vol = np.clip(np.rint(rng.normal(hi // 10, hi // 100, (nz, ny, nx))), 0, hi)
     vol[-1, -1, :] = hi - 3
     vol[0, 0, 0] = vol[-1, -1, -1] = hi
+    if min(dims) >= 7:
+        vol[-4, -4, -4] = hi - 1   # interior at r <= 2 (reach 3); its reach ends at the last voxel
     vol = vol.astype(np.uint16 if dt == "u16" else np.uint8)
     st = oracle.stats(vol)
     t = torch.from_numpy(vol).cuda()
