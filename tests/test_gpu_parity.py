@@ -333,6 +333,15 @@ def test_batched_mixed(lnf, autotune):
                 assert_same(host(j["out"]), w, f"batch job {i} rep {rep}")
                 hw = oracle.image_entropy(oracle.histogram(w))
                 assert abs(Hh[i] - hw) <= H_TOL * max(1.0, hw), (i, Hh[i], hw)
+        # the autotuner's record: one entry per class of specialised jobs, a z length
+        # among the candidates, a time for every candidate
+        tun = c.tuning()
+        if autotune:
+            assert tun["classes"], "the autotuner recorded no job class"
+            for cl in tun["classes"]:
+                assert cl["zlen"] in (4, 8, 16, 32) and all(v > 0 for v in cl["ms"].values()), cl
+        else:
+            assert not tun["classes"] and tun["generic_zchunk"] == 0
 
 
 def test_invalid_arguments(ctx, lnf):
