@@ -614,6 +614,16 @@ lnf_status lnf_run_one(lnf_ctx *ctx, int filter, int radius, const void *in, voi
     if (!ctx->no_fast) {
         int handled = 0;
         pk.jobs[0].orig = orig;
+        if (filter == LNF_ENTROPY_LOCAL && !ctx->no_gate && lnf_gate_covers(pk.jobs[0], filter)) {
+            // the gate-first kernel takes the volume while few voxels pass; the
+            // generic kernel below does it otherwise
+            int gh = 0;
+            if ((s = lnf_gate_launch_eloc(ctx, pk.jobs[0], stream, &gh)) != LNF_OK) {
+                lnf_prof_end(ctx, rec, filter_name(filter), stream, 1);
+                return s;
+            }
+            pk.jobs[0].gated = gh;
+        }
         s = lnf_fast_dispatch(ctx, pk.jobs[0], pk.jobs[0].tmap_idx >= 0 ? &pk.tmaps[0] : nullptr, stream, &handled,
                               nullptr, 1);
         if (s != LNF_OK || handled) {

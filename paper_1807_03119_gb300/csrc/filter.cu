@@ -370,6 +370,8 @@ __global__ void __launch_bounds__(kThreads) k_filter(const __grid_constant__ Fil
             hs.job = j;
             hs.base = J.dtype == 0 ? 0u : J.prm->minv;
         }
+        if (J.gated && lnf_gate_mode(*J.prm))
+            continue;   // the gate-first kernel writes this job's output (uniform over the CTA)
         const int local = item - J.item_begin;
         const CUtensorMap *tm = J.tmap_idx >= 0 ? &pk.tmaps[J.tmap_idx] : nullptr;
         if (J.dtype == 0)

@@ -90,32 +90,50 @@ __host__ __device__ constexpr bool ours_row(int R, int dy, int dz)
     return false;
 }
 
-enum { SET_OURS = 1, SET_CUBE = 2, SET_ALL = 3 };
+// filter sets of a launch: the paper's filter, the four cube filters, both, or
+// the entropy filter with the cube's own grey-level probabilities (alone; its
+// output takes the entropy filter's slot)
+enum { SET_OURS = 1, SET_CUBE = 2, SET_ALL = 3, SET_ELOC = 4 };
+
+// whether a launch of set SET writes the output slot of filter id f (0..4)
+template <int SET>
+__host__ __device__ constexpr bool gets(int f)
+{
+    return f == LNF_OURS ? (SET & SET_OURS) != 0
+                         : (f == LNF_ENTROPY ? (SET & (SET_CUBE | SET_ELOC)) != 0 : (SET & SET_CUBE) != 0);
+}
 
 template <typename T, int R, int SET>
 struct GGeo {
     static constexpr bool OURS = (SET & SET_OURS) != 0;
     static constexpr bool CUBE = (SET & SET_CUBE) != 0;
+    static constexpr bool ELOC = (SET & SET_ELOC) != 0;
+    static constexpr bool BOX = CUBE || ELOC;         // evaluates the M^3 cube
     static constexpr int M = 2 * R + 1;
     static constexpr int H = OURS ? R + 1 : R;       // reach of the taps on each axis
     static constexpr int W = 2 * H + 1;
-    static constexpr int CT = CUBE ? M * M * M : 0;  // cube taps
+    static constexpr int CT = BOX ? M * M * M : 0;   // cube taps
     static constexpr int ES = (int)sizeof(T);
-    static constexpr int NOUT = (OURS ? 1 : 0) + (CUBE ? 4 : 0);
+    static constexpr int NOUT = (OURS ? 1 : 0) + (CUBE ? 4 : 0) + (ELOC ? 1 : 0);
     static constexpr int LUTN = CUBE ? (ES == 1 ? 256 : kLutW) : 0;
     static constexpr int HISTB = NOUT * kHistW * 2;   // two 16-bit bins per 32-bit word
     // chunks: VL 16-byte vectors of 8 voxels per lane; PF: the next chunk's loads
     // are issued before the current chunk is used
-    static constexpr int VL = CUBE ? LNF_GATE_VL_CUBE : LNF_GATE_VL_OURS;
-    static constexpr bool PF = (CUBE ? LNF_GATE_PF_CUBE : LNF_GATE_PF_OURS) != 0;
+    static constexpr int VL = BOX ? LNF_GATE_VL_CUBE : LNF_GATE_VL_OURS;
+    static constexpr bool PF = (BOX ? LNF_GATE_PF_CUBE : LNF_GATE_PF_OURS) != 0;
     static constexpr int CVEC = 32 * VL;            // vectors per chunk
     static constexpr int CVOX = CVEC * 8;           // voxels per chunk
     static constexpr int LCAP = CVOX + 32;          // a warp's list: one chunk plus 31 carried over
     static constexpr int LSTB = kWarpsC * LCAP * 4;
-    static constexpr int SMEM = HISTB + LUTN * 4 + LSTB;
+    // the local entropy filter: each lane's column of its voxel's cube values
+    // (16-bit, value t of lane L at t * 32 + L in its warp's block), and the table
+    // t[0..CT] of round(2^22 c log2 c)
+    static constexpr int ELB = ELOC ? kWarpsC * CT * 32 * 2 : 0;
+    static constexpr int LTB = ELOC ? ((CT + 1) * 8 + 15) / 16 * 16 : 0;
+    static constexpr int SMEM = HISTB + LUTN * 4 + LSTB + ELB + LTB;
     // CTAs per SM the register budget aims for: the kernel waits on loads, so
     // more warps hide more of it where the evaluation needs fewer registers
-    static constexpr int MINB = CUBE ? LNF_GATE_MINB_CUBE : LNF_GATE_MINB_OURS;
+    static constexpr int MINB = BOX ? LNF_GATE_MINB_CUBE : LNF_GATE_MINB_OURS;
     // sigma: value and count packed in one word (count in the low bits) while exact
     static constexpr int SSH = ES == 1 ? 10 : 8;
     static constexpr bool SPACK = CT < (1 << SSH) &&
@@ -128,7 +146,7 @@ struct GGeo {
 template <int SET>
 __host__ __device__ constexpr int oslot(int f)
 {
-    return f == LNF_OURS ? ((SET & SET_CUBE) ? 4 : 0) : f;
+    return (SET & SET_ELOC) ? 0 : (f == LNF_OURS ? ((SET & SET_CUBE) ? 4 : 0) : f);
 }
 
 struct GateArgs {
@@ -315,6 +333,9 @@ __global__ void __launch_bounds__(kThreadsC, GGeo<T, R, SET>::MINB) k_gate(const
     u32 *hsh = reinterpret_cast<u32 *>(smem);                                  // NOUT windows of 16-bit bins
     u32 *lut_sh = reinterpret_cast<u32 *>(smem + G::HISTB);                    // LUTN entropy weights
     u32 *lst = reinterpret_cast<u32 *>(smem + G::HISTB + G::LUTN * 4);         // the warps' lists
+    uint16_t *elb = reinterpret_cast<uint16_t *>(smem + G::HISTB + G::LUTN * 4 + G::LSTB);   // cube columns
+    unsigned long long *lt_sh =
+        reinterpret_cast<unsigned long long *>(smem + G::HISTB + G::LUTN * 4 + G::LSTB + G::ELB);   // t[c]
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const T *in = static_cast<const T *>(a.in);
 
@@ -333,6 +354,13 @@ __global__ void __launch_bounds__(kThreadsC, GGeo<T, R, SET>::MINB) k_gate(const
         hsh[i] = 0;
     for (int i = tid; i < G::LUTN; i += kThreadsC)
         lut_sh[i] = (lbase + i < (G::ES == 1 ? 256u : 65536u)) ? a.lut[lbase + i] : 0u;
+    if constexpr (G::ELOC)
+        for (int i = tid; i <= G::CT; i += kThreadsC)
+            lt_sh[i] = P.lt ? P.lt[i] : 0ull;
+    // the local entropy filter's theta (2^-22 bits): default floor(t[m] / 2m)
+    long long lte = P.lte_cfg;
+    if (G::ELOC && lte == -2)
+        lte = P.lt ? (long long)(P.lt[G::CT] / (2ull * (u64)(G::CT ? G::CT : 1))) : 0;
     __syncthreads();
 
     typedef ExactDiv<27ull * G::M, 27ull * G::M * 65536ull> DivO;   // the paper's filter: U / 27M
@@ -376,7 +404,41 @@ __global__ void __launch_bounds__(kThreadsC, GGeo<T, R, SET>::MINB) k_gate(const
         const u64 reach = (u64)G::H * ((u64)nxny + (u64)a.nx + 1ull);
         if (inner && !lnfdev::lnf_dbg_ok((u64)i >= reach && (u64)i + reach < a.n, a.err))
             return;
-        if (inner && (lutall || !G::CUBE)) {
+        if constexpr (G::ELOC) {
+            // the entropy filter with the cube's own probabilities: the lane's cube
+            // values into its column, then m 2^22 H = t[m] - sum_g t[c_g], the sum taken
+            // over the taps a as t[k_a] - t[k_a - 1] (k_a: taps up to a at a's level)
+            uint16_t *col = elb + warp * (G::CT * 32) + lane;
+            if (inner) {
+                const T *c0 = in + i;
+                const long long sxy = (long long)nxny;
+                sfor<G::CT>([&](auto ti) {
+                    constexpr int t = decltype(ti)::value;
+                    constexpr int dx = t % G::M - R, dy = (t / G::M) % G::M - R, dz = t / (G::M * G::M) - R;
+                    col[t * 32] = (uint16_t)ldgv<T>(c0 + (dz * sxy + (long long)dy * a.nx + dx));
+                });
+            } else {
+                int t = 0;
+                for (int dz = -R; dz <= R; ++dz)
+                    for (int dy = -R; dy <= R; ++dy) {
+                        const T *rp = in + ((long long)clampi(z + dz, 0, a.nz - 1) * nxny +
+                                            (long long)clampi(y + dy, 0, a.ny - 1) * a.nx);
+                        for (int dx = -R; dx <= R; ++dx, ++t)
+                            col[t * 32] = (uint16_t)ldgv<T>(rp + clampi(x + dx, 0, a.nx - 1));
+                    }
+            }
+            u64 K = 0;
+            for (int t = 0; t < G::CT; ++t) {
+                const u32 va = col[t * 32];
+                u32 k = 1;
+#pragma unroll 4
+                for (int b = 0; b < t; ++b)
+                    k += col[b * 32] == va ? 1u : 0u;
+                K += lt_sh[k] - lt_sh[k - 1];
+            }
+            const long long crit = (long long)(lt_sh[G::CT] - K);
+            fv[LNF_ENTROPY] = crit > (long long)G::CT * lte ? P0 : 0u;
+        } else if (inner && (lutall || !G::CUBE)) {
             Sums<T, R, SET, true, false> sm;
             sm.run(in, x, y, z, a.nx, a.ny, a.nz, slo, swd, olo, owd, lut_sh, lbase, a.lut);
             finish(sm);
@@ -387,7 +449,7 @@ __global__ void __launch_bounds__(kThreadsC, GGeo<T, R, SET>::MINB) k_gate(const
         }
 #pragma unroll
         for (int f = 0; f < 5; ++f) {
-            if (!(((f == LNF_OURS) ? G::OURS : G::CUBE) && a.out[f]))
+            if (!(gets<SET>(f) && a.out[f]))
                 continue;
             const u32 v = fv[f];
             if (!v)
@@ -464,7 +526,7 @@ __global__ void __launch_bounds__(kThreadsC, GGeo<T, R, SET>::MINB) k_gate(const
                     word |= (u64)pass_bits<T>(w[k], T_) << (8 * k);
 #pragma unroll
                     for (int f = 0; f < 5; ++f)
-                        if (((f == LNF_OURS) ? G::OURS : G::CUBE) && a.out[f]) {
+                        if (gets<SET>(f) && a.out[f]) {
                             if (sizeof(T) == 2)
                                 reinterpret_cast<uint4 *>(a.out[f])[v] = make_uint4(0u, 0u, 0u, 0u);
                             else
@@ -477,7 +539,7 @@ __global__ void __launch_bounds__(kThreadsC, GGeo<T, R, SET>::MINB) k_gate(const
                         const u64 vi = nvec * 8 + q;
                         bits |= (ldgv<T>(in + vi) >= T_ ? 1u : 0u) << q;
                         for (int f = 0; f < 5; ++f)
-                            if (((f == LNF_OURS) ? G::OURS : G::CUBE) && a.out[f])
+                            if (gets<SET>(f) && a.out[f])
                                 static_cast<T *>(a.out[f])[vi] = (T)0;
                     }
                     word |= (u64)bits << (8 * k);
@@ -536,7 +598,7 @@ __global__ void __launch_bounds__(kThreadsC, GGeo<T, R, SET>::MINB) k_gate(const
     __syncthreads();
 #pragma unroll
     for (int f = 0; f < 5; ++f) {
-        if (!(((f == LNF_OURS) ? G::OURS : G::CUBE) && a.out[f] && a.hist[f]))
+        if (!(gets<SET>(f) && a.out[f] && a.hist[f]))
             continue;
         const u32 *h = hsh + oslot<SET>(f) * (kHistW / 2);
         for (int i = tid; i < kHistW / 2; i += kThreadsC) {
@@ -586,10 +648,21 @@ lnf_status gate_by_radius(lnf_ctx *ctx, int radius, const GateArgs &a, cudaStrea
     }
 }
 
-// The gate kernel for one job (outs / hists by filter id).
+// the local entropy filter at r = 1..2 (its cube's columns in shared memory
+// bound the radius)
+template <typename T>
+lnf_status gate_eloc_by_radius(lnf_ctx *ctx, int radius, const GateArgs &a, cudaStream_t st)
+{
+    if (radius == 1)
+        return gate_launch_t<T, 1, SET_ELOC>(ctx, a, st);
+    return gate_launch_t<T, 2, SET_ELOC>(ctx, a, st);
+}
+
+// The gate kernel for one job (outs / hists by filter id; `eloc`: the entropy
+// filter with the cube's own probabilities, its output in the entropy slot).
 template <typename T>
 lnf_status gate_dispatch_t(lnf_ctx *ctx, const FilterJob &j, void *const outs[5], u64 *const hists[5],
-                           cudaStream_t st, int *handled)
+                           cudaStream_t st, int *handled, bool eloc = false)
 {
     const u64 n = (u64)j.nx * j.ny * j.nz;
     if (n >= (1ull << 32) || j.pitch != j.nx || reinterpret_cast<uintptr_t>(j.in) % 16 != 0)
@@ -615,7 +688,11 @@ lnf_status gate_dispatch_t(lnf_ctx *ctx, const FilterJob &j, void *const outs[5]
     const bool ours = outs[LNF_OURS] != nullptr;
     const bool cube = outs[0] || outs[1] || outs[2] || outs[3];
     lnf_status s;
-    if (ours && cube)
+    if (eloc)
+        s = (j.radius >= 1 && j.radius <= 2 && outs[LNF_ENTROPY] && !ours && !outs[0] && !outs[1] && !outs[3])
+                ? gate_eloc_by_radius<T>(ctx, j.radius, a, st)
+                : lnf_fail(ctx, LNF_EINVAL, "gate-first kernel: local entropy job not covered");
+    else if (ours && cube)
         s = gate_by_radius<T, SET_ALL>(ctx, j.radius, a, st);
     else if (ours)
         s = gate_by_radius<T, SET_OURS>(ctx, j.radius, a, st);

@@ -194,6 +194,10 @@ lnf_status lnf_fast2_box(lnf_ctx *ctx, const FilterJob &job, cudaStream_t stream
 // and its launch for the filters whose outputs are given (outs / hists indexed
 // by filter id 0..4, null where not requested); *handled = 1 if launched
 bool lnf_gate_covers(const FilterJob &j, int filter);
+// the entropy filter with local probabilities (LNF_ENTROPY_LOCAL) of a whole
+// volume through the gate-first kernel; *handled = 1 if launched (the generic
+// kernel then skips the job while the gate takes the volume: FilterJob::gated)
+lnf_status lnf_gate_launch_eloc(lnf_ctx *ctx, const FilterJob &j, cudaStream_t st, int *handled);
 lnf_status lnf_gate_launch(lnf_ctx *ctx, const FilterJob &j, void *const outs[5], u64 *const hists[5],
                            cudaStream_t st, int *handled);
 // render.cu: one ray per pixel (see lnf_render)

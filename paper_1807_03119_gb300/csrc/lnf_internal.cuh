@@ -85,6 +85,8 @@ struct FilterJob {
     u64 *out_hist;              // output histogram (levels entries) or null
     int tmap_idx;               // index of the job's TMA map in the pack, -1: plain loads
     const void *orig;           // the caller's dense volume when `in` is a row-padded copy of it (or null)
+    int gated;                  // 1: a gate-first kernel was launched for the job; the generic kernel
+                                // skips its work while the gate takes the volume (lnf_gate_mode)
     int tiles_x, tiles_y, zchunks;
     int item_begin;             // first flattened work item of this job
 };

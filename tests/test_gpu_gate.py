@@ -218,3 +218,39 @@ def test_volume_tails(lnf, dt, dims):
             prm = oracle.derive_params(st, r, oracle.Config(threshold_mode="fixed", threshold_value=hi // 2))
             assert np.count_nonzero(vol >= prm["T"]) * 32 <= vol.size
             _check_multi(c, t, vol, r, prm)
+
+
+@pytest.mark.parametrize("dt,dims,seed", [("u16", (96, 40, 36), 761), ("u8", (128, 33, 29), 762),
+                                          ("u16", (93, 37, 21), 763), ("u16", (9, 7, 4), 764)])
+@pytest.mark.parametrize("theta", [None, int(3.2 * (1 << oracle.ENTROPY_W_BITS))])
+def test_gate_local_entropy(lnf, monkeypatch, dt, dims, seed, theta):
+    """The entropy filter with the cube's own grey-level probabilities (id 8)
+    through the gate-first kernel (few voxels pass; each lane's cube values in
+    shared memory, the levels counted by rank) against the oracle and against
+    the generic kernel alone, r = 1, 2, two thresholds."""
+    if dims[0] * dims[1] * dims[2] < 1000:
+        vol = _tiny(dims, seed, dt)
+    else:
+        vol = _sparse_u16(dims, seed) if dt == "u16" else _sparse_u8(dims, seed)
+    st = oracle.stats(vol)
+    kw = {} if theta is None else {"entropy_local_te": theta}
+    a = lnf.Context(**kw)
+    b = _ring_context(lnf, monkeypatch, **kw)
+    try:
+        t = torch.from_numpy(vol).cuda()
+        for r in (1, 2):
+            prm = oracle.derive_params(st, r, oracle.Config(entropy_local_te=theta))
+            assert np.count_nonzero(vol >= prm["T"]) * 32 <= vol.size, "volume not sparse enough"
+            want = oracle.filter_volume(vol, oracle.ENTROPY_LOCAL, r, params=prm)
+            got = a.filter_volume(t, oracle.ENTROPY_LOCAL, r).cpu().numpy()
+            ring = b.filter_volume(t, oracle.ENTROPY_LOCAL, r).cpu().numpy()
+            assert np.array_equal(got, want), (r, theta, int((got != want).sum()))
+            assert np.array_equal(ring, want), (r, theta, "generic")
+            outs, H = a.filter_multi(t, [oracle.ENTROPY_LOCAL], r)
+            assert np.array_equal(outs[0].cpu().numpy(), want)
+            hw = oracle.image_entropy(oracle.histogram(want))
+            assert abs(float(H.cpu().numpy()[1]) - hw) <= 1e-9 * max(1.0, hw)
+        a.params()
+    finally:
+        a.close()
+        b.close()
