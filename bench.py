@@ -326,6 +326,17 @@ def run_reference(args):
 
 # ----------------------------------------------------------------------------- extra configurations
 
+def ctx_kwargs(args):
+    """lnf.Context keyword arguments from the configuration flags, and the
+    non-default ones (for the line's config)."""
+    kw = {"threshold_mode": args.threshold_mode, "threshold_value": args.threshold_value, "sigma_k": args.sigma_k,
+          "okada_td": args.okada_td, "entropy_te": args.entropy_te, "entropy_local_te": args.entropy_local_te,
+          "cluster_offset": args.cluster_offset, "autotune": args.autotune}
+    defaults = {"threshold_mode": 0, "threshold_value": 0, "sigma_k": 2, "okada_td": -1, "entropy_te": -2,
+                "entropy_local_te": -2, "cluster_offset": 1, "autotune": False}
+    return kw, {k: v for k, v in kw.items() if v != defaults[k]}
+
+
 def start_generation():
     """Draw the extra workloads' volumes (the 1024^3 uint8 phantom, the 64^3
     phantom, the served and the batched volumes) in a spawn process pool started
@@ -475,6 +486,17 @@ def main():
     ap.add_argument("--dims", type=int, nargs=3, default=None,
                     help="profiling: a smaller phantom of the same workload (nx ny nz); not a bench line")
     ap.add_argument("--no-e2e", action="store_true", help="profiling: skip the host-buffer leg")
+    # the library's configuration (lnf_config), for the main step and --mode ours
+    ap.add_argument("--threshold-mode", type=int, default=0, choices=[0, 1, 2],
+                    help="noise threshold: 0 Otsu (Eq. 1), 1 fixed (--threshold-value), 2 none")
+    ap.add_argument("--threshold-value", type=int, default=0)
+    ap.add_argument("--sigma-k", type=int, default=2, help="sigma band half-width in units of sigma (Eq. 5: 2)")
+    ap.add_argument("--okada-td", type=int, default=-1, help="Okada T_d (Eq. 6), -1 automatic")
+    ap.add_argument("--entropy-te", type=int, default=-2, help="entropy filter T_e in weight units, -2 auto, -1 all")
+    ap.add_argument("--entropy-local-te", type=int, default=-2,
+                    help="local entropy filter theta in 2^-22 bits, -2 auto (log2(m)/2), -1 all")
+    ap.add_argument("--cluster-offset", type=int, default=1, help="d of the diagonal clusters (paper: 1)")
+    ap.add_argument("--autotune", action="store_true", help="lnf_config.autotune (batched calls)")
     ap.add_argument("--dense", action="store_true",
                     help="--mode ours: no noise threshold, so every voxel passes and the ring kernel does the work")
     ap.add_argument("--no-extras", action="store_true",
@@ -543,7 +565,8 @@ def main():
     outs = [torch.empty_like(t) for _ in filters]
     H = torch.zeros(len(filters) + 1, dtype=torch.float64, device="cuda")
     stream = torch.cuda.current_stream()
-    ctx = lnf.Context()
+    ckw, cfg_set = ctx_kwargs(args)
+    ctx = lnf.Context(**ckw)
 
     def step():
         ctx.filter_multi(t, filters, RADIUS, outs=outs, H=H)
@@ -657,9 +680,10 @@ def main():
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u16", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "radius": RADIUS, "filters": FILTER_NAMES,
-                   "l2": "inputs larger than L2 (268 MB per volume, 1.6 GB touched per step)",
-                   "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
+        "config": dict({"workload": WORKLOAD, "radius": RADIUS, "filters": FILTER_NAMES,
+                        "l2": "inputs larger than L2 (268 MB per volume, 1.6 GB touched per step)",
+                        "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
+                       **({"lnf_config": cfg_set} if cfg_set else {})),
         "e2e": e2e, "gpu_launches": launches, "roofline": roof, "rooflines": rooflines,
         "kernel_ms": {k: v[1] / args.steps for k, v in kern.items()},
         "hbm_gbs_step": (N_VOX * ES + 5 * N_VOX * ES * 2) / (ms / 1e3) / 1e9,
@@ -876,7 +900,10 @@ def run_ours(args):
     vol = phantoms.P2()
     t = torch.from_numpy(vol).cuda()
     out = torch.empty_like(t)
-    ctx = lnf.Context(threshold_mode=lnf.THRESH_NONE) if args.dense else lnf.Context()
+    ckw, cfg_set = ctx_kwargs(args)
+    if args.dense:
+        ckw["threshold_mode"] = lnf.THRESH_NONE
+    ctx = lnf.Context(**ckw)
     sampler = ClockSampler(0, args.clocks_csv)
     sampler.start()
     call_ms, kern = timed_calls(ctx, lambda: ctx.filter_volume(t, lnf.OURS, RADIUS, out=out), torch, args.warmup,
@@ -888,9 +915,10 @@ def run_ours(args):
     line = {"metric": "paper's filter alone, 512^3 uint16 r=2, GVoxel/s", "mode": "ours_dense" if args.dense else "ours",
             "value": N_VOX / call_ms / 1e6, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
             "ms_per_call": call_ms, "higher_is_better": True, "dtype": "u16", "data": "synthetic",
-            "config": {"workload": "512x512x512 uint16 insect-like phantom, the paper's filter at r=2 with its "
-                                   "output histogram" + (", no noise threshold (every voxel passes)" if args.dense else ""),
-                       "l2": "inputs larger than L2"},
+            "config": dict({"workload": "512x512x512 uint16 insect-like phantom, the paper's filter at r=2 with "
+                                        "its output histogram" +
+                                        (", no noise threshold (every voxel passes)" if args.dense else ""),
+                            "l2": "inputs larger than L2"}, **({"lnf_config": cfg_set} if cfg_set else {})),
             "roofline": {"bound": "hbm", "achieved": ach, "peak": pk["hbm_gbs"], "unit": "GB/s",
                          "frac": ach / pk["hbm_gbs"], "avg_ms": kms, "kernel": kind, "traffic": recorded_traffic(kind)},
             "kernel_ms": kern, "clocks": clocks}
