@@ -444,6 +444,47 @@ def test_full_1024_u8_ours_radius_sweep(ctx):
         torch.cuda.empty_cache()
 
 
+def test_largest_accepted_volume(lnf):
+    """2048 x 2048 x 1023 uint8 = 4,290,772,992 voxels, just under the API's limit
+    of 2^32 - 1 (32-bit voxel indices in the gate-first kernel, 64-bit offsets
+    elsewhere): the statistics against the host, the paper's filter through the
+    gate-first kernel (0.6% of the voxels pass) and, with no noise threshold,
+    through the plane-ring kernel, each on sampled voxels and whole first and last
+    planes against the oracle; a volume of exactly 2^32 voxels is refused."""
+    nx, ny, nz = 2048, 2048, 1023
+    rng = np.random.default_rng(99)
+    vol = rng.integers(0, 40, size=(nz, ny, nx), dtype=np.uint8)
+    vol[100:140, 500:1000, 500:1500] = 200          # 0.47% of the voxels
+    vol[nz - 40:, ny - 200:, nx - 600:] = 210        # up to the last plane, row and column
+    vol[:2, :300, :64] = 220                         # in the first planes
+    st = oracle.stats(vol)
+    t = dev(vol)
+    for mode in (0, 2):   # Otsu (gate-first kernel), none (plane-ring kernel)
+        cfg = oracle.Config(threshold_mode="otsu" if mode == 0 else "none")
+        prm = oracle.derive_params(st, 1, cfg)
+        if mode == 0:
+            assert np.count_nonzero(vol >= prm["T"]) * 32 <= vol.size
+        with lnf.Context(threshold_mode=mode) as c:
+            out = c.filter_volume(t, oracle.OURS, 1)
+            p = c.params()
+            assert p["n_voxels"] == vol.size and p["sum"] == st.S and p["sum_sq"] == st.Q
+            assert p["threshold"] == prm["T"]
+            o = host(out)
+            del out
+        _check_sampled(vol, [o], [oracle.OURS], 1, prm, 41 + mode)
+        _check_slabs(vol, [o], [oracle.OURS], 1, prm, (0, 1, nz - 2, nz - 1))
+        del o
+    del t
+    torch.cuda.empty_cache()
+    big = torch.empty((1024, 2048, 2048), dtype=torch.uint8, device="cuda")   # 2^32 voxels
+    with lnf.Context() as c:
+        with pytest.raises(lnf.LnfError) as e:
+            c.filter_volume(big, oracle.OURS, 1)
+        assert e.value.status == 1
+    del big
+    torch.cuda.empty_cache()
+
+
 # ----------------------------------------------------------------------------- specialised kernels
 
 FAST_CASES = [
