@@ -22,7 +22,11 @@
 // hundred claims earlier, so those taps come from L2.  A voxel within the
 // filter's reach of a face takes a clamped path (clamp-to-edge sampling).
 // One launch serves any subset of the five filters: one read of the volume,
-// one write per output.
+// one write per output.  A launch of set SET_ELOC instead evaluates the entropy
+// filter with the cube's own grey-level probabilities (filter id 8, r = 1..2):
+// each lane copies its voxel's M^3 values into its own column of shared memory
+// and counts equal levels there by rank (the criterion t[m] - sum_g t[c_g]
+// with t[c] = round(2^22 c log2 c) from the parameter block).
 //
 // Output histograms: nonzero outputs (all >= max(1, T, min)) go to a shared
 // window of 4096 16-bit bins per output (all 12-bit levels), the rest to
