@@ -257,6 +257,10 @@ extern "C" lnf_status lnf_create(const lnf_config *cfg_in, lnf_ctx **out)
         ctx->no_fast = ev && ev[0] == '1';
         ev = getenv("LNF_NO_GATE");
         ctx->no_gate = ev && ev[0] == '1';
+        // test hook: the plane-ring kernels' work-item z length (planes per item)
+        ev = getenv("LNF_FAST_ZLEN");
+        if (ev && atoi(ev) >= 1 && atoi(ev) <= 1024)
+            ctx->fast_zlen = atoi(ev);
 
         if (cudaDeviceSynchronize() != cudaSuccess)
             s = LNF_ECUDA;

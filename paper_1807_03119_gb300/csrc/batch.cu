@@ -144,13 +144,13 @@ static lnf_status check_job(lnf_ctx *ctx, const lnf_job &j, int i)
 static int job_class(const lnf_job &j) { return (j.dtype * 16 + j.filter_id) * 16 + j.radius; }
 
 // z length of a specialised work item for job j: the tuned one of its class, the
-// override `zlen` (> 0, used while tuning), else the default
+// override `zlen` (> 0, used while tuning), else 0 (the kernel's automatic choice)
 static int zlen_for(const lnf_ctx *ctx, const lnf_job &j, int zlen)
 {
     if (zlen > 0)
         return zlen;
     auto it = ctx->tuned_zlen.find(job_class(j));
-    return it != ctx->tuned_zlen.end() ? it->second : 16;
+    return it != ctx->tuned_zlen.end() ? it->second : 0;   // 0: the kernel's automatic choice
 }
 
 lnf_status lnf_enqueue_batch(lnf_ctx *ctx, const lnf_job *jobs, int n, int zchunk, int zlen, cudaStream_t st,

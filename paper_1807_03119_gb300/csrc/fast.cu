@@ -661,6 +661,19 @@ __device__ void ours_items(const FastArgs &a, const CUtensorMap *tmap, unsigned 
     }
 }
 
+// Work-item z length (planes per item) when neither the autotuner nor the
+// caller set one: the longest of 64, 32 and 16 planes that still gives every CTA
+// of the persistent grid three items or more.  Longer items repeat fewer of the
+// 2R + 2 warm-up planes of their z march; enough items keep the grid balanced
+// (measured: 512^3 uint16 is fastest at 32, the 1024^3 uint8 volume at 64).
+static int auto_zlen(int tiles, int depth, int grid)
+{
+    for (int zl : {64, 32})
+        if ((long long)tiles * ((depth + zl - 1) / zl) >= 3ll * grid)
+            return zl;
+    return 16;
+}
+
 // MASK: masked per-voxel stores (a region of interest, an odd width), else dense
 // 4-voxel vector stores
 template <typename T, int R, bool MASK>
@@ -740,9 +753,6 @@ lnf_status launch(lnf_ctx *ctx, const FilterJob &j, cudaStream_t st, u64 *out_hi
     a.roi = whole && vec ? 0 : 1;
     a.tiles_x = (a.xend - a.xs + kTX - 1) / kTX;
     a.tiles_y = (j.by + kTY - 1) / kTY;
-    a.zlen = ctx->fast_zlen > 0 ? ctx->fast_zlen : 16;
-    a.zchunks = (j.bz + a.zlen - 1) / a.zlen;
-    a.total_items = a.tiles_x * a.tiles_y * a.zchunks;
     a.prm = j.prm;
     a.out_hist = out_hist;
     a.counter = counter ? counter : ctx->d_counter + 8;
@@ -755,7 +765,11 @@ lnf_status launch(lnf_ctx *ctx, const FilterJob &j, cudaStream_t st, u64 *out_hi
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kThreads, G::SMEM);
     if (occ < 1)
         occ = 1;
-    const int grid = std::min(a.total_items, ctx->num_sms * occ);
+    const int cap = ctx->num_sms * occ;
+    a.zlen = ctx->fast_zlen > 0 ? ctx->fast_zlen : auto_zlen(a.tiles_x * a.tiles_y, j.bz, cap);
+    a.zchunks = (j.bz + a.zlen - 1) / a.zlen;
+    a.total_items = a.tiles_x * a.tiles_y * a.zchunks;
+    const int grid = std::min(a.total_items, cap);
     if (cudaMemsetAsync(a.counter, 0, sizeof(u32), st) != cudaSuccess)
         return lnf_fail(ctx, LNF_ECUDA, "fast kernel: counter reset");
     kern<<<grid, kThreads, G::SMEM, st>>>(*tmap, a);

@@ -71,7 +71,7 @@ struct lnf_ctx {
     int device = 0;
     int num_sms = 1;
     int zchunk = 64;            // z chunk length of a work item (generic kernel)
-    int fast_zlen = 16;         // z chunk length of a work item (specialised kernels)
+    int fast_zlen = 0;          // z chunk length of a work item (specialised kernels; 0: automatic)
     bool no_tma = false;        // testing: force plain loads
     bool no_fast = false;       // testing: force the generic kernel
     bool no_gate = false;       // testing: never launch the gate-first kernel (the ring kernels work)
