@@ -339,12 +339,6 @@ lnf_status launch2(lnf_ctx *ctx, const FilterJob &j, cudaStream_t st, u32 *count
     a.roi = whole && vec ? 0 : 1;
     a.tiles_x = (a.xend - a.xs + kTX - 1) / kTX;
     a.tiles_y = (j.by + kTY - 1) / kTY;
-    a.zlen = ctx->fast_zlen > 0 ? ctx->fast_zlen : 16;
-    // the tap kernels' work is concentrated where voxels pass the gate: shorter
-    // z chunks (four times the work items) keep one heavy item from setting the end
-    if (!S::BOX)
-        a.zlen = std::max(1, a.zlen / 4);
-    a.total_items = a.tiles_x * a.tiles_y * ((j.bz + a.zlen - 1) / a.zlen);
     a.filter = FILTER;
     a.prm = j.prm;
     a.lut = j.lut;
@@ -361,7 +355,26 @@ lnf_status launch2(lnf_ctx *ctx, const FilterJob &j, cudaStream_t st, u32 *count
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kThreads, S::TOTAL);
     if (occ < 1)
         occ = 1;
-    const int grid = std::min(a.total_items, ctx->num_sms * occ);
+    const int cap = ctx->num_sms * occ;
+    if (ctx->fast_zlen > 0) {
+        a.zlen = ctx->fast_zlen;
+    } else if (S::BOX) {
+        // the longest of 64, 32, 16 planes that still gives every CTA three items
+        a.zlen = 16;
+        for (int zl : {64, 32})
+            if ((long long)a.tiles_x * a.tiles_y * ((j.bz + zl - 1) / zl) >= 3ll * cap) {
+                a.zlen = zl;
+                break;
+            }
+    } else {
+        a.zlen = 16;
+    }
+    // the tap kernels' work is concentrated where voxels pass the gate: shorter
+    // z chunks (four times the work items) keep one heavy item from setting the end
+    if (!S::BOX)
+        a.zlen = std::max(1, a.zlen / 4);
+    a.total_items = a.tiles_x * a.tiles_y * ((j.bz + a.zlen - 1) / a.zlen);
+    const int grid = std::min(a.total_items, cap);
     if (cudaMemsetAsync(a.counter, 0, sizeof(u32), st) != cudaSuccess)
         return lnf_fail(ctx, LNF_ECUDA, "fast2 kernel: counter reset");
     kern<<<grid, kThreads, S::TOTAL, st>>>(*tmap, a);
