@@ -361,7 +361,11 @@ typedef struct lnf_job {
  * launches (a whole volume of the paper's filter also gets the gate-first
  * kernel, which takes the job on the device while few voxels pass the gate),
  * and ONE persistent launch of the generic kernel over the flattened tile list
- * of all other jobs, then one entropy launch.  The sequence is captured once
+ * of all other jobs, then one entropy launch.  The specialised launches run as
+ * one chain per input volume, the chains side by side on the context's batch
+ * streams (forked from and joined back into its stream), so the outputs of
+ * different jobs must not overlap (not checked: overlapping outputs race).
+ * The sequence is captured once
  * into a CUDA graph and replayed when the same batch (same pointers and
  * shapes) is run again.  With lnf_config.autotune set, the first batch times
  * the candidate z lengths of the specialised kernels' work items per job class

@@ -280,6 +280,7 @@ extern "C" void lnf_destroy(lnf_ctx *ctx)
     lnf_serve_shutdown(ctx);
     cudaStreamSynchronize(ctx->stream);
     lnf_batch_cache_clear(ctx);
+    lnf_batch_streams_free(ctx);
     free_scratch(ctx->vs);
     for (auto &vs : ctx->pool)
         free_scratch(vs);
@@ -557,14 +558,6 @@ size_t lnf_pitched_row(const void *in, const int64_t dims[3], int dtype)
     if ((reinterpret_cast<uintptr_t>(in) & 15) == 0 && row % 16 == 0)
         return 0;
     return (row + 15) / 16 * 16;
-}
-
-lnf_status lnf_copy_pitched(lnf_ctx *ctx, void *dst, size_t prow, const void *in, const int64_t dims[3], int dtype,
-                            cudaStream_t st)
-{
-    const size_t row = (size_t)dims[0] * esize(dtype);
-    CK(cudaMemcpy2DAsync(dst, prow, in, row, row, (size_t)dims[1] * dims[2], cudaMemcpyDeviceToDevice, st));
-    return LNF_OK;
 }
 
 // A whole-volume input that TMA cannot address (an unaligned base or a row

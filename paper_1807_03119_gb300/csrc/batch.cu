@@ -4,8 +4,14 @@
 // the gate-first kernel, which takes the job on the device while few voxels
 // pass the gate; inputs TMA cannot address first get one padded copy per
 // volume), all other jobs share ONE persistent launch of the generic kernel
-// over their flattened tile list.  The whole sequence is captured once into a
-// CUDA graph and replayed for the same batch.
+// over their flattened tile list.  The specialised launches form one chain per
+// input volume (its padded copy, then its jobs in order), and the chains run
+// side by side on LNF_BATCH_CHAINS streams forked from the caller's stream
+// after the parameter launch and joined back before the generic launch: a
+// volume of a few million voxels gives a persistent grid only one or two work
+// items per CTA, and one chain's tail is the next chain's start.  Each job has
+// its own work counters.  The whole sequence is captured once into a CUDA graph
+// and replayed for the same batch.
 //
 // The autotuner (lnf_config.autotune) times the candidates on the first batch
 // it sees: for each class of specialised jobs (dtype, filter, radius), the z
@@ -18,6 +24,7 @@
 #include "lnf_ctx.h"
 
 #include <algorithm>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <memory>
@@ -109,6 +116,49 @@ static lnf_status alloc_stage(lnf_ctx *ctx, const lnf_job *jobs, int n, std::vec
     return LNF_OK;
 }
 
+// The batch streams, their fork / join events and the per-job work counters,
+// made once per context outside any capture; if any of them cannot be made the
+// batch runs as one chain on the context's stream.
+static void batch_streams(lnf_ctx *ctx)
+{
+    if (ctx->bfork)
+        return;
+    bool ok = cudaMalloc(&ctx->d_bcounter, sizeof(u32) * 2 * LNF_MAX_PACK) == cudaSuccess;
+    for (int k = 0; ok && k < LNF_BATCH_STREAMS; ++k)
+        ok = cudaStreamCreateWithFlags(&ctx->bstream[k], cudaStreamNonBlocking) == cudaSuccess &&
+             cudaEventCreateWithFlags(&ctx->bjoin[k], cudaEventDisableTiming) == cudaSuccess;
+    cudaEvent_t fork = nullptr;
+    ok = ok && cudaEventCreateWithFlags(&fork, cudaEventDisableTiming) == cudaSuccess;
+    if (ok) {
+        ctx->bfork = fork;
+        ctx->bchains = LNF_BATCH_CHAINS;
+        // test hook: the number of chains side by side (1..LNF_BATCH_STREAMS)
+        if (const char *e = std::getenv("LNF_BATCH_CHAINS"))
+            ctx->bchains = std::max(1, std::min(LNF_BATCH_STREAMS, std::atoi(e)));
+        return;
+    }
+    cudaGetLastError();
+    lnf_batch_streams_free(ctx);
+}
+
+void lnf_batch_streams_free(lnf_ctx *ctx)
+{
+    for (int k = 0; k < LNF_BATCH_STREAMS; ++k) {
+        if (ctx->bstream[k])
+            cudaStreamDestroy(ctx->bstream[k]);
+        if (ctx->bjoin[k])
+            cudaEventDestroy(ctx->bjoin[k]);
+        ctx->bstream[k] = nullptr;
+        ctx->bjoin[k] = nullptr;
+    }
+    if (ctx->bfork)
+        cudaEventDestroy(ctx->bfork);
+    ctx->bfork = nullptr;
+    ctx->bchains = 0;
+    cudaFree(ctx->d_bcounter);
+    ctx->d_bcounter = nullptr;
+}
+
 static bool same_jobs(const std::vector<lnf_job> &a, const lnf_job *b, int n)
 {
     return (int)a.size() == n && std::memcmp(a.data(), b, sizeof(lnf_job) * n) == 0;
@@ -183,17 +233,39 @@ lnf_status lnf_enqueue_batch(lnf_ctx *ctx, const lnf_job *jobs, int n, int zchun
     CK(lnf_launch_stats_batched(sp, per, st));
     CK(lnf_launch_params_batched(sp, lnf_param_cfg(ctx), st));
 
-    // padded copies of the inputs TMA cannot address
+    // the job chains: one per input volume, side by side on the batch streams
+    // (volume v on stream v % bchains) when the context has them, each
+    // job with its own work counters; else one chain on `st`
+    const bool fork = ctx->bfork != nullptr && n > 1;
+    auto chain = [&](int v) { return fork ? ctx->bstream[v % ctx->bchains] : st; };
+    if (fork) {
+        CK(cudaEventRecord(ctx->bfork, st));
+        for (int k = 0; k < ctx->bchains; ++k)
+            CK(cudaStreamWaitEvent(ctx->bstream[k], ctx->bfork, 0));
+    }
+
+    // padded copies of the inputs TMA cannot address, at the head of their chains;
+    // the copy of a volume whose only job is a whole volume of the paper's filter
+    // goes between that job's gate-first and ring kernels instead, where it is
+    // skipped on the device while the gate-first kernel takes the volume
+    std::vector<int> jobs_of(vols.size(), 0);
+    for (int i = 0; i < n; ++i)
+        ++jobs_of[vol_of[i]];
     std::vector<int64_t> pitch(vols.size(), 0);
+    std::vector<char> deferred(vols.size(), 0);
     for (size_t v = 0; stage && v < vols.size(); ++v) {
         if (!(*stage)[v])
             continue;
         int first = (int)(std::find(vol_of.begin(), vol_of.end(), (int)v) - vol_of.begin());
         const lnf_job &j = jobs[first];
         const size_t prow = lnf_pitched_row(j.in, j.dims, j.dtype);
-        if ((s = lnf_copy_pitched(ctx, (*stage)[v], prow, j.in, j.dims, j.dtype, st)) != LNF_OK)
-            return s;
         pitch[v] = (int64_t)(prow / (j.dtype == LNF_U8 ? 1 : 2));
+        if (jobs_of[v] == 1 && j.filter_id == LNF_OURS && whole_volume(j)) {
+            deferred[v] = 1;
+            continue;
+        }
+        if ((s = lnf_copy_pitched(ctx, (*stage)[v], prow, j.in, j.dims, j.dtype, chain((int)v))) != LNF_OK)
+            return s;
     }
 
     FilterPack &pk = ctx->pack;
@@ -205,11 +277,13 @@ lnf_status lnf_enqueue_batch(lnf_ctx *ctx, const lnf_job *jobs, int n, int zchun
     ctx->zchunk = zchunk;
     for (int i = 0; i < n; ++i) {
         const lnf_job &j = jobs[i];
+        const int v = vol_of[i];
+        const cudaStream_t sk = chain(v);
         u64 *oh = nullptr;
         const u32 levels = j.dtype == LNF_U8 ? LNF_LEVELS_U8 : LNF_LEVELS_U16;
         if (j.d_entropy) {
             oh = ctx->out_hist + (size_t)i * LNF_LEVELS_U16;
-            CK(lnf_launch_zero(oh, levels, st));
+            CK(lnf_launch_zero(oh, levels, sk));
             const int k = ep.count++;
             ep.hist[k] = oh;
             ep.levels[k] = levels;
@@ -217,20 +291,26 @@ lnf_status lnf_enqueue_batch(lnf_ctx *ctx, const lnf_job *jobs, int n, int zchun
                                         : (u64)j.dims[0] * j.dims[1] * j.dims[2];
             ep.H[k] = j.d_entropy;
         }
-        const int v = vol_of[i];
         const bool fast = !ctx->no_fast && lnf_fast_covers(j.filter_id, j.radius, ctx->cfg.cluster_offset);
         const bool staged = fast && stage && (*stage)[v];
         s = lnf_make_job(ctx, pk, g, j.filter_id, j.radius, staged ? (*stage)[v] : j.in, j.out, j.dims, j.dtype,
                          j.roi_origin, j.roi_dims, ctx->pool[v], oh, staged ? pitch[v] : 0);
         int handled = 0;
+        PitchedCopy pc{deferred[v] ? (*stage)[v] : nullptr, (size_t)pitch[v] * (j.dtype == LNF_U8 ? 1 : 2), j.in,
+                       j.dims, j.dtype, ctx->pool[v].prm, false};
         if (s == LNF_OK && fast) {
             FilterJob &fj = pk.jobs[g];
             // the gate-first kernel reads the caller's dense volume, not a padded copy
             fj.orig = j.in;
             ctx->fast_zlen = zlen_for(ctx, j, zlen);
-            s = lnf_fast_dispatch(ctx, fj, fj.tmap_idx >= 0 ? &pk.tmaps[fj.tmap_idx] : nullptr, st, &handled,
-                                  nullptr, 1);
+            s = lnf_fast_dispatch(ctx, fj, fj.tmap_idx >= 0 ? &pk.tmaps[fj.tmap_idx] : nullptr, sk, &handled,
+                                  fork ? ctx->d_bcounter + 2 * i : nullptr, 1,
+                                  fork ? ctx->d_bcounter + 2 * i + 1 : nullptr, deferred[v] ? &pc : nullptr);
         }
+        // a deferred copy the dispatch did not enqueue (no specialised launch):
+        // the generic kernel may read it
+        if (s == LNF_OK && deferred[v] && !pc.done)
+            s = lnf_copy_pitched(ctx, pc.dst, pc.prow, pc.src, pc.dims, pc.dtype, sk);
         if (s != LNF_OK) {
             ctx->zchunk = zsave;
             ctx->fast_zlen = lsave;
@@ -241,6 +321,13 @@ lnf_status lnf_enqueue_batch(lnf_ctx *ctx, const lnf_job *jobs, int n, int zchun
     }
     ctx->zchunk = zsave;
     ctx->fast_zlen = lsave;
+    // the chains join before the generic launch (its jobs may read padded copies)
+    // and the entropies (every job's output histogram)
+    if (fork)
+        for (int k = 0; k < ctx->bchains; ++k) {
+            CK(cudaEventRecord(ctx->bjoin[k], ctx->bstream[k]));
+            CK(cudaStreamWaitEvent(st, ctx->bjoin[k], 0));
+        }
     pk.n_jobs = g;
     if (g > 0 && (s = lnf_run_pack(ctx, pk, 1, st)) != LNF_OK)
         return s;
@@ -395,6 +482,7 @@ extern "C" lnf_status lnf_filter_batch(lnf_ctx *ctx, const lnf_job *jobs, int n_
         return ss;
     if ((ss = alloc_stage(ctx, jobs, n_jobs, e->stage)) != LNF_OK)
         return ss;
+    batch_streams(ctx);
     if (ctx->cfg.autotune)
         autotune(ctx, jobs, n_jobs, e->stage);
     const int zc = ctx->tuned_zchunk ? ctx->tuned_zchunk : 64;

@@ -796,7 +796,7 @@ bool lnf_fast_covers(int filter, int radius, int offset)
 }
 
 lnf_status lnf_fast_dispatch(lnf_ctx *ctx, const FilterJob &job, const CUtensorMap *tmap, cudaStream_t stream,
-                             int *handled, u32 *counter, int allow_gate)
+                             int *handled, u32 *counter, int allow_gate, u32 *gate_counter, PitchedCopy *pre)
 {
     *handled = 0;
     if (!tmap || job.aniso || !lnf_fast_covers(job.filter, job.radius, job.offset))
@@ -821,12 +821,19 @@ lnf_status lnf_fast_dispatch(lnf_ctx *ctx, const FilterJob &job, const CUtensorM
         outs[job.filter] = job.out;
         hists[job.filter] = job.out_hist;
         const int rec = lnf_prof_begin(ctx, stream);   // the gate kernels alone (counted by the caller)
-        s = lnf_gate_launch(ctx, job, outs, hists, stream, &own);
+        s = lnf_gate_launch(ctx, job, outs, hists, stream, &own, gate_counter);
         lnf_prof_end(ctx, rec, names[job.filter], stream, 0);
         if (s != LNF_OK)
             return s;
     }
     const int gated = in_multi || own ? 1 : 0;
+    if (pre) {
+        s = lnf_copy_pitched(ctx, pre->dst, pre->prow, pre->src, pre->dims, pre->dtype, stream,
+                             own ? pre->prm : nullptr);
+        if (s != LNF_OK)
+            return s;
+        pre->done = true;
+    }
     if (job.filter != LNF_OURS) {
         s = lnf_fast2_dispatch(ctx, job, tmap, stream, handled, counter, gated);
     } else {

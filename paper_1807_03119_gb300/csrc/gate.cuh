@@ -663,10 +663,11 @@ lnf_status gate_eloc_by_radius(lnf_ctx *ctx, int radius, const GateArgs &a, cuda
 }
 
 // The gate kernel for one job (outs / hists by filter id; `eloc`: the entropy
-// filter with the cube's own probabilities, its output in the entropy slot).
+// filter with the cube's own probabilities, its output in the entropy slot;
+// `counter`: the chunk counter, null for the context's own).
 template <typename T>
 lnf_status gate_dispatch_t(lnf_ctx *ctx, const FilterJob &j, void *const outs[5], u64 *const hists[5],
-                           cudaStream_t st, int *handled, bool eloc = false)
+                           cudaStream_t st, int *handled, bool eloc = false, u32 *counter = nullptr)
 {
     const u64 n = (u64)j.nx * j.ny * j.nz;
     if (n >= (1ull << 32) || j.pitch != j.nx || reinterpret_cast<uintptr_t>(j.in) % 16 != 0)
@@ -687,7 +688,7 @@ lnf_status gate_dispatch_t(lnf_ctx *ctx, const FilterJob &j, void *const outs[5]
     a.n = n;
     a.prm = j.prm;
     a.lut = j.lut;
-    a.counter = ctx->d_counter + 14;
+    a.counter = counter ? counter : ctx->d_counter + 14;
     a.err = ctx->d_err;
     const bool ours = outs[LNF_OURS] != nullptr;
     const bool cube = outs[0] || outs[1] || outs[2] || outs[3];

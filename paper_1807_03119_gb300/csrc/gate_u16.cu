@@ -3,7 +3,7 @@
 #include "gate.cuh"
 
 lnf_status lnf_gate_launch_u8(lnf_ctx *ctx, const FilterJob &j, void *const outs[5], u64 *const hists[5],
-                              cudaStream_t st, int *handled, bool eloc);
+                              cudaStream_t st, int *handled, bool eloc, u32 *counter);
 
 bool lnf_gate_covers(const FilterJob &j, int filter)
 {
@@ -19,7 +19,7 @@ bool lnf_gate_covers(const FilterJob &j, int filter)
 }
 
 lnf_status lnf_gate_launch(lnf_ctx *ctx, const FilterJob &j, void *const outs[5], u64 *const hists[5],
-                           cudaStream_t st, int *handled)
+                           cudaStream_t st, int *handled, u32 *counter)
 {
     *handled = 0;
     for (int f = 0; f < 5; ++f)
@@ -32,8 +32,8 @@ lnf_status lnf_gate_launch(lnf_ctx *ctx, const FilterJob &j, void *const outs[5]
         jd.pitch = j.nx;
     }
     if (j.dtype == LNF_U8)
-        return lnf_gate_launch_u8(ctx, jd, outs, hists, st, handled, false);
-    return gatek::gate_dispatch_t<uint16_t>(ctx, jd, outs, hists, st, handled);
+        return lnf_gate_launch_u8(ctx, jd, outs, hists, st, handled, false, counter);
+    return gatek::gate_dispatch_t<uint16_t>(ctx, jd, outs, hists, st, handled, false, counter);
 }
 
 lnf_status lnf_gate_launch_eloc(lnf_ctx *ctx, const FilterJob &j, cudaStream_t st, int *handled)
@@ -49,6 +49,6 @@ lnf_status lnf_gate_launch_eloc(lnf_ctx *ctx, const FilterJob &j, cudaStream_t s
         jd.pitch = j.nx;
     }
     if (j.dtype == LNF_U8)
-        return lnf_gate_launch_u8(ctx, jd, outs, hists, st, handled, true);
+        return lnf_gate_launch_u8(ctx, jd, outs, hists, st, handled, true, nullptr);
     return gatek::gate_dispatch_t<uint16_t>(ctx, jd, outs, hists, st, handled, true);
 }

@@ -3,7 +3,7 @@
 #include "gate.cuh"
 
 lnf_status lnf_gate_launch_u8(lnf_ctx *ctx, const FilterJob &j, void *const outs[5], u64 *const hists[5],
-                              cudaStream_t st, int *handled, bool eloc)
+                              cudaStream_t st, int *handled, bool eloc, u32 *counter)
 {
-    return gatek::gate_dispatch_t<uint8_t>(ctx, j, outs, hists, st, handled, eloc);
+    return gatek::gate_dispatch_t<uint8_t>(ctx, j, outs, hists, st, handled, eloc, counter);
 }

@@ -63,6 +63,8 @@ struct FaultPlan {
 
 struct BatchEntry;
 // batch.cu
+#define LNF_BATCH_STREAMS 8   // side streams made per context
+#define LNF_BATCH_CHAINS 8    // chains side by side by default
 struct Server;          // serve.cu
 
 struct lnf_ctx {
@@ -85,6 +87,15 @@ struct lnf_ctx {
     u32 *d_counter = nullptr;   // work counters: [0] generic, [1..4] serving streams (generic),
                                 // [8] paper's filter, [9] comparison filters, [10..13] serving
                                 // streams (specialised), [14] fused kernel, [15] the self-test's status word
+    // batched launches: the side streams that carry a batch's job chains side by
+    // side (one chain per input volume, volume v on stream v % bchains), the fork /
+    // join events, and two work counters per job (ring kernel, gate-first kernel)
+    // so that chains running at once share none; made on first use
+    int bchains = 0;
+    cudaStream_t bstream[LNF_BATCH_STREAMS] = {};
+    cudaEvent_t bfork = nullptr;
+    cudaEvent_t bjoin[LNF_BATCH_STREAMS] = {};
+    u32 *d_bcounter = nullptr;      // 2 x LNF_MAX_PACK
     double *d_ent_part = nullptr;   // entropy reduction partials (LNF_ENT_SPLIT x LNF_MAX_ENT)
     u32 *d_ent_done = nullptr;      // entropy reduction tickets (LNF_MAX_ENT)
     PFN_encodeTiled encode = nullptr;
@@ -166,9 +177,25 @@ lnf_status lnf_run_one(lnf_ctx *ctx, int filter, int radius, const void *in, voi
 // Row length in bytes of the padded copy of an input TMA cannot address (0: the
 // input itself is addressable: 16-byte-aligned base and row length)
 size_t lnf_pitched_row(const void *in, const int64_t dims[3], int dtype);
-// Copy `in` into `dst` with rows padded to `prow` bytes (on `st`)
+// pitch.cu: copy `in` into `dst` (16-byte aligned) with rows padded to `prow`
+// bytes (a multiple of 16), on `st`; with `skip_prm` the copy kernel returns at
+// once while the gate-first kernel takes the volume (lnf_gate_mode(*skip_prm))
 lnf_status lnf_copy_pitched(lnf_ctx *ctx, void *dst, size_t prow, const void *in, const int64_t dims[3], int dtype,
-                            cudaStream_t st);
+                            cudaStream_t st, const DevParams *skip_prm = nullptr);
+// A padded copy that lnf_fast_dispatch enqueues between its job's gate-first and
+// ring kernels (`done` set once enqueued).  Where the gate-first kernel was
+// launched, the copy is skipped on the device while it takes the volume: only
+// for a volume whose ring kernels are all launched beside the gate-first kernel
+// (the caller's promise), since those return at once in that case.
+struct PitchedCopy {
+    void *dst;
+    size_t prow;
+    const void *src;
+    const int64_t *dims;
+    int dtype;
+    const DevParams *prm;
+    bool done;
+};
 // profiling helpers (api.cu): bracket one launch (or a group of `count` launches)
 int lnf_prof_begin(lnf_ctx *ctx, cudaStream_t st);
 void lnf_prof_end(lnf_ctx *ctx, int rec, const char *name, cudaStream_t st, int count);
@@ -178,10 +205,13 @@ bool lnf_fast_covers(int filter, int radius, int offset);
 // fast.cu: run the job through a specialised kernel if one covers it (*handled = the
 // number of kernels launched: 1, or 2 with the gate-first kernel beside, else 0);
 // `counter` is the launch's work counter (null: the context's own, for its stream)
-// `allow_gate`: the gate-first kernel may take a whole-volume job (plain calls on
-// the context's stream only: it uses the context's chunk counter)
+// `allow_gate`: the gate-first kernel may take a whole-volume job, with
+// `gate_counter` as its chunk counter (null: the context's own, which only calls
+// on the context's stream may use); `pre`: a padded copy of the job's input to
+// enqueue after the gate-first kernel and before the ring kernel
 lnf_status lnf_fast_dispatch(lnf_ctx *ctx, const FilterJob &job, const CUtensorMap *tmap, cudaStream_t stream,
-                             int *handled, u32 *counter = nullptr, int allow_gate = 0);
+                             int *handled, u32 *counter = nullptr, int allow_gate = 0,
+                             u32 *gate_counter = nullptr, PitchedCopy *pre = nullptr);
 // `gated`: the gate-first kernel was launched for this job (the ring kernel
 // returns at once when that one does the work)
 lnf_status lnf_fast2_dispatch(lnf_ctx *ctx, const FilterJob &job, const CUtensorMap *tmap, cudaStream_t stream,
@@ -192,14 +222,15 @@ lnf_status lnf_fast2_box(lnf_ctx *ctx, const FilterJob &job, cudaStream_t stream
 // gate.cu: whether the gate-first kernel covers `filter` on the job's volume (a
 // whole volume, isotropic radius 1..4, the paper's filter at cluster offset 1),
 // and its launch for the filters whose outputs are given (outs / hists indexed
-// by filter id 0..4, null where not requested); *handled = 1 if launched
+// by filter id 0..4, null where not requested); *handled = 1 if launched;
+// `counter`: the launch's chunk counter (null: the context's own, for its stream)
 bool lnf_gate_covers(const FilterJob &j, int filter);
 // the entropy filter with local probabilities (LNF_ENTROPY_LOCAL) of a whole
 // volume through the gate-first kernel; *handled = 1 if launched (the generic
 // kernel then skips the job while the gate takes the volume: FilterJob::gated)
 lnf_status lnf_gate_launch_eloc(lnf_ctx *ctx, const FilterJob &j, cudaStream_t st, int *handled);
 lnf_status lnf_gate_launch(lnf_ctx *ctx, const FilterJob &j, void *const outs[5], u64 *const hists[5],
-                           cudaStream_t st, int *handled);
+                           cudaStream_t st, int *handled, u32 *counter = nullptr);
 // render.cu: one ray per pixel (see lnf_render)
 cudaError_t lnf_launch_render(const void *vol, const int64_t dims[3], int64_t pitch, int dtype, int view,
                               int filter, int radius, int offset, const DevParams *prm, const u32 *lut,
@@ -212,5 +243,7 @@ cudaError_t lnf_launch_f32_dequantize(const uint16_t *q, u64 n, const u32 *range
                                       cudaStream_t st);
 // batch.cu
 void lnf_batch_cache_clear(lnf_ctx *ctx);
+// the batch streams, events and per-job counters (made on a context's first batch)
+void lnf_batch_streams_free(lnf_ctx *ctx);
 // serve.cu
 void lnf_serve_shutdown(lnf_ctx *ctx);

@@ -169,6 +169,30 @@ def test_forced_generic_matches(lnf, monkeypatch):
                             f"generic filter {f} r={r}")
 
 
+@pytest.mark.parametrize("dt,off", [("u8", 0), ("u8", 1), ("u8", 7), ("u8", 13), ("u16", 0), ("u16", 1),
+                                    ("u16", 3)])
+def test_padded_copy_of_unaligned_inputs(lnf, dt, off):
+    # inputs TMA cannot address (row lengths that are not a multiple of 16 bytes,
+    # bases `off` elements past a 16-byte boundary) are copied into padded rows
+    # before the plane-ring kernels read them; no threshold, so those kernels do
+    # the work.  Rows of 530 and 301 elements span several 512-byte segments of
+    # the copy kernel; with an odd base every row starts at another offset
+    # within its 16-byte block
+    for dims, seed in (((530, 9, 5), 71), ((37, 23, 19), 72), ((301, 7, 6), 73)):
+        vol = phantoms.random_volume(dims, seed, dt)
+        n = vol.size
+        padded = np.zeros(n + 16, vol.dtype)
+        padded[off:off + n] = vol.ravel()
+        buf = dev(padded)
+        t = buf[off:off + n].view(vol.shape)
+        assert (t.data_ptr() % 16 == 0) == (off == 0)
+        with lnf.Context(threshold_mode=lnf.THRESH_NONE) as c:
+            for f in (oracle.OURS, oracle.MEAN, oracle.SIGMA):
+                got = host(c.filter_volume(t, f, 2))
+                want = oracle.filter_volume(vol, f, 2, cfg=oracle_cfg(threshold_mode=2))
+                assert_same(got, want, f"{dt} base +{off} dims {dims} filter {f}")
+
+
 @pytest.mark.parametrize("dims", [(1, 1, 1), (1, 1, 9), (9, 1, 1), (1, 7, 1), (3, 2, 1), (17, 1, 33)])
 @pytest.mark.parametrize("dt", ["u8", "u16"])
 def test_degenerate_shapes(ctx, dims, dt):
@@ -342,6 +366,40 @@ def test_batched_mixed(lnf, autotune):
                 assert cl["zlen"] in (4, 8, 16, 32) and all(v > 0 for v in cl["ms"].values()), cl
         else:
             assert not tun["classes"] and tun["generic_zchunk"] == 0
+
+
+@pytest.mark.parametrize("autotune", [False, True])
+def test_batched_chains_side_by_side(lnf, autotune):
+    # eight whole volumes of the uneven batch workload (uint8 blobs and uint16
+    # insects, 2.9-4.0 M voxels): 7, 11 and 46 pass few enough voxels for the
+    # gate-first kernel to take them, the others go to the plane-ring kernels;
+    # the batch runs them as job chains side by side on several streams, each
+    # job with its own work counters; volume 36 also carries a mean-filter job
+    # on the same chain
+    pick = (4, 7, 11, 46, 19, 36, 27, 51)
+    specs = [s for s in phantoms.batch_volume_specs(64) if s["index"] in pick]
+    vols = [phantoms.batch_volume(s) for s in specs]
+    with lnf.Context(autotune=autotune) as c:
+        tv = [dev(v) for v in vols]
+        jobs, wants = [], []
+        Hs = torch.zeros(len(specs) + 1, dtype=torch.float64, device="cuda")
+        for s, v, t in zip(specs, vols, tv):
+            prm = oracle.derive_params(oracle.stats(v), s["radius"])
+            fs = (oracle.OURS, oracle.MEAN) if s["index"] == 36 else (oracle.OURS,)
+            for f in fs:
+                k = len(jobs)
+                jobs.append({"in": t, "out": torch.empty_like(t), "filter": f, "radius": s["radius"],
+                             "entropy": Hs[k:k + 1]})
+                wants.append(oracle.filter_volume(v, f, s["radius"], params=prm))
+        for rep in range(2):   # capture, then replay
+            for j in jobs:
+                j["out"].fill_(7)
+            c.filter_batch(jobs)
+            Hh = host(Hs)
+            for i, (j, w) in enumerate(zip(jobs, wants)):
+                assert_same(host(j["out"]), w, f"batch job {i} rep {rep}")
+                hw = oracle.image_entropy(oracle.histogram(w))
+                assert abs(Hh[i] - hw) <= H_TOL * max(1.0, hw), (i, Hh[i], hw)
 
 
 def test_invalid_arguments(ctx, lnf):
