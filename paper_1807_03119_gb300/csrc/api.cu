@@ -608,9 +608,21 @@ lnf_status lnf_run_one(lnf_ctx *ctx, int filter, int radius, const void *in, voi
         return lnf_fail(ctx, LNF_ECUDA, "injected fault: filter launch failed");
     LNF_RANGE(filter_name(filter));
     const int rec = lnf_prof_begin(ctx, stream);
+    int sparse = 0;
     if (!ctx->no_fast) {
         int handled = 0;
         pk.jobs[0].orig = orig;
+        if (lnf_sparse_covers(filter, radius) && !ctx->no_gate && pk.jobs[0].tmap_idx >= 0 && !pk.jobs[0].aniso) {
+            // the tap kernel takes the job while few voxels pass the gate (it
+            // evaluates the listed voxels alone); the generic kernel below does
+            // it otherwise
+            if ((s = lnf_fast2_dispatch(ctx, pk.jobs[0], &pk.tmaps[pk.jobs[0].tmap_idx], stream, &sparse, nullptr,
+                                        2)) != LNF_OK) {
+                lnf_prof_end(ctx, rec, filter_name(filter), stream, 1);
+                return s;
+            }
+            pk.jobs[0].gated = sparse ? 1 : 0;
+        }
         if (filter == LNF_ENTROPY_LOCAL && !ctx->no_gate && lnf_gate_covers(pk.jobs[0], filter)) {
             // the gate-first kernel takes the volume while few voxels pass; the
             // generic kernel below does it otherwise
@@ -629,7 +641,7 @@ lnf_status lnf_run_one(lnf_ctx *ctx, int filter, int radius, const void *in, voi
         }
     }
     s = lnf_run_pack(ctx, pk, 0, stream);
-    lnf_prof_end(ctx, rec, filter_name(filter), stream, 1);
+    lnf_prof_end(ctx, rec, filter_name(filter), stream, 1 + sparse);
     return s;
 }
 
@@ -655,7 +667,7 @@ extern "C" lnf_status lnf_filter_volume(lnf_ctx *ctx, int filter_id, int radius,
         return s;
     const void *src = in;
     int64_t pitch = 0;
-    if (lnf_fast_covers(filter_id, radius, ctx->cfg.cluster_offset) &&
+    if ((lnf_fast_covers(filter_id, radius, ctx->cfg.cluster_offset) || lnf_sparse_covers(filter_id, radius)) &&
         (s = stage_input(ctx, in, dims, dtype, ctx->stream, &src, &pitch)) != LNF_OK)
         return s;
     return lnf_run_one(ctx, filter_id, radius, src, out, dims, dtype, nullptr, nullptr, ctx->vs, nullptr,
@@ -795,7 +807,8 @@ static lnf_status multi_impl(lnf_ctx *ctx, int radius, const void *in, const int
     // one padded copy serves every filter a specialised kernel covers
     bool any_fast = false;
     for (int i = 0; i < n; ++i)
-        any_fast = any_fast || lnf_fast_covers(filter_ids[i], radius, ctx->cfg.cluster_offset);
+        any_fast = any_fast || lnf_fast_covers(filter_ids[i], radius, ctx->cfg.cluster_offset) ||
+                   lnf_sparse_covers(filter_ids[i], radius);
     const void *src = in;
     int64_t pitch = 0;
     if (any_fast && (s = stage_input(ctx, in, dims, dtype, st, &src, &pitch)) != LNF_OK)
@@ -841,7 +854,8 @@ static lnf_status multi_impl(lnf_ctx *ctx, int radius, const void *in, const int
     int done = 0;
     for (int i = 0; i < n; ++i) {
         u64 *oh = d_entropy ? ctx->out_hist + (size_t)i * LNF_LEVELS_U16 : nullptr;
-        const bool f = lnf_fast_covers(filter_ids[i], radius, ctx->cfg.cluster_offset);
+        const bool f = lnf_fast_covers(filter_ids[i], radius, ctx->cfg.cluster_offset) ||
+                       lnf_sparse_covers(filter_ids[i], radius);
         s = lnf_run_one(ctx, filter_ids[i], radius, f ? src : in, outs[i], dims, dtype, nullptr, nullptr, ctx->vs,
                         oh, st, f ? pitch : 0, nullptr, nullptr, in);
         if (s == LNF_OK && after && cudaEventRecord(after[i], st) != cudaSuccess)

@@ -781,13 +781,21 @@ lnf_status launch(lnf_ctx *ctx, const FilterJob &j, cudaStream_t st, u64 *out_hi
 
 }  // namespace
 
+bool lnf_sparse_covers(int filter, int radius)
+{
+    // sigma at r = 3..4: the tap kernel only while few voxels pass the gate (it
+    // evaluates the listed voxels alone), the generic kernel beside it otherwise
+    return filter == LNF_SIGMA && radius >= 3 && radius <= 4;
+}
+
 bool lnf_fast_covers(int filter, int radius, int offset)
 {
     if (radius < 1 || radius > 4)
         return false;
     switch (filter) {
     case LNF_OURS: return offset == 1;
-    case LNF_SIGMA: return radius <= 2;   // r = 3 (343 taps per voxel) runs faster on the generic kernel
+    case LNF_SIGMA: return radius <= 2;   // dense r = 3..4 (343, 729 taps per voxel): the generic kernel is
+                                          // faster; sparse ones take the tap kernel (lnf_sparse_covers)
     case LNF_MEAN:
     case LNF_ENTROPY:
     case LNF_OKADA: return true;

@@ -133,7 +133,9 @@ struct Args2 {
     u32 *err;
     u32 one;        // always 1; a multiplier the compiler cannot fold, so that adds
                     // written as multiply-adds issue on the FMA pipe (see tap_items)
-    int gated;      // 1: launched beside the gate-first kernel, which may take the job (lnf_gate_mode)
+    int gated;      // 1: launched beside the gate-first kernel, which takes the job while few voxels
+                    // pass the gate (lnf_gate_mode); 2: launched beside the generic kernel, which
+                    // takes the job unless few voxels pass
 };
 
 // shared histogram of nonzero outputs (window [hbase, hbase + bins)), zero count by difference
@@ -255,8 +257,10 @@ __global__ void __launch_bounds__(kThreads, (K2Smem<T, R, FILTER>::BOX && R > 2)
     k_fast2(const __grid_constant__ CUtensorMap tmap, const Args2 a)
 {
     typedef K2Smem<T, R, FILTER> S;
-    if (a.gated && lnf_gate_mode(*a.prm))
+    if (a.gated == 1 && lnf_gate_mode(*a.prm))
         return;   // few voxels pass the gate: the gate-first kernel does the work
+    if (a.gated == 2 && !lnf_gate_mode(*a.prm))
+        return;   // many voxels pass: the generic kernel launched beside does the work
     extern __shared__ __align__(128) unsigned char smem_raw[];
     unsigned char *smem = smem_raw + ((128 - (lnfdev::smem_u32(smem_raw) & 127)) & 127);
     __shared__ int s_item, s_abort;

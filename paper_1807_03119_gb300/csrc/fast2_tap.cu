@@ -518,7 +518,9 @@ lnf_status lnf_fast2_dispatch(lnf_ctx *ctx, const FilterJob &job, const CUtensor
                               int *handled, u32 *counter, int gated)
 {
     *handled = 0;
-    if (!tmap || job.aniso || job.filter == LNF_OURS || !lnf_fast_covers(job.filter, job.radius, job.offset))
+    if (!tmap || job.aniso || job.filter == LNF_OURS)
+        return LNF_OK;
+    if (gated == 2 ? !lnf_sparse_covers(job.filter, job.radius) : !lnf_fast_covers(job.filter, job.radius, job.offset))
         return LNF_OK;
     const bool u8 = job.dtype == LNF_U8;
     switch (job.filter) {

@@ -202,6 +202,10 @@ void lnf_prof_end(lnf_ctx *ctx, int rec, const char *name, cudaStream_t st, int 
 // fast.cu: whether a specialised kernel covers this filter, radius and cluster
 // offset (on an input TMA can address)
 bool lnf_fast_covers(int filter, int radius, int offset);
+// fast.cu: whether a specialised kernel takes this filter and radius only while
+// few voxels pass the gate (launched with gated = 2 beside the generic kernel,
+// whose job is marked FilterJob::gated)
+bool lnf_sparse_covers(int filter, int radius);
 // fast.cu: run the job through a specialised kernel if one covers it (*handled = the
 // number of kernels launched: 1, or 2 with the gate-first kernel beside, else 0);
 // `counter` is the launch's work counter (null: the context's own, for its stream)
@@ -212,8 +216,9 @@ bool lnf_fast_covers(int filter, int radius, int offset);
 lnf_status lnf_fast_dispatch(lnf_ctx *ctx, const FilterJob &job, const CUtensorMap *tmap, cudaStream_t stream,
                              int *handled, u32 *counter = nullptr, int allow_gate = 0,
                              u32 *gate_counter = nullptr, PitchedCopy *pre = nullptr);
-// `gated`: the gate-first kernel was launched for this job (the ring kernel
-// returns at once when that one does the work)
+// `gated`: 1 if the gate-first kernel was launched for this job (the ring kernel
+// returns at once when that one does the work); 2 for a job lnf_sparse_covers
+// names (the kernel returns at once unless few voxels pass)
 lnf_status lnf_fast2_dispatch(lnf_ctx *ctx, const FilterJob &job, const CUtensorMap *tmap, cudaStream_t stream,
                               int *handled, u32 *counter = nullptr, int gated = 0);
 // fast2_box.cu: the mean / entropy-filter job through its box kernel

@@ -229,7 +229,16 @@ lnf_status launch_wave(Server *s, Wave *w)
             return lnf_fail(ctx, LNF_ECUDA, "injected fault: filter launch failed");
         int handled = 0;
         if (!ctx->no_fast) {
-            const FilterJob &j = pk.jobs[0];
+            FilterJob &j = pk.jobs[0];
+            // sigma at r = 3..4: the tap kernel while few voxels pass the gate,
+            // the generic kernel (its job marked gated) otherwise
+            if (lnf_sparse_covers(j.filter, j.radius) && !ctx->no_gate && j.tmap_idx >= 0 && !j.aniso) {
+                int sparse = 0;
+                r = lnf_fast2_dispatch(ctx, j, &pk.tmaps[j.tmap_idx], st, &sparse, fast_counter, 2);
+                if (r != LNF_OK)
+                    return r;
+                j.gated = sparse ? 1 : 0;
+            }
             r = lnf_fast_dispatch(ctx, j, j.tmap_idx >= 0 ? &pk.tmaps[j.tmap_idx] : nullptr, st, &handled,
                                   fast_counter);
             if (r != LNF_OK)

@@ -92,6 +92,45 @@ def test_alone_and_in_the_mix(lnf):
         assert st["queued"] == 0 and st["inflight"] == 0
 
 
+def _sparse_u16(dims, seed):
+    """12-bit noise around 400 with a small bright ellipsoid and 0.1% salt: few
+    voxels pass the Otsu gate."""
+    nx, ny, nz = dims
+    rng = np.random.default_rng(seed)
+    v = np.clip(np.rint(rng.normal(400, 30, (nz, ny, nx))), 0, 4095)
+    z, y, x = np.mgrid[0:nz, 0:ny, 0:nx]
+    v[((x - nx / 2) / 4) ** 2 + ((y - ny / 3) / 3) ** 2 + ((z - nz / 2) / 3) ** 2 <= 1] = 3000
+    v[rng.random(v.shape) < 0.001] = 4095
+    return v.astype(np.uint16)
+
+
+def test_sigma_wide_radius_requests(lnf):
+    # sigma at r = 3 and 4: the tap kernel takes a request while few voxels pass
+    # the gate, the generic kernel otherwise; whole volumes and ROIs of a sparse
+    # and a dense volume against the oracle
+    sparse = _sparse_u16((61, 40, 37), 2101)
+    dense = phantoms.random_volume((45, 30, 26), 2102, "u16")
+    st = oracle.stats(sparse)
+    for r in (3, 4):
+        prm = oracle.derive_params(st, r)
+        assert np.count_nonzero(sparse >= prm["T"]) * 32 <= sparse.size, "volume not sparse enough"
+    with lnf.Context() as c:
+        ids = [c.register_volume(v) for v in (sparse, dense)]
+        cases = []
+        for vi, vol in enumerate((sparse, dense)):
+            nz, ny, nx = vol.shape
+            for r in (3, 4):
+                for roi in (None, (3, 5, 2, nx - 9, ny // 2, nz - 6)):
+                    out = np.zeros(_roi_shape(roi, vol), vol.dtype)
+                    tk = c.submit(ids[vi], oracle.SIGMA, r, out_host=out, roi_origin=roi[:3] if roi else None,
+                                  roi_dims=roi[3:] if roi else None)
+                    cases.append((tk, out, vol, r, roi))
+        for tk, out, vol, r, roi in cases:
+            c.wait(tk)
+            assert np.array_equal(out, _want(vol, oracle.SIGMA, r, roi)), (vol.dtype, r, roi)
+            c.release(tk)
+
+
 def test_device_result_copy(lnf):
     vol = _vols()[1]
     with lnf.Context() as c:
