@@ -36,6 +36,11 @@ __device__ __forceinline__ u32 eval_filter(int filter, const S &R, const StepPar
     const int rx = p.r[0], ry = p.r[1], rz = p.r[2];
     const u64 box = (u64)(2 * rx + 1) * (2 * ry + 1) * (2 * rz + 1);   // voxels of the box
     const u32 P0 = R.at(0, 0, 0);
+    // every filter is 0 below the noise gate (Eq. 6 / Eq. 7 "0, otherwise", and
+    // the same test in each case below): a gated voxel needs none of its taps,
+    // and a warp whose voxels are all gated skips the tap loops
+    if (P0 < p.T)
+        return 0;
     switch (filter) {
     case 0: {   // mean, Eq. 4
         u64 B = 0;
