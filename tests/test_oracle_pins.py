@@ -253,6 +253,34 @@ def test_brute_force_sigma(dims, dt, seed, mode, k):
             assert got[z, y, x] == b.sigma(r, k, T, x, y, z), ("sigma", r, x, y, z)
 
 
+@pytest.mark.parametrize("dims,dt,seed", [((5, 6, 7), "u16", 31), ((7, 5, 6), "u8", 32)])
+@pytest.mark.parametrize("mode", ["none", "otsu"])
+def test_brute_force_sigma_wide_radius(dims, dt, seed, mode):
+    # r = 3 and 4: cubes of 343 and 729 taps (clamped at the faces).  Thirteen
+    # neighbouring grey levels and k = 3 put most taps in the band, so band
+    # counts of 256 and more occur, which the GPU tap kernel divides by
+    # instead of taking a reciprocal from its table
+    rng = np.random.default_rng(seed)
+    nx, ny, nz = dims
+    base = 2000 if dt == "u16" else 120
+    vol = (base + rng.integers(-6, 7, (nz, ny, nx))).astype(np.uint16 if dt == "u16" else np.uint8)
+    T, cfg = _fixed_T(vol, mode, seed)
+    cfg.sigma_k = 3
+    b = Brute(vol)
+    st = oracle.stats(vol)
+    for r in (3, 4):
+        prm = oracle.derive_params(st, r, cfg)
+        got = oracle.filter_volume(vol, SIGMA, r, params=prm)
+        most = 0
+        for z, y, x in itertools.product(range(nz), range(ny), range(nx)):
+            assert got[z, y, x] == b.sigma(r, 3, T, x, y, z), ("sigma", r, x, y, z)
+            P0 = b.P(x, y, z)
+            most = max(most, sum((v - P0) ** 2 <= 9 * b.var for v in b.cube(r, x, y, z)))
+        assert most >= 256, (r, most)
+        if mode == "otsu":
+            assert 0 < np.count_nonzero(got) < got.size   # the gate splits the volume
+
+
 @pytest.mark.parametrize("dims,dt,seed", SMALL_CASES)
 def test_brute_force_entropy_filter(dims, dt, seed):
     """Eq. 7 in real arithmetic: the fixed-point decision must agree wherever
